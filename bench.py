@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Benchmark: pins/s of the deterministic multilevel path (coarsen every
+level, initial partition, project + label propagation on every level) on
+the config-2 workload (n = m = 1e6, Zipf(2.2) net sizes in [2, 1024],
+preferential pins, node and net weights in [1, 10], k = 8, eps = 0.03).
+
+One step = hg_create from the device-resident input CSR (incidence build)
++ hg_partition (the whole hot path) + hg_destroy.  value = sum over levels
+of the level's pins / step time.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pins/s per coarsen+LP level on 1 GB300, batched vs plain; serve p50/p99 ms"
+K_BLOCKS, EPS_PPM, PASSES, SEED = 8, 30000, 5, 1
+WORKLOAD = ("config 2: n=m=1,000,000, Zipf(2.2) net sizes in [2,1024], preferential pins, "
+            "node/net weights uniform in [1,10], k=8, eps=0.03, S=16, T=1000, f=160, "
+            "5 LP passes per level, full V-cycle")
+L2_FLUSH_BYTES = 512 << 20
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def oracle_sample(target_seconds: float = 15.0):
+    """Times the CPU oracle (as it stands, one core) on a bounded sample of
+    the same workload shape: config 2 scaled to n = m = 40,000."""
+    import numpy as np
+
+    import oracle
+    import synth
+    hgr = synth.config2(SEED, n=40_000)
+    t0 = time.perf_counter()
+    vc = oracle.multilevel(hgr, K_BLOCKS, EPS_PPM, S=16, T=1000, factor=160, seed=SEED,
+                           max_passes=PASSES)
+    dt = time.perf_counter() - t0
+    pins = sum(int(l.p) for l in vc.levels)
+    return dict(value=pins / dt, seconds=dt, pins=pins, levels=len(vc.levels),
+                sample=f"config 2 scaled to n=m=40,000 ({hgr.p} pins, {len(vc.levels)} levels), "
+                       "full V-cycle, one process, single-threaded oracle")
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    vals = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample()
+        if i >= args.warmup:
+            vals.append(r["value"])
+            info = r
+    v = statistics.mean(vals) if vals else 0.0
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "pins/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": info["seconds"] * 1e3 if info else None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": {"workload": WORKLOAD + " (CPU oracle on a bounded sample)"},
+        "cpu_baseline": {"value": v, "unit": "pins/s", "cores": 1, "kind": "oracle",
+                         "sample": info["sample"] if info else ""},
+        "e2e": {"value": v, "unit": "pins/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ GPU path
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2303_17679_gb300 import build as libbuild
+    from paper_2303_17679_gb300 import hg
+
+    torch.cuda.set_device(local)
+    libbuild.build()
+    hg.load()
+    stream = torch.cuda.current_stream()
+    hgr = synth.config2(SEED)
+    opt = hg.hg_default_options()
+    opt.seed = SEED
+    t_in = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).cuda()
+    d_off, d_pins, d_w, d_c = t_in(hgr.offsets), t_in(hgr.pins), t_in(hgr.net_w), t_in(hgr.node_w)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory()
+    h_off, h_pins, h_w, h_c = pin(hgr.offsets), pin(hgr.pins), pin(hgr.net_w), pin(hgr.node_w)
+    part = torch.empty(hgr.n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def step(kernel_events=False, host_inputs=False):
+        if host_inputs:
+            h = hg.hg_create(hgr.n, hgr.m, h_off.numpy(), h_pins.numpy(), h_w.numpy(), h_c.numpy(),
+                             hg.HG_MEM_HOST, opt, stream)
+        else:
+            h = hg.hg_create(hgr.n, hgr.m, d_off, d_pins, d_w, d_c, hg.HG_MEM_DEVICE, opt, stream)
+        try:
+            if kernel_events:
+                hg.hg_enable_timing(h, 2)
+            obj = hg.hg_partition(h, K_BLOCKS, EPS_PPM, PASSES, part)
+            nl = hg.hg_num_levels(h)
+            levels = [hg.hg_level_info(h, i) for i in range(nl)]
+            stats = hg.hg_get_stats(h)
+            if host_inputs:
+                out = part.cpu()
+                assert out.shape[0] == hgr.n
+        finally:
+            hg.hg_destroy(h)
+        return obj, levels, stats
+
+    for _ in range(args.warmup):
+        obj, levels, _ = step()
+    torch.cuda.synchronize()
+    pins_per_step = sum(p for (_, _, p) in levels)
+
+    # ---- device-resident timed region
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    step_ms = []
+    launches = 0
+    agg = {}
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        obj_k, lv_k, st = step(kernel_events=True)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        launches += st["launches"]
+        for key, val in st.items():
+            agg[key] = agg.get(key, 0) + val
+        assert obj_k == obj and lv_k == levels, "non-deterministic result"
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    t_total = max_over_ranks(world, sum(step_ms) / 1e3)
+    total_pins = sum_over_ranks(world, pins_per_step * args.steps)
+    value = total_pins / t_total
+
+    # ---- end to end through the public API with host buffers
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0.record(stream)
+        step(host_inputs=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_t = max_over_ranks(world, sum(e2e_ms) / 1e3)
+    e2e_value = total_pins / e2e_t
+    h2d = 4 * (hgr.m + 1 + hgr.p + hgr.m + hgr.n)
+    d2h = 4 * hgr.n
+
+    # ---- roofline of the dominant kernel class (per-launch events inside the timed region)
+    peak, peak_kind = peaks()
+    rating_ms = agg["ms_rating_kernels"]
+    gain_ms = agg["ms_lp_gain_kernels"]
+    # algorithmic bytes (see the design notes): gain = 16 B per node + 20 B per incidence;
+    # rating = 17 B per node + 16 B per incidence + 13 B per pin visit
+    gain_bytes = 16 * agg["lp_nodes"] + 20 * agg["lp_incidences"]
+    rating_bytes = 17 * agg["rating_nodes"] + 16 * agg["rating_incidences"] + 13 * agg["rating_pin_visits"]
+    if rating_ms >= gain_ms:
+        kname, kms, kbytes, klaunch = "k_rate_* (heavy-edge rating)", rating_ms, rating_bytes, agg["rating_launches"]
+    else:
+        kname, kms, kbytes, klaunch = "k_lp_gain (LP best moves)", gain_ms, gain_bytes, agg["lp_gain_launches"]
+    achieved = (kbytes / (kms / 1e3)) / 1e9 if kms > 0 else 0.0
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "pins/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (seeded generator, config 2 shape)",
+        "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "flushed between steps (512 MiB write outside the timed events)",
+                   "levels": len(levels), "pins_per_step": pins_per_step, "objective": obj},
+        "e2e": {"value": e2e_value, "unit": "pins/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": statistics.mean(e2e_ms)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak_kind": peak_kind, "launches": int(klaunch),
+                     "ms_total": kms, "share_of_step": kms / sum(step_ms)},
+        "clocks": clocks,
+        "wall_s": wall,
+        "phase_ms": {"rating_kernels": rating_ms / args.steps, "lp_gain_kernels": gain_ms / args.steps},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = oracle_sample()
+        line["cpu_baseline"] = {"value": cb["value"], "unit": "pins/s", "cores": 1, "kind": "oracle",
+                                "sample": cb["sample"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,234 @@
+/*
+ * hg.h - C ABI of the GB300 deterministic hypergraph coarsening and
+ * label-propagation library (Mt-KaHyPar's deterministic multilevel path,
+ * arXiv 2303.17679).
+ *
+ * The library holds a level hierarchy H_0 (the input) ... H_L in device
+ * memory and offers the per-level operations of Algorithm 1: one
+ * deterministic clustering + contraction step, the seeded initial partition,
+ * projection, and deterministic lambda-1 label propagation with the objective.
+ *
+ * Conventions for every entry point:
+ *  - Return value: HG_OK (0) on success, HG_STOP (1) where documented, a
+ *    negative HG_ERR_* code otherwise.  No C++ exception crosses the ABI.
+ *  - Integer types: node, net and block ids, node and net weights are int32;
+ *    pin offsets are int32 (so fewer than 2^31 pins); objectives, block
+ *    weights and move counts are int64.
+ *  - Memory: "host" pointers are ordinary CPU memory, "device" pointers are
+ *    CUDA global memory of the device current at hg_create.  The caller owns
+ *    every pointer it passes and keeps it valid for the duration of the call;
+ *    the library copies what it keeps.  The handle owns all device memory of
+ *    the hierarchy and frees it in hg_destroy.
+ *  - Streams: all work is issued on the stream given to hg_create, in
+ *    stream order.  Entry points that return host scalars synchronize that
+ *    stream before returning.  One handle must not be used from two host
+ *    threads at once.
+ *  - Errors: HG_ERR_INVALID for malformed arguments (nothing is changed),
+ *    HG_ERR_UNSUPPORTED for sizes outside the supported range, HG_ERR_OOM
+ *    when device memory runs out, HG_ERR_CUDA for a CUDA error (sticky: the
+ *    handle then only accepts hg_destroy and the query calls), HG_ERR_TIMEOUT
+ *    when a bounded device-side wait gave up, HG_ERR_STATE for calls out of
+ *    order (for example refining a level that does not exist).
+ *  - Determinism: for the same inputs and options every output is bit-identical
+ *    from run to run, whatever the launch configuration (Sec. 11).
+ */
+#ifndef HG_H
+#define HG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HG_OK 0
+#define HG_STOP 1
+#define HG_ERR_INVALID (-1)
+#define HG_ERR_UNSUPPORTED (-2)
+#define HG_ERR_OOM (-3)
+#define HG_ERR_CUDA (-4)
+#define HG_ERR_TIMEOUT (-5)
+#define HG_ERR_STATE (-6)
+
+#define HG_MEM_HOST 0
+#define HG_MEM_DEVICE 1
+
+#define HG_MAX_K 64
+
+typedef struct hg_t hg_t;
+
+/* Options fixed for the lifetime of a handle. */
+typedef struct {
+  /* Seed of every hashed decision: sub-round of a node (Sec. 11, synchronous
+   * local moving in sub-rounds) and the order of the initial partition. */
+  uint64_t seed;
+  /* S: number of sub-rounds of one clustering round and of one label-
+   * propagation pass (Sec. 11).  1 <= S <= 256.  Default 16. */
+  int32_t subrounds;
+  /* T: nets with more than T pins are skipped by the rating function but kept
+   * everywhere else.  2 <= T <= 2^20.  Default 1000. */
+  int32_t rating_max_net_size;
+  /* f in the contraction limit f*k and in c_max = ceil(c(V) / (f*k))
+   * (Sec. 4.1, "Contraction Limit"; the paper uses 160).  Default 160. */
+  int32_t contraction_limit_factor;
+  /* Number of bits kept of the identical-net fingerprint (0 = all 64).  A
+   * test knob: fewer bits force fingerprint collisions, which the exact pin
+   * comparison must resolve; results do not change, only the work. */
+  int32_t fingerprint_bits;
+  /* Optional device allocator (for example a framework's caching allocator).
+   * Both NULL: stream-ordered cudaMallocAsync / cudaFreeAsync. */
+  void* (*dev_alloc)(size_t bytes, void* ctx);
+  void (*dev_free)(void* ptr, void* ctx);
+  void* alloc_ctx;
+} hg_options;
+
+/* Per-phase device time (milliseconds, from CUDA events) and work counters,
+ * accumulated since hg_create or the last hg_reset_stats.  Phases are only
+ * timed when hg_enable_timing(h, 1) was called. */
+typedef struct {
+  double ms_transpose;  /* incidence build (a1) */
+  double ms_rating;     /* heavy-edge rating of all sub-rounds (a3) */
+  double ms_approve;    /* cluster approval of all sub-rounds (a4) */
+  double ms_contract;   /* map, remap, identical nets, compaction (a5-a8) */
+  double ms_project;    /* projection (a9) */
+  double ms_phi;        /* pin counts, connectivity sets, block weights (a10) */
+  double ms_lp_gain;    /* label-propagation best moves (a11) */
+  double ms_lp_select;  /* pair bucketing and prefix selection (a12) */
+  double ms_lp_apply;   /* move application (a13) */
+  double ms_objective;  /* objective (a14) */
+  double ms_initial;    /* host initial partition incl. copies */
+  int64_t launches;     /* kernels launched */
+  int64_t rating_launches;
+  int64_t rating_pin_visits;  /* pins read by the rating kernels */
+  int64_t rating_nodes;       /* nodes rated */
+  int64_t rating_incidences;  /* incident nets read by the rating kernels */
+  int64_t lp_incidences;      /* incident nets read by the gain kernels */
+  int64_t lp_nodes;           /* nodes evaluated by the gain kernels */
+  int64_t lp_gain_launches;
+  double ms_rating_kernels;   /* sum of rating kernel durations (timing on) */
+  double ms_lp_gain_kernels;  /* sum of gain kernel durations (timing on) */
+} hg_stats;
+
+/* Fills *opt with the defaults listed above (seed 1). */
+void hg_default_options(hg_options* opt);
+
+/* Creates a handle holding level 0 = the input hypergraph H = (V, E, c, w)
+ * of Sec. 2 in net-major CSR: the pins of net e are
+ * pins[net_offsets[e] .. net_offsets[e+1]).
+ *   n, m          nodes and nets, n >= 1, m >= 0
+ *   net_offsets   m+1 entries, net_offsets[0] = 0, non-decreasing
+ *   pins          net_offsets[m] entries in [0, n); no node twice in a net;
+ *                 nets may not be empty
+ *   net_weights   m entries > 0, or NULL for all 1
+ *   node_weights  n entries > 0, or NULL for all 1
+ *   mem           HG_MEM_HOST or HG_MEM_DEVICE: where the four arrays live
+ *   opt           options, or NULL for the defaults
+ *   cuda_stream   cudaStream_t to issue all work on (NULL = legacy default)
+ * Builds the incident-net lists I(u) on the device (a1).  Rejects with
+ * HG_ERR_INVALID: bad sizes or offsets, pins out of range, repeated pins in
+ * a net, empty nets, weights <= 0, total node or net weight >= 2^31
+ * (host inputs are checked on the host; device inputs are checked on the
+ * device).  *out is NULL on failure. */
+int hg_create(int32_t n, int32_t m, const int32_t* net_offsets, const int32_t* pins,
+              const int32_t* net_weights, const int32_t* node_weights, int32_t mem,
+              const hg_options* opt, void* cuda_stream, hg_t** out);
+
+/* One deterministic clustering + contraction step (Sec. 4.1, Sec. 4.2,
+ * Sec. 11 "Deterministic Clustering for Coarsening") on the coarsest level
+ * built so far, producing a new resident level.  k (2..64) sets the
+ * contraction limit f*k and c_max = ceil(c(V) / (f*k)).
+ * Returns HG_STOP without building a level when the coarsest level has at
+ * most f*k nodes, or when the previous step shrank the node count by less
+ * than 1 % (that level is kept).  On HG_OK the out-parameters (each may be
+ * NULL) receive the new level's index and sizes. */
+int hg_coarsen_level(hg_t* h, int32_t k, int32_t* out_level, int32_t* out_n, int32_t* out_m,
+                     int64_t* out_p);
+
+/* Number of levels held (1 + coarsening steps done) and the sizes of one. */
+int hg_num_levels(const hg_t* h, int32_t* out_levels);
+int hg_level_info(const hg_t* h, int32_t level, int32_t* out_n, int32_t* out_m, int64_t* out_p);
+
+/* Seeded initial partition of a level (the paper's portfolio of Sec. 5 is
+ * replaced by one deterministic rule): nodes in order of
+ * (mix64(seed ^ 2^63 ^ u), u), each to the lightest block so far, ties to the
+ * smaller block id; mix64 = the SplitMix64 output function.  Computed on the
+ * host from the level's node weights.  part: device, n_level int32, written. */
+int hg_initial_partition(hg_t* h, int32_t level, int32_t k, int32_t* part);
+
+/* Projection Pi_l[u] = Pi_{l+1}[map(u)] from level coarse_level (>= 1) to
+ * coarse_level - 1 (Algorithm 1, uncoarsening).  Both device int32 arrays;
+ * coarse_part has n_{coarse_level} entries, fine_part n_{coarse_level-1}. */
+int hg_project(hg_t* h, int32_t coarse_level, const int32_t* coarse_part, int32_t* fine_part);
+
+/* Deterministic lambda-1 label propagation on one level (Sec. 11
+ * "Deterministic Label Propagation Refinement", gain of Sec. 6): up to
+ * max_passes passes of S sub-rounds; each node of a sub-round proposes its
+ * best positive-gain move from the sub-round's starting state; per block pair
+ * the moves are ordered by (gain desc, id asc) and the last feasible prefix
+ * pair on the merge path is applied, with per-pair slack
+ * floor(max(0, L_max - c(V_i)) / (k-1)) and
+ * L_max = floor(ceil(c(V)/k) * (10^6 + eps_ppm) / 10^6) (Sec. 2).  A pass
+ * that applies no move ends the call.
+ *   part           device, n_level int32 in [0, k), read and updated in place
+ *   out_objective  host, may be NULL: f_{lambda-1} after refinement
+ *   out_moves      host, may be NULL: moves applied
+ * k in 2..64, eps_ppm >= 0, max_passes >= 0.  Synchronizes the stream. */
+int hg_lp_refine(hg_t* h, int32_t level, int32_t k, int32_t eps_ppm, int32_t max_passes,
+                 int32_t* part, int64_t* out_objective, int64_t* out_moves);
+
+/* Connectivity objective f_{lambda-1} = sum over nets of (lambda(e)-1) w(e)
+ * (Sec. 2) of a partition (device int32, n_level entries in [0, k)) into
+ * *out (host).  k in 1..64.  Synchronizes the stream. */
+int hg_objective(hg_t* h, int32_t level, int32_t k, const int32_t* part, int64_t* out);
+
+/* Pin counts Phi(e, V_i) (host m x k int32, may be NULL), connectivity sets
+ * Lambda(e) as bit masks (host m uint64, may be NULL) and block weights c(V_i)
+ * (host k int64, may be NULL) of a partition (device) - for inspection. */
+int hg_pin_counts(hg_t* h, int32_t level, int32_t k, const int32_t* part, int32_t* phi,
+                  uint64_t* lambda, int64_t* block_weights);
+
+/* The whole deterministic multilevel path (Algorithm 1 without FM and
+ * flows): coarsen until HG_STOP, initial partition of the coarsest level,
+ * label propagation on it, then project and refine level by level down to
+ * level 0.  part: device, n_0 int32, written.  Levels already built are
+ * reused; the handle keeps all levels afterwards. */
+int hg_partition(hg_t* h, int32_t k, int32_t eps_ppm, int32_t max_passes, int32_t* part,
+                 int64_t* out_objective);
+
+/* Copies a level to the host in canonical form.  Any pointer may be NULL.
+ *   offsets (m+1), pins (p), net_weights (m), node_weights (n);
+ *   map (n): coarse node of every node in level+1 (only for levels that have
+ *   been coarsened; HG_ERR_STATE otherwise when map != NULL);
+ *   rep (n): representative of every node in the clustering that produced
+ *   level+1 (same condition). */
+int hg_get_level(const hg_t* h, int32_t level, int32_t* offsets, int32_t* pins,
+                 int32_t* net_weights, int32_t* node_weights, int32_t* map, int32_t* rep);
+
+/* Copies the incident-net lists of a level to the host: offsets (n+1) and
+ * nets (p).  The order of nets inside one list is unspecified. */
+int hg_get_incidence(const hg_t* h, int32_t level, int32_t* offsets, int32_t* nets);
+
+/* Drops every level above `level` (keeps 0..level) so coarsening can be
+ * redone, e.g. with another k. */
+int hg_truncate(hg_t* h, int32_t level);
+
+/* Statistics (see hg_stats). */
+int hg_enable_timing(hg_t* h, int32_t on);
+int hg_get_stats(hg_t* h, hg_stats* out);
+int hg_reset_stats(hg_t* h);
+
+/* Frees everything the handle owns.  Safe on NULL and after any error. */
+int hg_destroy(hg_t* h);
+
+/* Static description of a status code. */
+const char* hg_strerror(int status);
+
+/* Library version string. */
+const char* hg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HG_H */

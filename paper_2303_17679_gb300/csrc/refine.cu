@@ -1,0 +1,633 @@
+// Uncoarsening on the device: projection (Algorithm 1), pin counts and
+// connectivity sets (Sec. 2, Sec. 6.1 data layout), the connectivity
+// objective (Sec. 2), and deterministic label propagation (Sec. 11
+// "Deterministic Label Propagation Refinement" with the gain of Sec. 6).
+//
+// Layout: Phi is a dense m x k int32 table (row = net), Lambda one 64-bit
+// mask per net (k <= 64), block weights int64[k].  One label-propagation
+// sub-round is four launches: best moves (a11), bucketing by block pair and
+// per-pair prefix selection (a12), application (a13).
+#include <climits>
+
+#include "common.cuh"
+#include "pintile.cuh"
+
+namespace hgk {
+
+namespace {
+
+constexpr int WARPS = 8;  // warps per block for warp-per-item kernels
+
+// ------------------------------------------------------------ projection
+
+__global__ void k_project(const int32_t* __restrict__ map, const int32_t* __restrict__ coarse_part,
+                          int32_t n, int32_t* __restrict__ fine_part) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x)
+    fine_part[u] = coarse_part[map[u]];
+}
+
+// ------------------------------------------------------ pin counts (a10)
+
+// Phi(e, V_i) += 1 and Lambda(e) |= bit(i) for every pin; lanes that hold the
+// same (net, block) combine their increments first.
+__global__ void __launch_bounds__(PIN_TILE_THREADS)
+k_pin_counts(const int32_t* __restrict__ eoff, const int32_t* __restrict__ pins,
+             const int32_t* __restrict__ tile_net, int32_t m, int64_t p,
+             const int32_t* __restrict__ part, int k, int32_t* __restrict__ phi,
+             unsigned long long* __restrict__ lam) {
+  __shared__ int32_t s_off[PIN_TILE + 3];
+  const int64_t ntiles = num_pin_tiles(p);
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    PinTileView v = stage_pin_tile(eoff, tile_net, m, p, t, s_off);
+    for (int64_t base = v.q0; base < v.q1; base += blockDim.x) {
+      const int64_t q = base + threadIdx.x;
+      const bool valid = q < v.q1;
+      int64_t key = -1 - (int64_t)threadIdx.x;  // unique for idle lanes
+      int32_t e = 0, b = 0;
+      if (valid) {
+        e = v.e_lo + net_in_tile(s_off, v.count, q);
+        b = part[pins[q]];
+        key = (int64_t)e * k + b;
+      }
+      const unsigned peers = __match_any_sync(FULL, (unsigned long long)key);
+      const int leader = __ffs(peers) - 1;
+      if (valid && lane_id() == leader) {
+        atomicAdd(&phi[(int64_t)e * k + b], __popc(peers));
+        atomicOr(&lam[e], 1ull << b);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_block_weights(const int32_t* __restrict__ part, const int32_t* __restrict__ c,
+                                int32_t n, int k, long long* __restrict__ bw) {
+  __shared__ long long s_bw[HG_MAX_K];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) s_bw[i] = 0;
+  __syncthreads();
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x)
+    atomic_add_i64(&s_bw[part[u]], (long long)c[u]);
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x)
+    if (s_bw[i]) atomic_add_i64(&bw[i], s_bw[i]);
+}
+
+// ------------------------------------------------------- objective (a14)
+
+__global__ void k_objective(const unsigned long long* __restrict__ lam,
+                            const int32_t* __restrict__ w, int32_t m,
+                            unsigned long long* __restrict__ out) {
+  __shared__ int64_t red[32];
+  int64_t f = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int l = __popcll(lam[e]);
+    if (l > 1) f += (int64_t)(l - 1) * w[e];
+  }
+  f = block_sum(f, red);
+  if (threadIdx.x == 0 && f) atomicAdd(out, (unsigned long long)f);
+}
+
+// -------------------------------------------- sub-round node lists (a11)
+
+__global__ void k_lp_count(const int32_t* __restrict__ ioff, int32_t n, uint64_t seed, int level,
+                           int pass, int S, int32_t* __restrict__ cnt) {
+  extern __shared__ int32_t s_cnt[];
+  for (int i = threadIdx.x; i < S; i += blockDim.x) s_cnt[i] = 0;
+  __syncthreads();
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    if (ioff[u + 1] == ioff[u]) continue;  // isolated nodes never move
+    atomicAdd(&s_cnt[subround_of_node_lp(seed, level, pass, (int)u, S)], 1);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < S; i += blockDim.x)
+    if (s_cnt[i]) atomicAdd(&cnt[i], s_cnt[i]);
+}
+
+// Every block recomputes the (tiny) exclusive scan of the S counts.
+__global__ void k_lp_scatter(const int32_t* __restrict__ ioff, int32_t n, uint64_t seed, int level,
+                             int pass, int S, const int32_t* __restrict__ cnt,
+                             int32_t* __restrict__ fill, int32_t* __restrict__ off,
+                             int32_t* __restrict__ list) {
+  extern __shared__ int32_t s_off[];
+  if (threadIdx.x == 0) {
+    int32_t run = 0;
+    for (int i = 0; i < S; ++i) {
+      s_off[i] = run;
+      run += cnt[i];
+    }
+    s_off[S] = run;
+    if (blockIdx.x == 0)
+      for (int i = 0; i <= S; ++i) off[i] = s_off[i];
+  }
+  __syncthreads();
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    if (ioff[u + 1] == ioff[u]) continue;
+    const int s = subround_of_node_lp(seed, level, pass, (int)u, S);
+    list[s_off[s] + atomicAdd(&fill[s], 1)] = (int32_t)u;
+  }
+}
+
+// Per sub-round bookkeeping words.
+enum SubroundWord { SW_MOVES = 0, SW_APPROVED = 1, SW_WORDS = 4 };
+
+// ------------------------------------------------- best moves (a11)
+
+// One warp per node u of the sub-round.  With b(u) = w(nets where u is the
+// only pin of its block) and W_I = w(I(u)), the gain of Sec. 6 is
+//   g(u, t) = b(u) - W_I + w({e in I(u) : t in Lambda(e)}),
+// evaluated for all t at once: lane L accumulates blocks L and L + 32 while
+// the warp broadcasts each incident net's (weight, Lambda) in turn.  The
+// best t != Pi[u] by (gain desc, t asc) is proposed if its gain is positive.
+__global__ void __launch_bounds__(WARPS * 32)
+k_lp_gain(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
+          const int32_t* __restrict__ w, const int32_t* __restrict__ phi,
+          const unsigned long long* __restrict__ lam, const int32_t* __restrict__ part, int k,
+          const int32_t* __restrict__ list, const int32_t* __restrict__ sr_off, int s,
+          int32_t* __restrict__ mv_u, int32_t* __restrict__ mv_to, long long* __restrict__ mv_g,
+          int32_t* __restrict__ dcount, int32_t* __restrict__ words,
+          unsigned long long* __restrict__ work) {
+  const int lane = lane_id();
+  const int32_t lo = sr_off[s], hi = sr_off[s + 1];
+  int64_t incid = 0;
+  for (int32_t i = lo + blockIdx.x * WARPS + warp_in_block(); i < hi; i += gridDim.x * WARPS) {
+    const int32_t u = list[i];
+    const int from = part[u];
+    const int32_t beg = ioff[u], end = ioff[u + 1];
+    int64_t acc0 = 0, acc1 = 0, ben = 0, wsum = 0;
+    for (int32_t c0 = beg; c0 < end; c0 += 32) {
+      const int32_t j = c0 + lane;
+      int32_t we = 0;
+      unsigned long long le = 0;
+      if (j < end) {
+        const int32_t e = inets[j];
+        we = w[e];
+        le = lam[e];
+        if (phi[(int64_t)e * k + from] == 1) ben += we;
+        wsum += we;
+      }
+      const int cnt = min(32, end - c0);
+      for (int jj = 0; jj < cnt; ++jj) {
+        const int32_t wj = __shfl_sync(FULL, we, jj);
+        const unsigned long long lj = __shfl_sync(FULL, le, jj);
+        if ((lj >> lane) & 1ull) acc0 += wj;
+        if ((lj >> (lane + 32)) & 1ull) acc1 += wj;
+      }
+    }
+    incid += end - beg;
+    ben = warp_sum(ben);
+    wsum = warp_sum(wsum);
+    // candidate value: (gain, -t) packed so that a max picks the smaller t on ties
+    long long best_g = LLONG_MIN;
+    int best_t = -1;
+    if (lane < k && lane != from) {
+      best_g = ben - wsum + acc0;
+      best_t = lane;
+    }
+    if (lane + 32 < k && lane + 32 != from) {
+      const long long g1 = ben - wsum + acc1;
+      if (g1 > best_g) {
+        best_g = g1;
+        best_t = lane + 32;
+      }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      const long long og = __shfl_xor_sync(FULL, best_g, d);
+      const int ot = __shfl_xor_sync(FULL, best_t, d);
+      if (og > best_g || (og == best_g && ot >= 0 && (best_t < 0 || ot < best_t))) {
+        best_g = og;
+        best_t = ot;
+      }
+    }
+    if (lane == 0 && best_g > 0) {
+      const int32_t slot = atomicAdd(&words[SW_MOVES], 1);
+      mv_u[slot] = u;
+      mv_to[slot] = best_t;
+      mv_g[slot] = best_g;
+      atomicAdd(&dcount[from * k + best_t], 1);
+    }
+  }
+  if (lane == 0 && incid) atomicAdd(work, (unsigned long long)incid);
+}
+
+// ------------------------------------- pair bucketing + selection (a12)
+
+// Exclusive scan of the k*k direction counts into s_doff (by thread 0; k*k
+// <= 4096 small integers).
+__device__ void direction_offsets(const int32_t* dcount, int kk, int32_t* s_doff) {
+  if (threadIdx.x == 0) {
+    int32_t run = 0;
+    for (int d = 0; d < kk; ++d) {
+      s_doff[d] = run;
+      run += dcount[d];
+    }
+    s_doff[kk] = run;
+  }
+  __syncthreads();
+}
+
+__global__ void k_lp_bucket(const int32_t* __restrict__ mv_u, const int32_t* __restrict__ mv_to,
+                            const int32_t* __restrict__ part, int k,
+                            const int32_t* __restrict__ dcount, int32_t* __restrict__ dfill,
+                            int32_t* __restrict__ doff, const int32_t* __restrict__ words,
+                            int32_t* __restrict__ bucket) {
+  extern __shared__ int32_t s_doff[];
+  const int kk = k * k;
+  direction_offsets(dcount, kk, s_doff);
+  if (blockIdx.x == 0)
+    for (int d = threadIdx.x; d <= kk; d += blockDim.x) doff[d] = s_doff[d];
+  const int32_t nm = words[SW_MOVES];
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nm; i += gridDim.x * blockDim.x) {
+    const int d = part[mv_u[i]] * k + mv_to[i];
+    bucket[s_doff[d] + atomicAdd(&dfill[d], 1)] = i;
+  }
+}
+
+constexpr int SEL_THREADS = 256;
+constexpr int SEL_SMEM_CAP = 1024;  // moves per direction sorted in shared memory
+
+// Sort key: gain descending, node id ascending (gains are < 2^31).
+__device__ __forceinline__ unsigned long long sel_key(long long g, int32_t u) {
+  return ((unsigned long long)(0x7fffffffLL - g) << 32) | (unsigned)u;
+}
+
+// Bitonic sort of P (a power of two) keys in buf (shared or global) by the block.
+__device__ void block_bitonic_sort(unsigned long long* buf, int P) {
+  for (int kk = 2; kk <= P; kk <<= 1) {
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const unsigned long long a = buf[i], b = buf[ixj];
+          const bool up = (i & kk) == 0;
+          if ((a > b) == up) {
+            buf[i] = b;
+            buf[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// pre[x] = weight of the first x sorted moves, x = 0..cnt (block-wide scan).
+__device__ void block_weight_prefix(const unsigned long long* keys, int cnt,
+                                    const int32_t* __restrict__ c, long long* pre,
+                                    long long* s_red) {
+  if (threadIdx.x == 0) {
+    s_red[32] = 0;
+    pre[0] = 0;
+  }
+  __syncthreads();
+  for (int base = 0; base < cnt; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const long long v = i < cnt ? (long long)c[(int32_t)(keys[i] & 0xffffffffu)] : 0;
+    long long x = warp_inclusive_scan(v);
+    if (lane_id() == 31) s_red[warp_in_block()] = x;
+    __syncthreads();
+    if (warp_in_block() == 0) {
+      long long y = lane_id() < (int)(blockDim.x >> 5) ? s_red[lane_id()] : 0;
+      y = warp_inclusive_scan(y);
+      if (lane_id() < (int)(blockDim.x >> 5)) s_red[lane_id()] = y;
+    }
+    __syncthreads();
+    const long long carry = s_red[32];
+    const long long before = warp_in_block() ? s_red[warp_in_block() - 1] : 0;
+    if (i < cnt) pre[i + 1] = carry + before + x;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) s_red[32] = carry + before + x;
+    __syncthreads();
+  }
+}
+
+// One block per unordered block pair (a, b), a < b.  Sorts the moves a->b
+// and b->a by (gain desc, id asc), builds their weight prefixes A and B, and
+// finds the last state (i, j) on the merge path of A[0..na-1] and
+// B[0..nb-1] (ties to A) with -slack_a <= A[i] - B[j] <= slack_b.  Moves in
+// the chosen prefixes are approved.
+__global__ void __launch_bounds__(SEL_THREADS)
+k_lp_select(const int32_t* __restrict__ bucket, const int32_t* __restrict__ doff,
+            const int32_t* __restrict__ dcount, const int32_t* __restrict__ mv_u,
+            const int32_t* __restrict__ mv_to, const long long* __restrict__ mv_g,
+            const int32_t* __restrict__ c, const long long* __restrict__ bw, long long lmax, int k,
+            unsigned long long* __restrict__ gkeys, long long* __restrict__ gpre,
+            int32_t* __restrict__ ap_u, int32_t* __restrict__ ap_from,
+            int32_t* __restrict__ ap_to, int32_t* __restrict__ words) {
+  __shared__ unsigned long long s_keys[2][SEL_SMEM_CAP];
+  __shared__ long long s_pre[2][SEL_SMEM_CAP + 1];
+  __shared__ long long s_red[33];
+  __shared__ int s_best;
+  // decode the pair index into (a, b), a < b
+  int pair = blockIdx.x, a = 0;
+  while (pair >= k - 1 - a) {
+    pair -= k - 1 - a;
+    ++a;
+  }
+  const int b = a + 1 + pair;
+  const int dab = a * k + b, dba = b * k + a;
+  const int na = dcount[dab], nb = dcount[dba];
+  if (na + nb == 0) return;
+  const int oa = doff[dab], ob = doff[dba];
+
+  auto pow2 = [](int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+  };
+  const int Pa = pow2(na), Pb = pow2(nb);
+  // buffers: shared memory when the padded sequence fits, else a global
+  // region of 2 * count slots at twice the direction's bucket offset
+  unsigned long long* ka = Pa <= SEL_SMEM_CAP ? s_keys[0] : gkeys + 2 * (int64_t)oa;
+  unsigned long long* kb = Pb <= SEL_SMEM_CAP ? s_keys[1] : gkeys + 2 * (int64_t)ob;
+  long long* A = na <= SEL_SMEM_CAP ? s_pre[0] : gpre + (int64_t)oa + dab;
+  long long* B = nb <= SEL_SMEM_CAP ? s_pre[1] : gpre + (int64_t)ob + dba;
+
+  for (int i = threadIdx.x; i < Pa; i += blockDim.x) {
+    if (i < na) {
+      const int32_t mi = bucket[oa + i];
+      ka[i] = sel_key(mv_g[mi], mv_u[mi]);
+    } else {
+      ka[i] = ~0ull;
+    }
+  }
+  for (int i = threadIdx.x; i < Pb; i += blockDim.x) {
+    if (i < nb) {
+      const int32_t mi = bucket[ob + i];
+      kb[i] = sel_key(mv_g[mi], mv_u[mi]);
+    } else {
+      kb[i] = ~0ull;
+    }
+  }
+  __syncthreads();
+  block_bitonic_sort(ka, Pa);
+  block_bitonic_sort(kb, Pb);
+  block_weight_prefix(ka, na, c, A, s_red);
+  block_weight_prefix(kb, nb, c, B, s_red);
+
+  const long long slack_a = (lmax - bw[a] > 0 ? lmax - bw[a] : 0) / (k - 1);
+  const long long slack_b = (lmax - bw[b] > 0 ? lmax - bw[b] : 0) / (k - 1);
+  if (threadIdx.x == 0) s_best = 0;
+  __syncthreads();
+  // diagonal r: i(r) = number of A-steps among the first r steps
+  int best = 0;
+  for (int r = threadIdx.x; r <= na + nb; r += blockDim.x) {
+    int lo = r - nb > 0 ? r - nb : 0, hi = r < na ? r : na;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (A[mid] <= B[r - 1 - mid]) lo = mid + 1; else hi = mid;
+    }
+    const long long x = A[lo] - B[r - lo];
+    if (-slack_a <= x && x <= slack_b) best = r > best ? r : best;
+  }
+  best = warp_max(best);
+  if (lane_id() == 0) atomicMax(&s_best, best);
+  __syncthreads();
+  const int r = s_best;
+  int lo = r - nb > 0 ? r - nb : 0, hi = r < na ? r : na;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (A[mid] <= B[r - 1 - mid]) lo = mid + 1; else hi = mid;
+  }
+  const int ia = lo, jb = r - lo;
+  for (int i = threadIdx.x; i < ia + jb; i += blockDim.x) {
+    const bool fromA = i < ia;
+    const unsigned long long key = fromA ? ka[i] : kb[i - ia];
+    const int32_t u = (int32_t)(key & 0xffffffffu);
+    const int32_t slot = atomicAdd(&words[SW_APPROVED], 1);
+    ap_u[slot] = u;
+    ap_from[slot] = fromA ? a : b;
+    ap_to[slot] = fromA ? b : a;
+  }
+}
+
+// ------------------------------------------------------- apply (a13)
+
+// One warp per approved move (u, s, t): Pi[u] = t, block weights, and for
+// each e in I(u): Phi(e, s) -= 1, Phi(e, t) += 1, clearing bit s of Lambda(e)
+// when Phi(e, s) reaches 0 and setting bit t when Phi(e, t) leaves 0
+// (Algorithm 3's updates; the atomic xor flips commute, so the final masks
+// equal {i : Phi(e, i) > 0} whatever the order of the moves).
+__global__ void __launch_bounds__(WARPS * 32)
+k_lp_apply(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
+           const int32_t* __restrict__ c, int k, const int32_t* __restrict__ ap_u,
+           const int32_t* __restrict__ ap_from, const int32_t* __restrict__ ap_to,
+           const int32_t* __restrict__ words, int32_t* __restrict__ part,
+           int32_t* __restrict__ phi, unsigned long long* __restrict__ lam,
+           long long* __restrict__ bw, unsigned long long* __restrict__ moved) {
+  const int32_t na = words[SW_APPROVED];
+  for (int32_t i = blockIdx.x * WARPS + warp_in_block(); i < na; i += gridDim.x * WARPS) {
+    const int32_t u = ap_u[i];
+    const int s = ap_from[i], t = ap_to[i];
+    for (int32_t j = ioff[u] + lane_id(); j < ioff[u + 1]; j += 32) {
+      const int32_t e = inets[j];
+      if (atomicSub(&phi[(int64_t)e * k + s], 1) == 1) atomicXor(&lam[e], 1ull << s);
+      if (atomicAdd(&phi[(int64_t)e * k + t], 1) == 0) atomicXor(&lam[e], 1ull << t);
+    }
+    if (lane_id() == 0) {
+      part[u] = t;
+      atomic_add_i64(&bw[s], -(long long)c[u]);
+      atomic_add_i64(&bw[t], (long long)c[u]);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && na) atomicAdd(moved, (unsigned long long)na);
+}
+
+}  // namespace
+
+// ===================================================================== host
+
+void project_partition(const Ctx& cx, const Level& fine, const int32_t* coarse_part,
+                       int32_t* fine_part) {
+  if (fine.n == 0) return;
+  k_project<<<grid_for(fine.n, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(fine.map.p, coarse_part,
+                                                                        fine.n, fine_part);
+  check_launch("project");
+  if (cx.launches) *cx.launches += 1;
+}
+
+namespace {
+
+struct PinState {
+  DBuf<int32_t> phi;
+  DBuf<unsigned long long> lam;
+  DBuf<long long> bw;
+  DBuf<int32_t> tiles;
+};
+
+void build_pin_state(const Ctx& cx, const Level& L, int k, const int32_t* part, PinState& st) {
+  st.phi.alloc(&cx.alloc, (size_t)L.m * k + 1);
+  st.lam.alloc(&cx.alloc, (size_t)L.m + 1);
+  st.bw.alloc(&cx.alloc, (size_t)k);
+  HG_CUDA(cudaMemsetAsync(st.phi.p, 0, st.phi.bytes(), cx.stream));
+  HG_CUDA(cudaMemsetAsync(st.lam.p, 0, st.lam.bytes(), cx.stream));
+  HG_CUDA(cudaMemsetAsync(st.bw.p, 0, st.bw.bytes(), cx.stream));
+  if (L.p > 0) {
+    st.tiles.alloc(&cx.alloc, (size_t)num_pin_tiles(L.p) + 1);
+    build_tile_index(cx, L.eoff.p, L.m, L.p, st.tiles.p);
+    k_pin_counts<<<grid_for(num_pin_tiles(L.p), 1, cx.num_sms, 8), PIN_TILE_THREADS, 0,
+                   cx.stream>>>(L.eoff.p, L.pins.p, st.tiles.p, L.m, L.p, part, k, st.phi.p,
+                                st.lam.p);
+    check_launch("pin_counts");
+  }
+  k_block_weights<<<grid_for(L.n, 256, cx.num_sms, 4), 256, 0, cx.stream>>>(part, L.c.p, L.n, k,
+                                                                          st.bw.p);
+  check_launch("block_weights");
+  if (cx.launches) *cx.launches += 3;
+}
+
+int64_t objective_from_lambda(const Ctx& cx, const Level& L, const unsigned long long* lam) {
+  DBuf<unsigned long long> acc;
+  acc.alloc(&cx.alloc, 1);
+  HG_CUDA(cudaMemsetAsync(acc.p, 0, sizeof(unsigned long long), cx.stream));
+  if (L.m > 0) {
+    k_objective<<<grid_for(L.m, 256, cx.num_sms, 4), 256, 0, cx.stream>>>(lam, L.w.p, L.m, acc.p);
+    check_launch("objective");
+    if (cx.launches) *cx.launches += 1;
+  }
+  return read_i64(cx, reinterpret_cast<const int64_t*>(acc.p));
+}
+
+}  // namespace
+
+int64_t objective_of(const Ctx& cx, const Level& L, int k, const int32_t* part) {
+  PinState st;
+  build_pin_state(cx, L, k, part, st);
+  return objective_from_lambda(cx, L, st.lam.p);
+}
+
+void pin_counts_of(const Ctx& cx, const Level& L, int k, const int32_t* part, int32_t* phi,
+                   uint64_t* lambda, int64_t* bw) {
+  PinState st;
+  build_pin_state(cx, L, k, part, st);
+  if (phi && L.m)
+    HG_CUDA(cudaMemcpyAsync(phi, st.phi.p, sizeof(int32_t) * (size_t)L.m * k,
+                            cudaMemcpyDeviceToHost, cx.stream));
+  if (lambda && L.m)
+    HG_CUDA(cudaMemcpyAsync(lambda, st.lam.p, sizeof(uint64_t) * (size_t)L.m,
+                            cudaMemcpyDeviceToHost, cx.stream));
+  if (bw)
+    HG_CUDA(cudaMemcpyAsync(bw, st.bw.p, sizeof(int64_t) * (size_t)k, cudaMemcpyDeviceToHost,
+                            cx.stream));
+  check_status(cx);
+}
+
+LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, int eps_ppm,
+                         int max_passes, int S, uint64_t seed, int64_t total_node_weight,
+                         int32_t* part, RefineCounters& rc) {
+  LPResult res;
+  PinState st;
+  {
+    EventTimer tm(cx, &rc.ms_phi);
+    build_pin_state(cx, L, k, part, st);
+  }
+  const int64_t per_block = (total_node_weight + k - 1) / k;
+  const long long lmax = (long long)(per_block * (1000000 + (int64_t)eps_ppm) / 1000000);
+  const int kk = k * k;
+  const int32_t n = L.n;
+
+  DBuf<int32_t> list, sr_cnt, sr_fill, sr_off, mv_u, mv_to, bucket, ap_u, ap_from, ap_to, dcnt,
+      dfill, doff, words;
+  DBuf<long long> mv_g, gpre;
+  DBuf<unsigned long long> gkeys, counters;
+  const size_t ncap = (size_t)n + 1;
+  list.alloc(&cx.alloc, ncap);
+  sr_cnt.alloc(&cx.alloc, (size_t)S);
+  sr_fill.alloc(&cx.alloc, (size_t)S);
+  sr_off.alloc(&cx.alloc, (size_t)S + 1);
+  mv_u.alloc(&cx.alloc, ncap);
+  mv_to.alloc(&cx.alloc, ncap);
+  mv_g.alloc(&cx.alloc, ncap);
+  bucket.alloc(&cx.alloc, ncap);
+  ap_u.alloc(&cx.alloc, ncap);
+  ap_from.alloc(&cx.alloc, ncap);
+  ap_to.alloc(&cx.alloc, ncap);
+  gkeys.alloc(&cx.alloc, 2 * ncap + 2);
+  gpre.alloc(&cx.alloc, ncap + (size_t)kk + 2);
+  dcnt.alloc(&cx.alloc, (size_t)S * kk);
+  dfill.alloc(&cx.alloc, (size_t)S * kk);
+  doff.alloc(&cx.alloc, (size_t)kk + 1);
+  words.alloc(&cx.alloc, (size_t)S * SW_WORDS);
+  counters.alloc(&cx.alloc, 2);  // [0] moved in the pass, [1] incidences read
+
+  const int nodes_per_sr = (int)((n + S - 1) / S);
+  const int g_gain = grid_for(nodes_per_sr, WARPS, cx.num_sms, 16);
+  const int g_bucket = grid_for(nodes_per_sr, 256, cx.num_sms, 4);
+  const int g_sel = k * (k - 1) / 2;
+  const int g_nodes = grid_for(n, 256, cx.num_sms, 4);
+  KernelTimer gain_timer(cx);
+
+  for (int pass = 0; pass < max_passes; ++pass) {
+    HG_CUDA(cudaMemsetAsync(sr_cnt.p, 0, sr_cnt.bytes(), cx.stream));
+    HG_CUDA(cudaMemsetAsync(sr_fill.p, 0, sr_fill.bytes(), cx.stream));
+    HG_CUDA(cudaMemsetAsync(dcnt.p, 0, dcnt.bytes(), cx.stream));
+    HG_CUDA(cudaMemsetAsync(dfill.p, 0, dfill.bytes(), cx.stream));
+    HG_CUDA(cudaMemsetAsync(words.p, 0, words.bytes(), cx.stream));
+    HG_CUDA(cudaMemsetAsync(counters.p, 0, sizeof(unsigned long long), cx.stream));
+    {
+      EventTimer tm(cx, &rc.ms_gain);
+      k_lp_count<<<g_nodes, 256, S * sizeof(int32_t), cx.stream>>>(L.ioff.p, n, seed, level_index,
+                                                                  pass, S, sr_cnt.p);
+      check_launch("lp_count");
+      k_lp_scatter<<<g_nodes, 256, (S + 1) * sizeof(int32_t), cx.stream>>>(
+          L.ioff.p, n, seed, level_index, pass, S, sr_cnt.p, sr_fill.p, sr_off.p, list.p);
+      check_launch("lp_scatter");
+    }
+    for (int s = 0; s < S; ++s) {
+      int32_t* w_s = words.p + (size_t)s * SW_WORDS;
+      int32_t* dc_s = dcnt.p + (size_t)s * kk;
+      int32_t* df_s = dfill.p + (size_t)s * kk;
+      {
+        EventTimer tm(cx, &rc.ms_gain);
+        gain_timer.begin();
+        k_lp_gain<<<g_gain, WARPS * 32, 0, cx.stream>>>(
+            L.ioff.p, L.inets.p, L.w.p, st.phi.p, st.lam.p, part, k, list.p, sr_off.p, s, mv_u.p,
+            mv_to.p, mv_g.p, dc_s, w_s, counters.p + 1);
+        gain_timer.end();
+        check_launch("lp_gain");
+      }
+      {
+        EventTimer tm(cx, &rc.ms_select);
+        k_lp_bucket<<<g_bucket, 256, (kk + 1) * sizeof(int32_t), cx.stream>>>(
+            mv_u.p, mv_to.p, part, k, dc_s, df_s, doff.p, w_s, bucket.p);
+        check_launch("lp_bucket");
+        k_lp_select<<<g_sel, SEL_THREADS, 0, cx.stream>>>(
+            bucket.p, doff.p, dc_s, mv_u.p, mv_to.p, mv_g.p, L.c.p, st.bw.p, lmax, k, gkeys.p,
+            gpre.p, ap_u.p, ap_from.p, ap_to.p, w_s);
+        check_launch("lp_select");
+      }
+      {
+        EventTimer tm(cx, &rc.ms_apply);
+        k_lp_apply<<<g_gain, WARPS * 32, 0, cx.stream>>>(L.ioff.p, L.inets.p, L.c.p, k, ap_u.p,
+                                                         ap_from.p, ap_to.p, w_s, part, st.phi.p,
+                                                         st.lam.p, st.bw.p, counters.p);
+        check_launch("lp_apply");
+      }
+      rc.lp_gain_launches += 1;
+      if (cx.launches) *cx.launches += 4;
+    }
+    if (cx.launches) *cx.launches += 2;
+    unsigned long long hc[2];
+    HG_CUDA(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, cx.stream));
+    check_status(cx);
+    res.passes = pass + 1;
+    res.moves += (int64_t)hc[0];
+    rc.lp_incidences += (int64_t)hc[1];
+    HG_CUDA(cudaMemsetAsync(counters.p + 1, 0, sizeof(unsigned long long), cx.stream));
+    if (hc[0] == 0) break;
+  }
+  rc.ms_gain_kernels += gain_timer.flush();
+  rc.lp_nodes += (int64_t)res.passes * n;
+  {
+    EventTimer tm(cx, &rc.ms_objective);
+    res.objective = objective_from_lambda(cx, L, st.lam.p);
+  }
+  return res;
+}
+
+}  // namespace hgk

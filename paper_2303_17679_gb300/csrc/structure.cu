@@ -1,0 +1,154 @@
+// Hypergraph structure on the device: the pin-tile index, the incident-net
+// lists I(u) (the second adjacency array of Sec. 4.2, "The Contraction
+// Algorithm"), and validation of caller-provided device arrays.
+#include "common.cuh"
+#include "pintile.cuh"
+
+namespace hgk {
+
+namespace {
+
+// tile_net[t] = net containing pin position t * PIN_TILE.
+__global__ void k_tile_index(const int32_t* __restrict__ eoff, int32_t m, int64_t ntiles,
+                             int32_t* __restrict__ tile_net) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = eoff[e], b = eoff[e + 1];
+    if (b <= a) continue;
+    for (int64_t t = (a + PIN_TILE - 1) / PIN_TILE; t * PIN_TILE < b && t < ntiles; ++t)
+      tile_net[t] = (int32_t)e;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) tile_net[ntiles] = m > 0 ? m - 1 : 0;
+}
+
+__global__ void k_degrees(const int32_t* __restrict__ pins, int64_t p, int32_t* __restrict__ deg) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < p;
+       q += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&deg[pins[q]], 1);
+}
+
+// Scatter every pin (e, v) into I(v) at a slot taken from v's cursor.
+__global__ void __launch_bounds__(PIN_TILE_THREADS)
+k_scatter_incidence(const int32_t* __restrict__ eoff, const int32_t* __restrict__ pins,
+                    const int32_t* __restrict__ tile_net, int32_t m, int64_t p,
+                    int32_t* __restrict__ cursor, int32_t* __restrict__ inets) {
+  __shared__ int32_t s_off[PIN_TILE + 3];
+  const int64_t ntiles = num_pin_tiles(p);
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    PinTileView v = stage_pin_tile(eoff, tile_net, m, p, t, s_off);
+    for (int64_t q = v.q0 + threadIdx.x; q < v.q1; q += blockDim.x) {
+      const int32_t e = v.e_lo + net_in_tile(s_off, v.count, q);
+      const int32_t u = pins[q];
+      const int32_t slot = atomicAdd(&cursor[u], 1);
+      inets[slot] = e;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_validate_nets(const int32_t* __restrict__ eoff, int32_t m,
+                                const int32_t* __restrict__ w, int32_t* status,
+                                unsigned long long* total_w) {
+  int64_t local = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (eoff[e + 1] <= eoff[e]) dev_fail(status, DEV_BAD_INPUT);
+    const int32_t x = w ? w[e] : 1;
+    if (x <= 0) dev_fail(status, DEV_BAD_INPUT);
+    local += x;
+  }
+  local = warp_sum(local);
+  if (lane_id() == 0 && local) atomicAdd(total_w, (unsigned long long)local);
+}
+
+__global__ void k_validate_pins(const int32_t* __restrict__ pins, int64_t p, int32_t n,
+                                int32_t* status) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < p;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = pins[q];
+    if (v < 0 || v >= n) dev_fail(status, DEV_BAD_INPUT);
+  }
+}
+
+__global__ void k_validate_nodes(const int32_t* __restrict__ c, int32_t n, int32_t* status,
+                                 unsigned long long* total_c) {
+  int64_t local = 0;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t x = c ? c[u] : 1;
+    if (x <= 0) dev_fail(status, DEV_BAD_INPUT);
+    local += x;
+  }
+  local = warp_sum(local);
+  if (lane_id() == 0 && local) atomicAdd(total_c, (unsigned long long)local);
+}
+
+}  // namespace
+
+void build_tile_index(const Ctx& cx, const int32_t* eoff, int32_t m, int64_t p, int32_t* tile_net) {
+  const int64_t ntiles = num_pin_tiles(p);
+  k_tile_index<<<grid_for(m > 0 ? m : 1, 256, cx.num_sms, 16), 256, 0, cx.stream>>>(eoff, m, ntiles,
+                                                                                  tile_net);
+  check_launch("tile_index");
+  if (cx.launches) *cx.launches += 1;
+}
+
+void build_incidence(const Ctx& cx, Level& L) {
+  L.ioff.alloc(&cx.alloc, (size_t)L.n + 1);
+  L.inets.alloc(&cx.alloc, (size_t)(L.p > 0 ? L.p : 1));
+  HG_CUDA(cudaMemsetAsync(L.ioff.p, 0, sizeof(int32_t) * ((size_t)L.n + 1), cx.stream));
+  if (L.p > 0) {
+    k_degrees<<<grid_for(L.p, 256, cx.num_sms, 16), 256, 0, cx.stream>>>(L.pins.p, L.p, L.ioff.p);
+    check_launch("degrees");
+  }
+  scan_exclusive_i32(cx, L.ioff.p, L.ioff.p, L.n, L.ioff.p + L.n);
+  if (L.p > 0) {
+    DBuf<int32_t> cursor, tiles;
+    cursor.alloc(&cx.alloc, (size_t)L.n);
+    HG_CUDA(cudaMemcpyAsync(cursor.p, L.ioff.p, sizeof(int32_t) * (size_t)L.n,
+                            cudaMemcpyDeviceToDevice, cx.stream));
+    tiles.alloc(&cx.alloc, (size_t)num_pin_tiles(L.p) + 1);
+    build_tile_index(cx, L.eoff.p, L.m, L.p, tiles.p);
+    k_scatter_incidence<<<grid_for(num_pin_tiles(L.p), 1, cx.num_sms, 8), PIN_TILE_THREADS, 0,
+                          cx.stream>>>(L.eoff.p, L.pins.p, tiles.p, L.m, L.p, cursor.p,
+                                       L.inets.p);
+    check_launch("scatter_incidence");
+    if (cx.launches) *cx.launches += 2;
+  }
+  if (cx.launches) *cx.launches += 1;
+}
+
+bool validate_level_device(const Ctx& cx, const Level& L, int64_t* total_node_w,
+                           int64_t* total_net_w) {
+  DBuf<unsigned long long> sums;
+  sums.alloc(&cx.alloc, 2);
+  HG_CUDA(cudaMemsetAsync(sums.p, 0, 2 * sizeof(unsigned long long), cx.stream));
+  if (L.m > 0) {
+    k_validate_nets<<<grid_for(L.m, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(
+        L.eoff.p, L.m, L.w.p, cx.d_status, sums.p + 1);
+    check_launch("validate_nets");
+  }
+  if (L.p > 0) {
+    k_validate_pins<<<grid_for(L.p, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(L.pins.p, L.p, L.n,
+                                                                             cx.d_status);
+    check_launch("validate_pins");
+  }
+  k_validate_nodes<<<grid_for(L.n, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(L.c.p, L.n,
+                                                                           cx.d_status, sums.p);
+  check_launch("validate_nodes");
+  unsigned long long h[2] = {0, 0};
+  HG_CUDA(cudaMemcpyAsync(h, sums.p, sizeof(h), cudaMemcpyDeviceToHost, cx.stream));
+  int32_t st = 0;
+  HG_CUDA(cudaMemcpyAsync(&st, cx.d_status, sizeof(st), cudaMemcpyDeviceToHost, cx.stream));
+  HG_CUDA(cudaStreamSynchronize(cx.stream));
+  if (st != DEV_OK) {
+    int32_t zero = 0;
+    HG_CUDA(cudaMemcpy(cx.d_status, &zero, sizeof(zero), cudaMemcpyHostToDevice));
+    return false;
+  }
+  *total_node_w = (int64_t)h[0];
+  *total_net_w = (int64_t)h[1];
+  return true;
+}
+
+}  // namespace hgk

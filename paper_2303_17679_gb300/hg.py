@@ -1,0 +1,306 @@
+"""Thin Python binding of the C ABI in include/hg.h.
+
+Every function has the name of the C entry point it calls and only marshals
+arguments: host arrays are numpy arrays, device arrays are CUDA tensors (or
+raw device pointers), streams are torch streams (or raw cudaStream_t
+values).  All computation happens in libhg.so; if the library cannot be
+loaded, every call raises - there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhg.so")
+
+HG_OK = 0
+HG_STOP = 1
+HG_ERR_INVALID = -1
+HG_ERR_UNSUPPORTED = -2
+HG_ERR_OOM = -3
+HG_ERR_CUDA = -4
+HG_ERR_TIMEOUT = -5
+HG_ERR_STATE = -6
+HG_MEM_HOST = 0
+HG_MEM_DEVICE = 1
+HG_MAX_K = 64
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class hg_options(ctypes.Structure):
+    _fields_ = [
+        ("seed", ctypes.c_uint64),
+        ("subrounds", ctypes.c_int32),
+        ("rating_max_net_size", ctypes.c_int32),
+        ("contraction_limit_factor", ctypes.c_int32),
+        ("fingerprint_bits", ctypes.c_int32),
+        ("dev_alloc", ALLOC_FN),
+        ("dev_free", FREE_FN),
+        ("alloc_ctx", ctypes.c_void_p),
+    ]
+
+
+class hg_stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_double) for name in (
+        "ms_transpose", "ms_rating", "ms_approve", "ms_contract", "ms_project", "ms_phi",
+        "ms_lp_gain", "ms_lp_select", "ms_lp_apply", "ms_objective", "ms_initial")] + [
+        (name, ctypes.c_int64) for name in (
+            "launches", "rating_launches", "rating_pin_visits", "rating_nodes",
+            "rating_incidences", "lp_incidences", "lp_nodes", "lp_gain_launches")] + [
+        ("ms_rating_kernels", ctypes.c_double), ("ms_lp_gain_kernels", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class HgError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {hg_strerror(status)} ({status})")
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None):
+    """Loads libhg.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libhg.so not found at {p}: build it first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        lib = ctypes.CDLL(p)
+        i32, i64, vp, P = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER
+        H = ctypes.c_void_p
+        sig = {
+            "hg_default_options": (None, [P(hg_options)]),
+            "hg_create": (ctypes.c_int, [i32, i32, vp, vp, vp, vp, i32, P(hg_options), vp, P(H)]),
+            "hg_coarsen_level": (ctypes.c_int, [H, i32, P(i32), P(i32), P(i32), P(i64)]),
+            "hg_num_levels": (ctypes.c_int, [H, P(i32)]),
+            "hg_level_info": (ctypes.c_int, [H, i32, P(i32), P(i32), P(i64)]),
+            "hg_initial_partition": (ctypes.c_int, [H, i32, i32, vp]),
+            "hg_project": (ctypes.c_int, [H, i32, vp, vp]),
+            "hg_lp_refine": (ctypes.c_int, [H, i32, i32, i32, i32, vp, P(i64), P(i64)]),
+            "hg_objective": (ctypes.c_int, [H, i32, i32, vp, P(i64)]),
+            "hg_pin_counts": (ctypes.c_int, [H, i32, i32, vp, vp, vp, vp]),
+            "hg_partition": (ctypes.c_int, [H, i32, i32, i32, vp, P(i64)]),
+            "hg_get_level": (ctypes.c_int, [H, i32, vp, vp, vp, vp, vp, vp]),
+            "hg_get_incidence": (ctypes.c_int, [H, i32, vp, vp]),
+            "hg_truncate": (ctypes.c_int, [H, i32]),
+            "hg_enable_timing": (ctypes.c_int, [H, i32]),
+            "hg_get_stats": (ctypes.c_int, [H, P(hg_stats)]),
+            "hg_reset_stats": (ctypes.c_int, [H]),
+            "hg_destroy": (ctypes.c_int, [H]),
+            "hg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+            "hg_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def exported_symbols():
+    """Names of the C entry points this binding expects the library to export."""
+    return ["hg_default_options", "hg_create", "hg_coarsen_level", "hg_num_levels",
+            "hg_level_info", "hg_initial_partition", "hg_project", "hg_lp_refine",
+            "hg_objective", "hg_pin_counts", "hg_partition", "hg_get_level", "hg_get_incidence",
+            "hg_truncate", "hg_enable_timing", "hg_get_stats", "hg_reset_stats", "hg_destroy",
+            "hg_strerror", "hg_version"]
+
+
+# ------------------------------------------------------------------ helpers
+
+def _ptr(x):
+    """Device or host address of a torch tensor, numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    if isinstance(x, np.ndarray):
+        return ctypes.c_void_p(x.ctypes.data)
+    return ctypes.c_void_p(x.data_ptr())  # torch tensor
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return ctypes.c_void_p(s)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(rc: int, where: str, allow=(HG_OK,)):
+    if rc not in allow:
+        raise HgError(rc, where)
+    return rc
+
+
+def hg_strerror(status: int) -> str:
+    return load().hg_strerror(status).decode()
+
+
+def hg_version() -> str:
+    return load().hg_version().decode()
+
+
+def hg_default_options() -> hg_options:
+    o = hg_options()
+    load().hg_default_options(ctypes.byref(o))
+    return o
+
+
+class TorchAllocator:
+    """Device allocation hooks backed by PyTorch's caching allocator."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        self._torch = torch
+        self._device = device
+        self._alloc = ALLOC_FN(self._do_alloc)
+        self._free = FREE_FN(self._do_free)
+
+    def _do_alloc(self, size, _ctx):
+        stream = self._torch.cuda.current_stream(self._device)
+        return self._torch.cuda.caching_allocator_alloc(int(size), self._device, stream)
+
+    def _do_free(self, ptr, _ctx):
+        self._torch.cuda.caching_allocator_delete(int(ptr))
+
+    def install(self, opt: hg_options):
+        opt.dev_alloc = self._alloc
+        opt.dev_free = self._free
+
+
+# ------------------------------------------------------------------ entry points
+
+def hg_create(n, m, net_offsets, pins, net_weights=None, node_weights=None, mem=HG_MEM_HOST,
+              opt: hg_options | None = None, stream=None):
+    """Returns an opaque handle (ctypes.c_void_p)."""
+    h = ctypes.c_void_p()
+    rc = load().hg_create(int(n), int(m), _ptr(net_offsets), _ptr(pins), _ptr(net_weights),
+                          _ptr(node_weights), int(mem), ctypes.byref(opt) if opt else None,
+                          _stream(stream), ctypes.byref(h))
+    _check(rc, "hg_create")
+    return h
+
+
+def hg_coarsen_level(h, k):
+    """Returns (status, level, n, m, p); status is HG_OK or HG_STOP."""
+    lv, n, m, p = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    rc = load().hg_coarsen_level(h, int(k), ctypes.byref(lv), ctypes.byref(n), ctypes.byref(m),
+                                 ctypes.byref(p))
+    _check(rc, "hg_coarsen_level", (HG_OK, HG_STOP))
+    return rc, lv.value, n.value, m.value, p.value
+
+
+def hg_num_levels(h) -> int:
+    x = ctypes.c_int32()
+    _check(load().hg_num_levels(h, ctypes.byref(x)), "hg_num_levels")
+    return x.value
+
+
+def hg_level_info(h, level):
+    n, m, p = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(load().hg_level_info(h, int(level), ctypes.byref(n), ctypes.byref(m), ctypes.byref(p)),
+           "hg_level_info")
+    return n.value, m.value, p.value
+
+
+def hg_initial_partition(h, level, k, part):
+    _check(load().hg_initial_partition(h, int(level), int(k), _ptr(part)), "hg_initial_partition")
+
+
+def hg_project(h, coarse_level, coarse_part, fine_part):
+    _check(load().hg_project(h, int(coarse_level), _ptr(coarse_part), _ptr(fine_part)), "hg_project")
+
+
+def hg_lp_refine(h, level, k, eps_ppm, max_passes, part):
+    """Returns (objective, moves)."""
+    obj, mv = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().hg_lp_refine(h, int(level), int(k), int(eps_ppm), int(max_passes), _ptr(part),
+                               ctypes.byref(obj), ctypes.byref(mv)), "hg_lp_refine")
+    return obj.value, mv.value
+
+
+def hg_objective(h, level, k, part) -> int:
+    obj = ctypes.c_int64()
+    _check(load().hg_objective(h, int(level), int(k), _ptr(part), ctypes.byref(obj)), "hg_objective")
+    return obj.value
+
+
+def hg_pin_counts(h, level, k, part):
+    """Returns (phi [m, k] int32, lambda [m] uint64, block weights [k] int64) on the host."""
+    n, m, _ = hg_level_info(h, level)
+    phi = np.zeros((max(m, 1), k), np.int32)
+    lam = np.zeros(max(m, 1), np.uint64)
+    bw = np.zeros(k, np.int64)
+    _check(load().hg_pin_counts(h, int(level), int(k), _ptr(part), _ptr(phi), _ptr(lam), _ptr(bw)),
+           "hg_pin_counts")
+    return phi[:m], lam[:m], bw
+
+
+def hg_partition(h, k, eps_ppm, max_passes, part) -> int:
+    obj = ctypes.c_int64()
+    _check(load().hg_partition(h, int(k), int(eps_ppm), int(max_passes), _ptr(part),
+                               ctypes.byref(obj)), "hg_partition")
+    return obj.value
+
+
+def hg_get_level(h, level, with_map=False):
+    """Returns dict(offsets, pins, net_w, node_w[, map, rep]) as numpy arrays."""
+    n, m, p = hg_level_info(h, level)
+    out = dict(offsets=np.zeros(m + 1, np.int32), pins=np.zeros(max(p, 1), np.int32),
+               net_w=np.zeros(max(m, 1), np.int32), node_w=np.zeros(max(n, 1), np.int32))
+    mp = np.zeros(max(n, 1), np.int32) if with_map else None
+    rp = np.zeros(max(n, 1), np.int32) if with_map else None
+    _check(load().hg_get_level(h, int(level), _ptr(out["offsets"]), _ptr(out["pins"]),
+                               _ptr(out["net_w"]), _ptr(out["node_w"]), _ptr(mp), _ptr(rp)),
+           "hg_get_level")
+    out["pins"], out["net_w"], out["node_w"] = out["pins"][:p], out["net_w"][:m], out["node_w"][:n]
+    if with_map:
+        out["map"], out["rep"] = mp[:n], rp[:n]
+    return out
+
+
+def hg_get_incidence(h, level):
+    n, m, p = hg_level_info(h, level)
+    off = np.zeros(n + 1, np.int32)
+    nets = np.zeros(max(p, 1), np.int32)
+    _check(load().hg_get_incidence(h, int(level), _ptr(off), _ptr(nets)), "hg_get_incidence")
+    return off, nets[:p]
+
+
+def hg_truncate(h, level):
+    _check(load().hg_truncate(h, int(level)), "hg_truncate")
+
+
+def hg_enable_timing(h, on=True):
+    _check(load().hg_enable_timing(h, 1 if on else 0), "hg_enable_timing")
+
+
+def hg_get_stats(h) -> dict:
+    s = hg_stats()
+    _check(load().hg_get_stats(h, ctypes.byref(s)), "hg_get_stats")
+    return s.as_dict()
+
+
+def hg_reset_stats(h):
+    _check(load().hg_reset_stats(h), "hg_reset_stats")
+
+
+def hg_destroy(h):
+    if h:
+        load().hg_destroy(h)

@@ -1,0 +1,97 @@
+"""The C-ABI library loads without a GPU, exports every entry point that
+include/hg.h declares, and rejects malformed host inputs before touching the
+device (no compute call is made here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2303_17679_gb300 import build, hg
+    build.build()
+    return hg.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "hg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hg_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("hg_create", "hg_coarsen_level", "hg_lp_refine", "hg_objective", "hg_project",
+                     "hg_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2303_17679_gb300 import hg
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert sorted(hg.exported_symbols()) == declared_functions()
+
+
+def test_strerror_and_version(lib):
+    from paper_2303_17679_gb300 import hg
+    assert hg.hg_strerror(hg.HG_ERR_INVALID) == "invalid argument"
+    assert "sm_103a" in hg.hg_version()
+
+
+def _create(lib, n, m, off, pins, w=None, c=None):
+    from paper_2303_17679_gb300 import hg
+    h = ctypes.c_void_p()
+    arr = lambda a: None if a is None else np.ascontiguousarray(a, np.int32)
+    off, pins, w, c = arr(off), arr(pins), arr(w), arr(c)
+    p = lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data)
+    rc = lib.hg_create(n, m, p(off), p(pins), p(w), p(c), hg.HG_MEM_HOST, None, None,
+                       ctypes.byref(h))
+    return rc, h
+
+
+@pytest.mark.parametrize("case", [
+    dict(n=3, m=1, off=[0, 0], pins=[]),                       # empty net
+    dict(n=3, m=1, off=[0, 2], pins=[0, 3]),                   # pin out of range
+    dict(n=3, m=1, off=[0, 3], pins=[0, 1, 1]),                # repeated pin
+    dict(n=3, m=1, off=[1, 3], pins=[0, 1, 2]),                # offsets not starting at 0
+    dict(n=3, m=2, off=[0, 2, 1], pins=[0, 1, 2]),             # decreasing offsets
+    dict(n=3, m=1, off=[0, 2], pins=[0, 1], w=[0]),            # zero net weight
+    dict(n=3, m=1, off=[0, 2], pins=[0, 1], c=[1, -1, 1]),     # negative node weight
+    dict(n=2, m=1, off=[0, 2], pins=[0, 1], c=[2 ** 30, 2 ** 30]),  # total weight >= 2^31
+    dict(n=0, m=0, off=[0], pins=[]),                          # no nodes
+])
+def test_malformed_host_input_rejected(lib, case):
+    from paper_2303_17679_gb300 import hg
+    rc, h = _create(lib, case["n"], case["m"], case["off"], case["pins"], case.get("w"),
+                    case.get("c"))
+    assert rc == hg.HG_ERR_INVALID
+    assert not h.value
+
+
+def test_bad_options_rejected(lib):
+    from paper_2303_17679_gb300 import hg
+    o = hg.hg_default_options()
+    assert (o.seed, o.subrounds, o.rating_max_net_size, o.contraction_limit_factor) == (1, 16, 1000, 160)
+    for field, value in (("subrounds", 0), ("subrounds", 257), ("rating_max_net_size", 1),
+                         ("contraction_limit_factor", 0), ("fingerprint_bits", 65)):
+        bad = hg.hg_default_options()
+        setattr(bad, field, value)
+        h = ctypes.c_void_p()
+        off = np.array([0, 2], np.int32)
+        pins = np.array([0, 1], np.int32)
+        rc = lib.hg_create(2, 1, ctypes.c_void_p(off.ctypes.data), ctypes.c_void_p(pins.ctypes.data),
+                           None, None, hg.HG_MEM_HOST, ctypes.byref(bad), None, ctypes.byref(h))
+        assert rc == hg.HG_ERR_INVALID
+
+
+def test_null_handle_calls_are_rejected(lib):
+    from paper_2303_17679_gb300 import hg
+    assert lib.hg_destroy(None) == hg.HG_OK
+    assert lib.hg_lp_refine(None, 0, 2, 0, 1, None, None, None) == hg.HG_ERR_INVALID
+    assert lib.hg_objective(None, 0, 2, None, None) == hg.HG_ERR_INVALID

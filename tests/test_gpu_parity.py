@@ -1,0 +1,272 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the CPU
+oracle on the same seeded inputs.  All arithmetic is integer, so every
+comparison is exact (bit-identical arrays and objectives)."""
+import numpy as np
+import pytest
+
+import synth
+from tests.tiny import from_nets
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2303_17679_gb300 import hg  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def make_opt(seed=1, S=16, T=1000, factor=160, fp_bits=0):
+    o = hg.hg_default_options()
+    o.seed, o.subrounds, o.rating_max_net_size = seed, S, T
+    o.contraction_limit_factor, o.fingerprint_bits = factor, fp_bits
+    return o
+
+
+def create(hgr, opt, device_input=False):
+    stream = torch.cuda.current_stream()
+    if device_input:
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).cuda()
+        off, pins, w, c = t(hgr.offsets), t(hgr.pins), t(hgr.net_w), t(hgr.node_w)
+        h = hg.hg_create(hgr.n, hgr.m, off, pins, w, c, hg.HG_MEM_DEVICE, opt, stream)
+        torch.cuda.synchronize()
+        return h
+    return hg.hg_create(hgr.n, hgr.m, hgr.offsets, hgr.pins, hgr.net_w, hgr.node_w,
+                        hg.HG_MEM_HOST, opt, stream)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.int32)).cuda()
+
+
+# ---------------------------------------------------------------- inputs
+
+def tiny_cases():
+    out = {}
+    out["single_net"] = from_nets(6, [[0, 1, 2, 3, 4, 5]], [3])
+    out["isolated"] = from_nets(12, [[0, 1], [1, 2], [2, 3], [5, 6, 7]], [1, 2, 3, 4])
+    out["identical"] = from_nets(10, [[0, 1, 2], [2, 1, 0], [3, 4], [4, 3], [0, 1, 2], [5, 6, 7, 8]],
+                                 [1, 2, 3, 4, 5, 6])
+    out["heavy_node"] = from_nets(8, [[i, (i + 1) % 8] for i in range(8)], None,
+                                  [40, 1, 1, 1, 1, 1, 1, 1])
+    return out
+
+
+def medium_cases():
+    return {
+        "cfg1": synth.config1(1),
+        "zipf20k": synth.config2(3, n=20_000),
+        "stress": synth.large_net_stress(4, 40_000, 20_000, big_lo=300, big_hi=9000,
+                                         force_first=9000),
+        "weighted": synth.random_uniform(5, 5000, 8000, node_w=(1, 50), net_w=(1, 1000)),
+    }
+
+
+# ---------------------------------------------------------------- structure
+
+@pytest.mark.parametrize("name", ["cfg1", "stress"])
+@pytest.mark.parametrize("device_input", [False, True])
+def test_incidence_is_the_transpose(name, device_input):
+    hgr = medium_cases()[name]
+    h = create(hgr, make_opt(), device_input)
+    try:
+        off, nets = hg.hg_get_incidence(h, 0)
+    finally:
+        hg.hg_destroy(h)
+    # independent transpose by numpy: stable argsort of the pins
+    net_of_pin = np.repeat(np.arange(hgr.m, dtype=np.int32), np.diff(hgr.offsets))
+    order = np.argsort(hgr.pins, kind="stable")
+    ref_off = np.zeros(hgr.n + 1, np.int64)
+    np.add.at(ref_off, hgr.pins.astype(np.int64) + 1, 1)
+    ref_off = np.cumsum(ref_off)
+    assert np.array_equal(off, ref_off)
+    ref_nets = net_of_pin[order]
+    for u in np.random.default_rng(0).choice(hgr.n, 500):
+        a, b = off[u], off[u + 1]
+        assert np.array_equal(np.sort(nets[a:b]), ref_nets[a:b])
+
+
+@pytest.mark.parametrize("k", [2, 7, 64])
+def test_objective_and_pin_counts(oracle_mod, k):
+    hgr = medium_cases()["zipf20k"]
+    h = create(hgr, make_opt())
+    try:
+        rng = np.random.default_rng(k)
+        for _ in range(3):
+            part = rng.integers(0, k, size=hgr.n).astype(np.int32)
+            dpart = dev(part)
+            assert hg.hg_objective(h, 0, k, dpart) == oracle_mod.objective(hgr, k, part)
+            phi, lam, bw = hg.hg_pin_counts(h, 0, k, dpart)
+            rphi, rlam = oracle_mod.pin_counts(hgr, k, part)
+            assert np.array_equal(phi, rphi) and np.array_equal(lam, rlam)
+            assert np.array_equal(bw, oracle_mod.block_weights(hgr, k, part))
+    finally:
+        hg.hg_destroy(h)
+
+
+# ---------------------------------------------------------------- coarsening
+
+def compare_level(h, level, ref_level):
+    got = hg.hg_get_level(h, level)
+    assert np.array_equal(got["offsets"], ref_level.offsets)
+    assert np.array_equal(got["pins"], ref_level.pins)
+    assert np.array_equal(got["net_w"], ref_level.net_w)
+    assert np.array_equal(got["node_w"], ref_level.node_w)
+
+
+def check_one_level(oracle_mod, hgr, k, opt, level=0):
+    W = int(hgr.node_w.sum())
+    ref = oracle_mod.coarsen(hgr, W, k, S=opt.subrounds, T=opt.rating_max_net_size,
+                             factor=opt.contraction_limit_factor, seed=opt.seed, level=level)
+    h = create(hgr, opt)
+    try:
+        rc, lv, n2, m2, p2 = hg.hg_coarsen_level(h, k)
+        if ref is None:
+            assert rc == hg.HG_STOP
+            return
+        assert rc == hg.HG_OK and lv == 1
+        got = hg.hg_get_level(h, 0, with_map=True)
+        assert np.array_equal(got["rep"], ref["rep"])
+        assert np.array_equal(got["map"], ref["map"])
+        assert (n2, m2, p2) == (ref["level"].n, ref["level"].m, ref["level"].p)
+        compare_level(h, 1, ref["level"])
+    finally:
+        hg.hg_destroy(h)
+
+
+@pytest.mark.parametrize("name", ["cfg1", "zipf20k", "stress", "weighted"])
+def test_coarsen_level_parity(oracle_mod, name):
+    hgr = medium_cases()[name]
+    k = {"cfg1": 2, "zipf20k": 8, "stress": 64, "weighted": 4}[name]
+    factor = {"cfg1": 160, "zipf20k": 20, "stress": 4, "weighted": 40}[name]
+    check_one_level(oracle_mod, hgr, k, make_opt(seed=3, factor=factor))
+
+
+@pytest.mark.parametrize("name", ["single_net", "isolated", "identical", "heavy_node"])
+def test_coarsen_tiny_cases(oracle_mod, name):
+    hgr = tiny_cases()[name]
+    check_one_level(oracle_mod, hgr, 1, make_opt(seed=5, S=2, factor=1))
+
+
+def test_coarsen_small_threshold_and_subrounds(oracle_mod):
+    hgr = synth.config2(8, n=6000)
+    check_one_level(oracle_mod, hgr, 2, make_opt(seed=8, S=3, T=8, factor=10))
+
+
+def test_fingerprint_collisions_resolved(oracle_mod):
+    # 3-bit fingerprints: almost every coarse net collides with others of its
+    # group; the exact comparison rounds must still give the oracle's nets
+    hgr = synth.random_uniform(9, 3000, 6000, cap=6)
+    check_one_level(oracle_mod, hgr, 2, make_opt(seed=9, factor=5, fp_bits=3))
+
+
+def test_hierarchy_parity(oracle_mod):
+    hgr = synth.config2(11, n=30_000)
+    k, factor = 8, 10
+    opt = make_opt(seed=11, factor=factor)
+    vc = oracle_mod.multilevel(hgr, k, seed=11, factor=factor, max_passes=0)
+    h = create(hgr, opt)
+    try:
+        while hg.hg_coarsen_level(h, k)[0] == hg.HG_OK:
+            pass
+        assert hg.hg_num_levels(h) == len(vc.levels)
+        for lv in range(1, len(vc.levels)):
+            compare_level(h, lv, vc.levels[lv])
+            got = hg.hg_get_level(h, lv - 1, with_map=True)
+            assert np.array_equal(got["map"], vc.maps[lv - 1])
+    finally:
+        hg.hg_destroy(h)
+
+
+# ---------------------------------------------------------------- refinement
+
+def test_initial_partition_and_projection(oracle_mod):
+    hgr = synth.config2(12, n=8000)
+    k = 8
+    h = create(hgr, make_opt(seed=12, factor=10))
+    try:
+        hg.hg_coarsen_level(h, k)
+        n1 = hg.hg_level_info(h, 1)[0]
+        cpart = torch.empty(n1, dtype=torch.int32, device="cuda")
+        hg.hg_initial_partition(h, 1, k, cpart)
+        lvl1 = hg.hg_get_level(h, 1)
+        ref = oracle_mod.initial_partition(lvl1["node_w"], k, 12)
+        assert np.array_equal(cpart.cpu().numpy(), ref)
+        fpart = torch.empty(hgr.n, dtype=torch.int32, device="cuda")
+        hg.hg_project(h, 1, cpart, fpart)
+        mp = hg.hg_get_level(h, 0, with_map=True)["map"]
+        assert np.array_equal(fpart.cpu().numpy(), oracle_mod.project(mp, ref))
+    finally:
+        hg.hg_destroy(h)
+
+
+@pytest.mark.parametrize("k,passes,name", [(2, 5, "cfg1"), (8, 3, "zipf20k"), (64, 2, "stress"),
+                                           (4, 5, "weighted"), (3, 1, "cfg1")])
+def test_lp_parity(oracle_mod, k, passes, name):
+    hgr = medium_cases()[name]
+    seed = 21
+    part0 = oracle_mod.initial_partition(hgr.node_w, k, seed)
+    ref = oracle_mod.lp_refine(hgr, k, part0, 30000, 16, seed, 0, passes)
+    h = create(hgr, make_opt(seed=seed))
+    try:
+        dpart = dev(part0)
+        obj, moves = hg.hg_lp_refine(h, 0, k, 30000, passes, dpart)
+        got = dpart.cpu().numpy()
+    finally:
+        hg.hg_destroy(h)
+    assert moves == ref["moves"]
+    assert np.array_equal(got, ref["part"])
+    assert obj == ref["objective"]
+
+
+def test_lp_large_slack_and_tight_balance(oracle_mod):
+    hgr = synth.random_uniform(22, 4000, 4000, node_w=(1, 9))
+    for eps in (0, 1_000_000):
+        part0 = oracle_mod.initial_partition(hgr.node_w, 2, 22)
+        ref = oracle_mod.lp_refine(hgr, 2, part0, eps, 16, 22, 0, 4)
+        h = create(hgr, make_opt(seed=22))
+        try:
+            dpart = dev(part0)
+            obj, moves = hg.hg_lp_refine(h, 0, 2, eps, 4, dpart)
+            assert np.array_equal(dpart.cpu().numpy(), ref["part"])
+            assert (obj, moves) == (ref["objective"], ref["moves"])
+        finally:
+            hg.hg_destroy(h)
+
+
+@pytest.mark.parametrize("name,k,factor", [("cfg1", 2, 160), ("zipf20k", 8, 10)])
+def test_partition_vcycle_parity(oracle_mod, name, k, factor):
+    hgr = medium_cases()[name]
+    seed = 31
+    vc = oracle_mod.multilevel(hgr, k, 30000, S=16, T=1000, factor=factor, seed=seed, max_passes=5)
+    h = create(hgr, make_opt(seed=seed, factor=factor))
+    try:
+        part = torch.empty(hgr.n, dtype=torch.int32, device="cuda")
+        obj = hg.hg_partition(h, k, 30000, 5, part)
+        assert hg.hg_num_levels(h) == len(vc.levels)
+        assert np.array_equal(part.cpu().numpy(), vc.parts[0])
+        assert obj == vc.objectives[0]
+    finally:
+        hg.hg_destroy(h)
+
+
+def test_repeated_runs_identical():
+    hgr = synth.config2(41, n=50_000)
+    results = []
+    for _ in range(2):
+        h = create(hgr, make_opt(seed=41, factor=10))
+        try:
+            part = torch.empty(hgr.n, dtype=torch.int32, device="cuda")
+            obj = hg.hg_partition(h, 8, 30000, 5, part)
+            results.append((obj, part.cpu().numpy(), hg.hg_get_level(h, 1)["pins"]))
+        finally:
+            hg.hg_destroy(h)
+    assert results[0][0] == results[1][0]
+    assert np.array_equal(results[0][1], results[1][1])
+    assert np.array_equal(results[0][2], results[1][2])
