@@ -192,15 +192,15 @@ def run_ours(args, world, rank, local):
     part = torch.empty(hgr.n, dtype=torch.int32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
 
-    def step(kernel_events=False, host_inputs=False):
+    def step(kernel_events=False, host_inputs=False, phases=False):
         if host_inputs:
             h = hg.hg_create(hgr.n, hgr.m, h_off.numpy(), h_pins.numpy(), h_w.numpy(), h_c.numpy(),
                              hg.HG_MEM_HOST, opt, stream)
         else:
             h = hg.hg_create(hgr.n, hgr.m, d_off, d_pins, d_w, d_c, hg.HG_MEM_DEVICE, opt, stream)
         try:
-            if kernel_events:
-                hg.hg_enable_timing(h, 2)
+            if kernel_events or phases:
+                hg.hg_enable_timing(h, (2 if kernel_events else 0) | (1 if phases else 0))
             obj = hg.hg_partition(h, K_BLOCKS, EPS_PPM, PASSES, part)
             nl = hg.hg_num_levels(h)
             levels = [hg.hg_level_info(h, i) for i in range(nl)]
@@ -249,7 +249,7 @@ def run_ours(args, world, rank, local):
 
     # ---- end to end through the public API with host buffers
     e2e_ms = []
-    for _ in range(args.steps):
+    for _ in range(0 if args.no_e2e else args.steps):
         flush.fill_(1)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -260,8 +260,8 @@ def run_ours(args, world, rank, local):
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_t = max_over_ranks(world, sum(e2e_ms) / 1e3)
-    e2e_value = total_pins / e2e_t
+    e2e_t = max_over_ranks(world, sum(e2e_ms) / 1e3) if e2e_ms else 0.0
+    e2e_value = total_pins / e2e_t if e2e_ms else None
     h2d = 4 * (hgr.m + 1 + hgr.p + hgr.m + hgr.n)
     d2h = 4 * hgr.n
 
@@ -288,7 +288,8 @@ def run_ours(args, world, rank, local):
                    "l2": "flushed between steps (512 MiB write outside the timed events)",
                    "levels": len(levels), "pins_per_step": pins_per_step, "objective": obj},
         "e2e": {"value": e2e_value, "unit": "pins/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": statistics.mean(e2e_ms)},
+                "d2h_bytes_per_step": d2h,
+                "ms_per_step": statistics.mean(e2e_ms) if e2e_ms else None},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": None,
@@ -298,6 +299,10 @@ def run_ours(args, world, rank, local):
         "wall_s": wall,
         "phase_ms": {"rating_kernels": rating_ms / args.steps, "lp_gain_kernels": gain_ms / args.steps},
     }
+    if args.phases:
+        # one extra, untimed step with synchronizing per-phase events
+        _, _, pst = step(phases=True)
+        line["phase_breakdown_ms"] = {k: round(v, 3) for k, v in pst.items() if k.startswith("ms_")}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_sample()
         line["cpu_baseline"] = {"value": cb["value"], "unit": "pins/s", "cores": 1, "kind": "oracle",
@@ -313,6 +318,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end steps")
+    ap.add_argument("--phases", action="store_true",
+                    help="add a per-phase breakdown from one extra, untimed step")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":

@@ -287,8 +287,10 @@ def hg_truncate(h, level):
     _check(load().hg_truncate(h, int(level)), "hg_truncate")
 
 
-def hg_enable_timing(h, on=True):
-    _check(load().hg_enable_timing(h, 1 if on else 0), "hg_enable_timing")
+def hg_enable_timing(h, flags=1):
+    """flags: 1 = per-phase event timing (synchronizing), 2 = event pair around
+    every rating / gain kernel launch (no synchronization); 0 = off."""
+    _check(load().hg_enable_timing(h, int(flags)), "hg_enable_timing")
 
 
 def hg_get_stats(h) -> dict:
