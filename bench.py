@@ -212,10 +212,10 @@ def run_ours(args, world, rank, local):
             hg.hg_destroy(h)
         return obj, levels, stats
 
+    obj = levels = None
     for _ in range(args.warmup):
         obj, levels, _ = step()
     torch.cuda.synchronize()
-    pins_per_step = sum(p for (_, _, p) in levels)
 
     # ---- device-resident timed region
     sampler = ClockSampler(local)
@@ -238,9 +238,12 @@ def run_ours(args, world, rank, local):
         launches += st["launches"]
         for key, val in st.items():
             agg[key] = agg.get(key, 0) + val
+        if obj is None:
+            obj, levels = obj_k, lv_k
         assert obj_k == obj and lv_k == levels, "non-deterministic result"
     torch.cuda.synchronize()
     barrier(world)
+    pins_per_step = sum(p for (_, _, p) in levels)
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
     t_total = max_over_ranks(world, sum(step_ms) / 1e3)
@@ -298,6 +301,9 @@ def run_ours(args, world, rank, local):
         "clocks": clocks,
         "wall_s": wall,
         "phase_ms": {"rating_kernels": rating_ms / args.steps, "lp_gain_kernels": gain_ms / args.steps},
+        "work_per_step": {key: int(agg[key] // args.steps) for key in (
+            "rating_nodes", "rating_incidences", "rating_pin_visits", "lp_nodes", "lp_incidences")},
+        "level_sizes": [list(x) for x in levels],
     }
     if args.phases:
         # one extra, untimed step with synchronizing per-phase events

@@ -108,6 +108,7 @@ typedef struct {
   int64_t lp_gain_launches;
   double ms_rating_kernels;   /* sum of rating kernel durations (timing on) */
   double ms_lp_gain_kernels;  /* sum of gain kernel durations (timing on) */
+  double ms_rating_refresh;   /* per-sub-round refresh of the deduplicated pin clusters */
 } hg_stats;
 
 /* Fills *opt with the defaults listed above (seed 1). */

@@ -259,6 +259,7 @@ int hg_coarsen_level(hg_t* h, int32_t k, int32_t* out_level, int32_t* out_n, int
     hgk::check_status(h->cx);
     h->stats.ms_rating += cc.ms_rating;
     h->stats.ms_approve += cc.ms_approve;
+    h->stats.ms_rating_refresh += cc.ms_refresh;
     h->stats.ms_rating_kernels += cc.ms_rating_kernels;
     h->stats.rating_launches += cc.rating_launches;
     h->stats.rating_pin_visits += cc.rating_pin_visits;

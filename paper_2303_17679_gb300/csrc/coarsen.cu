@@ -14,11 +14,34 @@
 //   approval a target whose moves all fit under c_max accepts them all;
 //            otherwise its movers are sorted by (c(u), u) and the longest
 //            prefix that fits is accepted.
-// Nodes are bucketed per level by sub-round and by a bound on their rating
-// work, W(u) = sum of |e| over rated nets, which decides the team and the
-// hash-table storage: a warp with a 256-slot shared-memory table (W <= 128),
-// a block with a 4096-slot shared-memory table (W <= 2048), or a block with a
-// global-memory table sized for the largest such node.
+//
+// Device state per level:
+//   rpin[q]  = rep[pins[q]] for the pins of rated nets (2 <= |e| <= T), with
+//              every repeat of a cluster inside its net replaced by -1, so a
+//              net contributes once per cluster without any per-visit check.
+//              At the start of a level every cluster is a singleton and rpin
+//              is a copy of the pins; after each sub-round only the nets of
+//              nodes that joined a cluster are recomputed.
+//   cst[C]   = {cw[C], status[C]}: cluster weight and status (the node's
+//              sub-round while it is unclustered, -1 once clustered), read by
+//              the rating with one 8-byte load.
+// Nodes are bucketed per level by class and sub-round.  With W(u) = sum of
+// |e| over u's rated nets (the pins its rating visits) and D = min(W(u), n)
+// (a bound on its distinct candidates), a team accumulates u's ratings in a
+// shared-memory hash table sized to D:
+//   class 0  D <= 256:  one warp, 512 slots;
+//   class 1  D <= 1024: two warps, 2048 slots;
+//   class 2  D <= 4096 (or the level is small), W <= 16384: one block, 8192
+//            slots, or a table direct-indexed by cluster id on small levels;
+//   class 3  the rest: the node's incident nets are cut into items of 32
+//            nets spread over the whole grid, which accumulate into a per-node
+//            global table (direct-indexed or hashed) with a list of the used
+//            slots; a second kernel takes the argmax per node.
+// Class 3 keeps the heaviest nodes (coarse levels: hundreds of thousands of
+// pin visits per node) from serialising a sub-round on one block.  Ratings
+// are accumulated in 32-bit words when the level's largest possible rating
+// fits (then a hash slot packs cluster id and rating into one 64-bit word),
+// else in 64-bit words.
 #include <algorithm>
 
 #include "common.cuh"
@@ -27,18 +50,19 @@ namespace hgk {
 
 namespace {
 
-constexpr int NCLASS = 3;
-constexpr int WARP_TABLE = 256;   // slots per warp table
-constexpr int WARP_MAXW = 128;
-constexpr int CTA_TABLE = 4096;   // slots per block table
-constexpr int CTA_MAXW = 2048;
-constexpr int RATE_WARPS = 8;
-constexpr int CTA_THREADS = 256;
-constexpr int BIG_THREADS = 512;
+constexpr int NCLASS = 4;
+constexpr int32_t D_WARP = 256;
+constexpr int32_t D_PAIR = 1024;
+constexpr int32_t D_BLOCK = 4096;
+constexpr int32_t SPLIT_W = 16384;       // class 3 above this many pin visits
+constexpr int32_t SPLIT_DENSE_MAX = 65536;
+constexpr int SPLIT_WARPS = 8;
+constexpr int ARGMAX_THREADS = 256;
 constexpr int32_t EMPTY_KEY = -1;
+constexpr size_t SMEM_BUDGET = 200 * 1024;
 
 // per sub-round bookkeeping words
-enum { CW_MOVES = 0, CW_TOUCHED = 1, CW_SLOTS = 2, CW_CURSOR = 3, CW_WORDS = 4 };
+enum { CW_MOVES = 0, CW_TOUCHED = 1, CW_SLOTS = 2, CW_CURSOR = 3, CW_DIRTY = 4, CW_WORDS = 8 };
 // work counters
 enum { ST_PINS = 0, ST_INCID = 1, ST_NODES = 2, ST_WORDS = 4 };
 
@@ -46,223 +70,205 @@ struct RateArgs {
   const int32_t* ioff;
   const int32_t* inets;
   const int32_t* eoff;
-  const int32_t* pins;
+  const int32_t* rpin;
   const int32_t* w;
   const int32_t* c;
-  const int32_t* rep;
-  const int32_t* cw;
-  const uint8_t* joined;
-  uint64_t seed;
-  int level, S, s, T;
+  const int2* cst;  // {cw, status}
+  int s, T;
   int32_t c_max, n;
-  const int32_t* list;  // nodes of this (sub-round, class)
+  const int32_t* list;  // nodes of this (class, sub-round)
   int32_t count;
   const int32_t* clusters;
   int32_t* target;
   int32_t* gw;
   int32_t* gcnt;
   int32_t* mv;
-  int32_t* touched;
+  int32_t* touched_targets;
   int32_t* words;
   unsigned long long* stats;
-  int32_t* status;
+  int32_t* status_word;
 };
-
-struct Table {
-  int32_t* key;
-  unsigned long long* claim;
-  long long* val;
-  uint32_t mask;   // capacity - 1 (power of two)
-  int32_t* used;   // slots in use (global tables only)
-  int32_t* nused;
-};
-
-__device__ __forceinline__ void team_sync(bool cta) {
-  if (cta) __syncthreads();
-  else __syncwarp();
-}
 
 __device__ __forceinline__ uint32_t slot_hash(int32_t C) { return (uint32_t)C * 0x9E3779B1u; }
 
-// Finds or inserts C; returns the slot or -1 when the table is full.
-__device__ __forceinline__ int32_t table_insert(const Table& T, int32_t C, bool track_used) {
-  uint32_t h = slot_hash(C) & T.mask;
-  for (uint32_t probe = 0; probe <= T.mask; ++probe) {
-    const int32_t k = T.key[h];
-    if (k == C) return (int32_t)h;
-    if (k == EMPTY_KEY) {
-      const int32_t old = atomicCAS(&T.key[h], EMPTY_KEY, C);
-      if (old == EMPTY_KEY) {
-        if (track_used) T.used[atomicAdd(T.nused, 1)] = (int32_t)h;
-        return (int32_t)h;
-      }
-      if (old == C) return (int32_t)h;
-    }
-    h = (h + 1) & T.mask;
-  }
-  return -1;
-}
+// ---------------------------------------------------- shared hash tables
 
-// Sets bit j of the claim word of a slot for net group g; true if this call
-// set it (the net has not yet contributed to this cluster).
-__device__ __forceinline__ bool claim_net(unsigned long long* word, uint32_t g, int j) {
-  const unsigned long long tag = (unsigned long long)(g + 1) << 32;
-  const unsigned long long bit = 1ull << j;
-  unsigned long long old = *(volatile unsigned long long*)word;
-  while (true) {
-    unsigned long long nw;
-    if ((old & 0xffffffff00000000ull) == tag) {
-      if (old & bit) return false;
-      nw = old | bit;
-    } else {
-      nw = tag | bit;
-    }
-    const unsigned long long prev = atomicCAS(word, old, nw);
-    if (prev == old) return true;
-    old = prev;
-  }
-}
-
-// Rates node u with a team of `nthreads` threads (a warp, or a whole block
-// when cta is true).  tid = thread index inside the team.
-template <bool CTA>
-__device__ void rate_node(const RateArgs& A, int32_t u, const Table& T, int tid, int nthreads,
-                          long long* s_red_val, int32_t* s_red_c, bool global_table) {
-  const int lane = tid & 31;
-  const int32_t cu = A.c[u];
-  const int32_t beg = A.ioff[u], end = A.ioff[u + 1];
-  int64_t visits = 0;
-  for (int32_t g0 = beg; g0 < end; g0 += 32) {
-    const uint32_t g = (uint32_t)((g0 - beg) >> 5);
-    // every warp of the team describes the same group of (up to) 32 nets
-    int32_t e = -1, size = 0, start = 0, eff = 0;
-    long long r = 0;
-    if (g0 + lane < end) {
-      e = A.inets[g0 + lane];
-      start = A.eoff[e];
-      size = A.eoff[e + 1] - start;
-      if (size >= 2 && size <= A.T) {
-        eff = size;
-        r = ((long long)A.w[e] << 20) / (size - 1);
-      }
-    }
-    const int32_t incl = warp_inclusive_scan(eff);
-    const int32_t Z = __shfl_sync(FULL, incl, 31);
-    visits += Z;
-    for (int32_t f0 = 0; f0 < Z; f0 += nthreads) {
-      const int32_t f = f0 + tid;
-      // net index j: number of lanes whose inclusive count is <= f
-      int j = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int32_t probe = __shfl_sync(FULL, incl, j + step - 1);
-        if (probe <= f) j += step;
-      }
-      j = j > 31 ? 31 : j;
-      const int32_t incl_j = __shfl_sync(FULL, incl, j);
-      const int32_t eff_j = __shfl_sync(FULL, eff, j);
-      const int32_t start_j = __shfl_sync(FULL, start, j);
-      const long long r_j = __shfl_sync(FULL, r, j);
-      if (f < Z) {
-        const int32_t pos = f - (incl_j - eff_j);
-        const int32_t v = A.pins[start_j + pos];
-        const int32_t C = A.rep[v];
-        bool ok = C != u;
-        if (ok && !A.joined[C]) ok = subround_of_node_cluster(A.seed, A.level, C, A.S) != A.s;
-        if (ok) ok = (long long)A.cw[C] + cu <= (long long)A.c_max;
-        if (ok) {
-          const int32_t slot = table_insert(T, C, global_table);
-          if (slot < 0) {
-            dev_fail(A.status, DEV_HASH_FULL);
-          } else if (claim_net(&T.claim[slot], g, j)) {
-            atomicAdd((unsigned long long*)&T.val[slot], (unsigned long long)r_j);
-          }
+// 32-bit ratings: one 64-bit word per slot, cluster id above the rating, an
+// empty slot = id -1 with rating 0.  An add to the low half never carries
+// into the id because every rating stays below 2^31.
+struct PackedHash {
+  unsigned long long* slot;
+  uint32_t mask;
+  static constexpr unsigned long long EMPTY = 0xFFFFFFFF00000000ull;
+  static constexpr size_t BYTES_PER_SLOT = 8;
+  __device__ __forceinline__ void init(uint32_t i) { slot[i] = EMPTY; }
+  __device__ __forceinline__ bool add(int32_t C, uint32_t r) {
+    const unsigned long long mine = ((unsigned long long)(uint32_t)C << 32) | r;
+    uint32_t h = slot_hash(C) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+      unsigned long long w = slot[h];
+      while (true) {
+        const uint32_t k = (uint32_t)(w >> 32);
+        if (k == (uint32_t)C) {
+          atomicAdd(&slot[h], (unsigned long long)r);
+          return true;
         }
+        if (k != 0xFFFFFFFFu) break;
+        const unsigned long long old = atomicCAS(&slot[h], w, mine);
+        if (old == w) return true;
+        w = old;
       }
+      h = (h + 1) & mask;
     }
-    team_sync(CTA);
+    return false;
   }
-  // argmax over the table: rating desc, cluster id asc
-  long long best_v = -1;
-  int32_t best_c = -1;
-  if (global_table) {
-    const int32_t nu = *T.nused;
-    for (int32_t i = tid; i < nu; i += nthreads) {
-      const int32_t sl = T.used[i];
-      const long long v = T.val[sl];
-      const int32_t C = T.key[sl];
-      if (v > best_v || (v == best_v && C < best_c)) {
-        best_v = v;
-        best_c = C;
+  // cluster and rating of slot i (C = -1 when empty); the slot is cleared
+  __device__ __forceinline__ void take(uint32_t i, int32_t& C, uint32_t& v) {
+    const unsigned long long w = slot[i];
+    C = (int32_t)(uint32_t)(w >> 32);
+    v = (uint32_t)w;
+    slot[i] = EMPTY;
+  }
+};
+
+// 64-bit ratings: separate key and value arrays.
+struct WideHash {
+  int32_t* key;
+  unsigned long long* val;
+  uint32_t mask;
+  static constexpr size_t BYTES_PER_SLOT = 12;
+  __device__ __forceinline__ void init(uint32_t i) {
+    key[i] = EMPTY_KEY;
+    val[i] = 0;
+  }
+  __device__ __forceinline__ bool add(int32_t C, unsigned long long r) {
+    uint32_t h = slot_hash(C) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+      int32_t k = key[h];
+      if (k == EMPTY_KEY) {
+        const int32_t old = atomicCAS(&key[h], EMPTY_KEY, C);
+        k = old == EMPTY_KEY ? C : old;
       }
+      if (k == C) {
+        atomicAdd(&val[h], r);
+        return true;
+      }
+      h = (h + 1) & mask;
     }
-  } else {
-    for (uint32_t sl = tid; sl <= T.mask; sl += nthreads) {
-      const int32_t C = T.key[sl];
-      if (C == EMPTY_KEY) continue;
-      const long long v = T.val[sl];
-      if (v > best_v || (v == best_v && C < best_c)) {
-        best_v = v;
-        best_c = C;
-      }
+    return false;
+  }
+  __device__ __forceinline__ void take(uint32_t i, int32_t& C, unsigned long long& v) {
+    C = key[i];
+    v = val[i];
+    key[i] = EMPTY_KEY;
+    val[i] = 0;
+  }
+};
+
+template <typename VT> struct HashOf;
+template <> struct HashOf<uint32_t> { using type = PackedHash; };
+template <> struct HashOf<unsigned long long> { using type = WideHash; };
+
+template <typename H>
+__device__ __forceinline__ H make_hash(unsigned char* base, uint32_t slots);
+template <>
+__device__ __forceinline__ PackedHash make_hash<PackedHash>(unsigned char* base, uint32_t slots) {
+  return PackedHash{reinterpret_cast<unsigned long long*>(base), slots - 1};
+}
+template <>
+__device__ __forceinline__ WideHash make_hash<WideHash>(unsigned char* base, uint32_t slots) {
+  unsigned long long* val = reinterpret_cast<unsigned long long*>(base);
+  return WideHash{reinterpret_cast<int32_t*>(val + slots), val, slots - 1};
+}
+
+// ------------------------------------------------------- the rating walk
+
+// Adds one group of (up to) 32 consecutive incident nets of u, starting at
+// position g0 of I(u), through `add`; returns the pin visits.  Nets of at
+// least 32 rated pins are walked one at a time with the lanes over their
+// pins; the smaller nets of the group are walked together over their
+// flattened pins.
+template <typename VT, typename Add>
+__device__ __forceinline__ int32_t rate_group(const RateArgs& A, int32_t u, int32_t cu, int32_t g0,
+                                              int32_t end, Add add) {
+  const int lane = lane_id();
+  int32_t start = 0, eff = 0;
+  VT r = 0;
+  if (g0 + lane < end) {
+    const int32_t e = A.inets[g0 + lane];
+    start = A.eoff[e];
+    const int32_t size = A.eoff[e + 1] - start;
+    if (size >= 2 && size <= A.T) {
+      eff = size;
+      r = (VT)((((long long)A.w[e]) << 20) / (size - 1));
     }
   }
+  auto visit = [&](int32_t q, VT rr) {
+    const int32_t C = A.rpin[q];
+    if (C >= 0 && C != u) {
+      const int2 cs = A.cst[C];
+      if (cs.y != A.s && (long long)cs.x + cu <= (long long)A.c_max) add(C, rr);
+    }
+  };
+  // big nets, one at a time
+  unsigned big = __ballot_sync(FULL, eff >= 32);
+  int32_t visits = 0;
+  while (big) {
+    const int j = __ffs(big) - 1;
+    big &= big - 1;
+    const int32_t st = __shfl_sync(FULL, start, j);
+    const int32_t sz = __shfl_sync(FULL, eff, j);
+    const VT rj = __shfl_sync(FULL, r, j);
+    for (int32_t q = lane; q < sz; q += 32) visit(st + q, rj);
+    visits += sz;
+  }
+  // small nets together
+  const int32_t small = eff < 32 ? eff : 0;
+  const int32_t incl = warp_inclusive_scan(small);
+  const int32_t Z = __shfl_sync(FULL, incl, 31);
+  for (int32_t f0 = 0; f0 < Z; f0 += 32) {
+    const int32_t f = f0 + lane;
+    int j = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int32_t probe = __shfl_sync(FULL, incl, j + step - 1);
+      if (probe <= f) j += step;
+    }
+    j = j > 31 ? 31 : j;
+    const int32_t incl_j = __shfl_sync(FULL, incl, j);
+    const int32_t eff_j = __shfl_sync(FULL, small, j);
+    const int32_t start_j = __shfl_sync(FULL, start, j);
+    const VT r_j = __shfl_sync(FULL, r, j);
+    if (f < Z) visit(start_j + f - (incl_j - eff_j), r_j);
+  }
+  return visits + Z;
+}
+
+template <typename VT>
+__device__ __forceinline__ void better(VT& bv, int32_t& bc, VT v, int32_t C) {
+  if (C >= 0 && (bc < 0 || v > bv || (v == bv && C < bc))) {
+    bv = v;
+    bc = C;
+  }
+}
+
+template <typename VT>
+__device__ __forceinline__ void warp_argmax(VT& best_v, int32_t& best_c) {
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) {
-    const long long ov = __shfl_xor_sync(FULL, best_v, d);
+    const VT ov = __shfl_xor_sync(FULL, best_v, d);
     const int32_t oc = __shfl_xor_sync(FULL, best_c, d);
-    if (ov > best_v || (ov == best_v && oc >= 0 && (best_c < 0 || oc < best_c))) {
-      best_v = ov;
-      best_c = oc;
-    }
+    better(best_v, best_c, ov, oc);
   }
-  if (CTA) {
-    if (lane == 0) {
-      s_red_val[tid >> 5] = best_v;
-      s_red_c[tid >> 5] = best_c;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      for (int wv = 1; wv < nthreads / 32; ++wv) {
-        const long long ov = s_red_val[wv];
-        const int32_t oc = s_red_c[wv];
-        if (ov > best_v || (ov == best_v && oc >= 0 && (best_c < 0 || oc < best_c))) {
-          best_v = ov;
-          best_c = oc;
-        }
-      }
-    }
-  }
-  team_sync(CTA);
-  // reset the table for the next node
-  if (global_table) {
-    const int32_t nu = *T.nused;
-    for (int32_t i = tid; i < nu; i += nthreads) {
-      const int32_t sl = T.used[i];
-      T.key[sl] = EMPTY_KEY;
-      T.claim[sl] = 0;
-      T.val[sl] = 0;
-    }
-    team_sync(CTA);
-    if (tid == 0) *T.nused = 0;
-  } else {
-    for (uint32_t sl = tid; sl <= T.mask; sl += nthreads) {
-      T.key[sl] = EMPTY_KEY;
-      T.claim[sl] = 0;
-      T.val[sl] = 0;
-    }
-  }
-  team_sync(CTA);
-  if (tid == 0) {
-    A.target[u] = best_c;
-    atomicAdd(&A.stats[ST_PINS], (unsigned long long)visits);
-    atomicAdd(&A.stats[ST_INCID], (unsigned long long)(end - beg));
-    atomicAdd(&A.stats[ST_NODES], 1ull);
-    if (best_c >= 0) {
-      A.mv[atomicAdd(&A.words[CW_MOVES], 1)] = u;
-      atomicAdd(&A.gw[best_c], cu);
-      if (atomicAdd(&A.gcnt[best_c], 1) == 0) A.touched[atomicAdd(&A.words[CW_TOUCHED], 1)] = best_c;
-    }
+}
+
+__device__ __forceinline__ void publish(const RateArgs& A, int32_t u, int32_t best_c) {
+  A.target[u] = best_c;
+  if (best_c >= 0) {
+    A.mv[atomicAdd(&A.words[CW_MOVES], 1)] = u;
+    atomicAdd(&A.gw[best_c], A.c[u]);
+    if (atomicAdd(&A.gcnt[best_c], 1) == 0)
+      A.touched_targets[atomicAdd(&A.words[CW_TOUCHED], 1)] = best_c;
   }
 }
 
@@ -270,95 +276,271 @@ __device__ __forceinline__ bool subround_stopped(const RateArgs& A) {
   return 5ll * (long long)(*A.clusters) <= 2ll * (long long)A.n;
 }
 
-// warp per node, 256-slot shared table per warp
-__global__ void __launch_bounds__(RATE_WARPS * 32) k_rate_warp(RateArgs A) {
-  __shared__ int32_t s_key[RATE_WARPS][WARP_TABLE];
-  __shared__ unsigned long long s_claim[RATE_WARPS][WARP_TABLE];
-  __shared__ long long s_val[RATE_WARPS][WARP_TABLE];
-  if (subround_stopped(A)) return;
-  const int wv = warp_in_block(), lane = lane_id();
-  Table T{s_key[wv], s_claim[wv], s_val[wv], WARP_TABLE - 1, nullptr, nullptr};
-  for (int i = lane; i < WARP_TABLE; i += 32) {
-    s_key[wv][i] = EMPTY_KEY;
-    s_claim[wv][i] = 0;
-    s_val[wv][i] = 0;
-  }
-  __syncwarp();
-  for (int32_t i = blockIdx.x * RATE_WARPS + wv; i < A.count; i += gridDim.x * RATE_WARPS) {
-    const int32_t u = A.list[i];
-    if (A.joined[u]) continue;
-    rate_node<false>(A, u, T, lane, 32, nullptr, nullptr, false);
+// Synchronises the TW warps of team `team` (TW = 1: the warp; TW = warps per
+// block: the block; else a named barrier per team).
+template <int TW>
+__device__ __forceinline__ void team_sync(int team) {
+  if (TW == 1) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(TW * 32) : "memory");
   }
 }
 
-// block per node, 4096-slot shared table (dynamic shared memory)
-__global__ void __launch_bounds__(CTA_THREADS) k_rate_cta(RateArgs A) {
-  extern __shared__ unsigned char smem[];
-  __shared__ long long s_rv[32];
-  __shared__ int32_t s_rc[32];
+// classes 0-2 with hash tables: TEAMS teams of TW warps per block, each team
+// rating one node at a time with a SLOTS-slot shared hash table
+template <typename VT, int TW, int TEAMS>
+__global__ void __launch_bounds__(TW * 32 * TEAMS) k_rate_team(RateArgs A, uint32_t slots) {
+  using H = typename HashOf<VT>::type;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ VT s_rv[TEAMS][TW];
+  __shared__ int32_t s_rc[TEAMS][TW];
   if (subround_stopped(A)) return;
-  unsigned long long* claim = reinterpret_cast<unsigned long long*>(smem);
-  long long* val = reinterpret_cast<long long*>(claim + CTA_TABLE);
-  int32_t* key = reinterpret_cast<int32_t*>(val + CTA_TABLE);
-  Table T{key, claim, val, CTA_TABLE - 1, nullptr, nullptr};
-  for (int i = threadIdx.x; i < CTA_TABLE; i += blockDim.x) {
-    key[i] = EMPTY_KEY;
-    claim[i] = 0;
-    val[i] = 0;
+  const int team = warp_in_block() / TW, wt = warp_in_block() % TW;
+  const int tid = threadIdx.x % (TW * 32), nthr = TW * 32;
+  H tab = make_hash<H>(smem + (size_t)team * slots * H::BYTES_PER_SLOT, slots);
+  for (uint32_t i = tid; i < slots; i += nthr) tab.init(i);
+  team_sync<TW>(team);
+  int64_t visits = 0, incid = 0, nodes = 0;
+  for (int32_t i = blockIdx.x * TEAMS + team; i < A.count; i += gridDim.x * TEAMS) {
+    const int32_t u = A.list[i];
+    if (A.cst[u].y < 0) continue;  // joined a cluster in an earlier sub-round
+    const int32_t cu = A.c[u], beg = A.ioff[u], end = A.ioff[u + 1];
+    for (int32_t g0 = beg + 32 * wt; g0 < end; g0 += 32 * TW)
+      visits += rate_group<VT>(A, u, cu, g0, end, [&](int32_t C, VT r) {
+        if (!tab.add(C, r)) dev_fail(A.status_word, DEV_HASH_FULL);
+      });
+    team_sync<TW>(team);
+    VT bv = 0;
+    int32_t bc = -1;
+    for (uint32_t x = tid; x < slots; x += nthr) {
+      int32_t C;
+      VT v;
+      tab.take(x, C, v);
+      better(bv, bc, v, C);
+    }
+    warp_argmax(bv, bc);
+    if (TW > 1) {
+      if (lane_id() == 0) {
+        s_rv[team][wt] = bv;
+        s_rc[team][wt] = bc;
+      }
+      team_sync<TW>(team);
+      if (tid == 0)
+        for (int x = 1; x < TW; ++x) better(bv, bc, s_rv[team][x], s_rc[team][x]);
+    }
+    if (tid == 0) publish(A, u, bc);
+    team_sync<TW>(team);
+    incid += end - beg;
+    ++nodes;
   }
+  if (lane_id() == 0 && visits) atomicAdd(&A.stats[ST_PINS], (unsigned long long)visits);
+  if (tid == 0 && nodes) {
+    atomicAdd(&A.stats[ST_INCID], (unsigned long long)incid);
+    atomicAdd(&A.stats[ST_NODES], (unsigned long long)nodes);
+  }
+}
+
+// class 2 on small levels: one block per node with a table direct-indexed by
+// cluster id (n values, then the list of touched ids)
+template <typename VT>
+__global__ void __launch_bounds__(256) k_rate_dense(RateArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int32_t s_nused;
+  __shared__ VT s_rv[8];
+  __shared__ int32_t s_rc[8];
+  if (subround_stopped(A)) return;
+  const uint32_t cap = (uint32_t)A.n;
+  VT* val = reinterpret_cast<VT*>(smem);
+  int32_t* used = reinterpret_cast<int32_t*>(val + cap);
+  for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) val[i] = 0;
+  if (threadIdx.x == 0) s_nused = 0;
   __syncthreads();
+  const int nw = blockDim.x >> 5, wv = warp_in_block();
+  int64_t visits = 0, incid = 0, nodes = 0;
   for (int32_t i = blockIdx.x; i < A.count; i += gridDim.x) {
     const int32_t u = A.list[i];
-    if (A.joined[u]) continue;
-    rate_node<true>(A, u, T, threadIdx.x, blockDim.x, s_rv, s_rc, false);
+    if (A.cst[u].y < 0) continue;
+    const int32_t cu = A.c[u], beg = A.ioff[u], end = A.ioff[u + 1];
+    for (int32_t g0 = beg + 32 * wv; g0 < end; g0 += 32 * nw)
+      visits += rate_group<VT>(A, u, cu, g0, end, [&](int32_t C, VT r) {
+        // every term is >= 1, so a zero before the add marks the first touch
+        if (atomicAdd(&val[C], r) == (VT)0) used[atomicAdd(&s_nused, 1)] = C;
+      });
+    __syncthreads();
+    VT bv = 0;
+    int32_t bc = -1;
+    const int32_t nu = s_nused;
+    for (int32_t x = threadIdx.x; x < nu; x += blockDim.x) {
+      const int32_t C = used[x];
+      better(bv, bc, val[C], C);
+      val[C] = 0;
+    }
+    warp_argmax(bv, bc);
+    if (lane_id() == 0) {
+      s_rv[wv] = bv;
+      s_rc[wv] = bc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int x = 1; x < nw; ++x) better(bv, bc, s_rv[x], s_rc[x]);
+      s_nused = 0;
+      publish(A, u, bc);
+      incid += end - beg;
+      ++nodes;
+    }
+    __syncthreads();
+  }
+  if (lane_id() == 0 && visits) atomicAdd(&A.stats[ST_PINS], (unsigned long long)visits);
+  if (threadIdx.x == 0 && nodes) {
+    atomicAdd(&A.stats[ST_INCID], (unsigned long long)incid);
+    atomicAdd(&A.stats[ST_NODES], (unsigned long long)nodes);
   }
 }
 
-// block per node, global table of 2^k slots per block
-__global__ void __launch_bounds__(BIG_THREADS)
-k_rate_big(RateArgs A, int32_t* gkey, unsigned long long* gclaim, long long* gval, int32_t* gused,
-           int32_t* gnused, uint32_t cap) {
-  __shared__ long long s_rv[32];
+// class 3, phase 1: one warp per item (a class-3 node of the sub-round and
+// one group of 32 of its incident nets); accumulates into the node's global
+// table at tab_off[i] - tab_base (values; keys in hash mode; the list of
+// used slots with its counter tnused[i])
+template <typename VT>
+__global__ void __launch_bounds__(SPLIT_WARPS * 32)
+k_rate_split_acc(RateArgs A, const int32_t* __restrict__ split, const int32_t* __restrict__ item_node,
+                 const int32_t* __restrict__ item_off, const int64_t* __restrict__ tab_off,
+                 const int64_t* __restrict__ tab_cap, const int8_t* __restrict__ tab_dense,
+                 int32_t item_lo, int32_t item_hi, int64_t tab_base, int32_t* __restrict__ tkey,
+                 VT* __restrict__ tval, int32_t* __restrict__ tused, int32_t* __restrict__ tnused) {
+  if (subround_stopped(A)) return;
+  int64_t visits = 0, incid = 0;
+  for (int32_t t = item_lo + blockIdx.x * SPLIT_WARPS + warp_in_block(); t < item_hi;
+       t += gridDim.x * SPLIT_WARPS) {
+    const int32_t i = item_node[t];
+    const int32_t u = split[i];
+    if (A.cst[u].y < 0) continue;
+    const int32_t cu = A.c[u], beg = A.ioff[u], end = A.ioff[u + 1];
+    const int32_t g0 = beg + 32 * (t - item_off[i]);
+    const int64_t base = tab_off[i] - tab_base;
+    VT* val = tval + base;
+    int32_t* used = tused + base;
+    int32_t* nused = tnused + i;
+    if (tab_dense[i]) {
+      visits += rate_group<VT>(A, u, cu, g0, end, [&](int32_t C, VT r) {
+        if (atomicAdd(&val[C], r) == (VT)0) used[atomicAdd(nused, 1)] = C;
+      });
+    } else {
+      int32_t* key = tkey + base;
+      const uint32_t mask = (uint32_t)tab_cap[i] - 1;
+      visits += rate_group<VT>(A, u, cu, g0, end, [&](int32_t C, VT r) {
+        uint32_t h = slot_hash(C) & mask;
+        for (uint32_t probe = 0; probe <= mask; ++probe) {
+          const int32_t k = key[h];
+          if (k == C) break;
+          if (k == EMPTY_KEY) {
+            const int32_t old = atomicCAS(&key[h], EMPTY_KEY, C);
+            if (old == EMPTY_KEY) {
+              used[atomicAdd(nused, 1)] = (int32_t)h;
+              break;
+            }
+            if (old == C) break;
+          }
+          h = (h + 1) & mask;
+        }
+        if (key[h] == C) atomicAdd(&val[h], r);
+        else dev_fail(A.status_word, DEV_HASH_FULL);
+      });
+    }
+    incid += min(32, end - g0);
+  }
+  if (lane_id() == 0 && visits) {
+    atomicAdd(&A.stats[ST_PINS], (unsigned long long)visits);
+    atomicAdd(&A.stats[ST_INCID], (unsigned long long)incid);
+  }
+}
+
+// class 3, phase 2: one block per class-3 node of the sub-round: argmax over
+// its used slots, which are cleared on the way for the next sub-round
+template <typename VT>
+__global__ void __launch_bounds__(ARGMAX_THREADS)
+k_rate_split_argmax(RateArgs A, const int32_t* __restrict__ split, int32_t lo, int32_t hi,
+                    const int64_t* __restrict__ tab_off, const int8_t* __restrict__ tab_dense,
+                    int64_t tab_base, int32_t* __restrict__ tkey, VT* __restrict__ tval,
+                    const int32_t* __restrict__ tused, int32_t* __restrict__ tnused) {
+  __shared__ VT s_rv[32];
   __shared__ int32_t s_rc[32];
   if (subround_stopped(A)) return;
-  const size_t off = (size_t)blockIdx.x * cap;
-  Table T{gkey + off, gclaim + off, gval + off, cap - 1, gused + off, gnused + blockIdx.x};
-  for (int32_t i = blockIdx.x; i < A.count; i += gridDim.x) {
-    const int32_t u = A.list[i];
-    if (A.joined[u]) continue;
-    rate_node<true>(A, u, T, threadIdx.x, blockDim.x, s_rv, s_rc, true);
+  for (int32_t i = lo + blockIdx.x; i < hi; i += gridDim.x) {
+    const int32_t u = split[i];
+    if (A.cst[u].y < 0) continue;
+    const int64_t base = tab_off[i] - tab_base;
+    const bool dense = tab_dense[i] != 0;
+    const int32_t nu = tnused[i];
+    VT bv = 0;
+    int32_t bc = -1;
+    for (int32_t x = threadIdx.x; x < nu; x += blockDim.x) {
+      const int32_t sl = tused[base + x];
+      const int32_t C = dense ? sl : tkey[base + sl];
+      better(bv, bc, tval[base + sl], C);
+      tval[base + sl] = 0;
+      if (!dense) tkey[base + sl] = EMPTY_KEY;
+    }
+    warp_argmax(bv, bc);
+    const int nw = blockDim.x >> 5;
+    if (lane_id() == 0) {
+      s_rv[warp_in_block()] = bv;
+      s_rc[warp_in_block()] = bc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int x = 1; x < nw; ++x) better(bv, bc, s_rv[x], s_rc[x]);
+      tnused[i] = 0;
+      publish(A, u, bc);
+      atomicAdd(&A.stats[ST_NODES], 1ull);
+    }
+    __syncthreads();
   }
 }
 
 // ------------------------------------------------------- node bucketing
 
-__device__ __forceinline__ int work_class(int32_t W) {
-  return W <= WARP_MAXW ? 0 : (W <= CTA_MAXW ? 1 : 2);
+__device__ __forceinline__ int rate_class(int64_t W, int32_t n, bool dense_block) {
+  const int64_t D = W < n ? W : n;  // bound on the distinct candidate clusters
+  if (D <= D_WARP) return 0;
+  if (dense_block && W <= SPLIT_W) return 2;
+  if (D <= D_PAIR) return 1;
+  if (D <= D_BLOCK && W <= SPLIT_W) return 2;
+  return 3;
 }
 
-// W(u) and the (sub-round, class) key of every node with W(u) > 0.
+// W(u) (pins of rated nets), the bound on u's rating (sum of its net terms)
+// and the key = class * S + sub-round of every node with W(u) > 0.
 __global__ void k_node_work(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
-                            const int32_t* __restrict__ eoff, int32_t n, int T, uint64_t seed,
-                            int level, int S, int32_t* __restrict__ key_of,
-                            int32_t* __restrict__ kcount, int32_t* __restrict__ max_big) {
+                            const int32_t* __restrict__ eoff, const int32_t* __restrict__ w,
+                            int32_t n, int T, uint64_t seed, int level, int S, bool dense_block,
+                            int32_t* __restrict__ key_of, int32_t* __restrict__ wof,
+                            int32_t* __restrict__ kcount, unsigned long long* __restrict__ max_r) {
+  unsigned long long lr = 0;
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
        u += (int64_t)gridDim.x * blockDim.x) {
     int64_t W = 0;
+    unsigned long long R = 0;
     for (int32_t j = ioff[u]; j < ioff[u + 1]; ++j) {
       const int32_t e = inets[j];
       const int32_t sz = eoff[e + 1] - eoff[e];
-      if (sz >= 2 && sz <= T) W += sz;
+      if (sz >= 2 && sz <= T) {
+        W += sz;
+        R += (((unsigned long long)w[e]) << 20) / (unsigned long long)(sz - 1);
+      }
     }
     int32_t key = -1;
     if (W > 0) {
-      const int32_t Wc = W > 0x7fffffff ? 0x7fffffff : (int32_t)W;
-      const int cls = work_class(Wc);
-      key = subround_of_node_cluster(seed, level, (int)u, S) * NCLASS + cls;
+      key = rate_class(W, n, dense_block) * S + subround_of_node_cluster(seed, level, (int)u, S);
       atomicAdd(&kcount[key], 1);
-      if (cls == 2) atomicMax(max_big, Wc);
+      lr = R > lr ? R : lr;
     }
     key_of[u] = key;
+    wof[u] = W > 0x7fffffff ? 0x7fffffff : (int32_t)W;
   }
+  const unsigned long long lr2 = warp_max(lr);
+  if (lane_id() == 0 && lr2) atomicMax(max_r, lr2);
 }
 
 __global__ void k_node_scatter(const int32_t* __restrict__ key_of, int32_t n, int nkeys,
@@ -380,22 +562,65 @@ __global__ void k_node_scatter(const int32_t* __restrict__ key_of, int32_t n, in
   }
 }
 
+// Item count (groups of 32 incident nets), table mode and capacity of every
+// class-3 node: direct-indexed (n entries) when n <= min(2 W(u), 65536), so
+// the table costs no more than the accumulation; else hashed, a power of two
+// >= 2 min(W, n) + 2.
+__global__ void k_split_sizes(const int32_t* __restrict__ split, int32_t nsplit,
+                              const int32_t* __restrict__ ioff, const int32_t* __restrict__ wof,
+                              int32_t n, int32_t* __restrict__ items, int32_t* __restrict__ cap,
+                              int8_t* __restrict__ dense) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nsplit; i += gridDim.x * blockDim.x) {
+    const int32_t u = split[i];
+    items[i] = (ioff[u + 1] - ioff[u] + 31) / 32;
+    const bool d = n <= SPLIT_DENSE_MAX && (int64_t)n <= 2 * (int64_t)wof[u];
+    dense[i] = d ? 1 : 0;
+    if (d) {
+      cap[i] = n;
+    } else {
+      const int64_t want = 2 * (int64_t)min(wof[u], n) + 2;
+      int64_t c = 1;
+      while (c < want) c <<= 1;
+      cap[i] = (int32_t)c;
+    }
+  }
+}
+
+__global__ void k_split_items(const int32_t* __restrict__ item_off, int32_t nsplit,
+                              int32_t* __restrict__ item_node) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nsplit; i += gridDim.x * blockDim.x)
+    for (int32_t t = item_off[i]; t < item_off[i + 1]; ++t) item_node[t] = i;
+}
+
+__global__ void k_widen(const int32_t* __restrict__ in, int64_t* __restrict__ out, int32_t cnt) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
+    out[i] = in[i];
+}
+
+template <typename VT>
+__global__ void k_init_table(int32_t* key, VT* val, size_t cnt) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+       i += (size_t)gridDim.x * blockDim.x) {
+    key[i] = EMPTY_KEY;
+    val[i] = 0;
+  }
+}
+
 // ------------------------------------------------------------- approval
 
 __global__ void k_approve(const int32_t* __restrict__ mv, const int32_t* __restrict__ words,
-                          const int32_t* __restrict__ target, const int32_t* __restrict__ cw,
+                          const int32_t* __restrict__ target, int2* __restrict__ cst,
                           const int32_t* __restrict__ gw, const int32_t* __restrict__ gcnt,
-                          int32_t c_max, int32_t* __restrict__ rep, uint8_t* __restrict__ joined,
-                          int32_t* __restrict__ slot_of, int32_t* __restrict__ slot_c,
-                          int32_t* __restrict__ slot_off, int32_t* __restrict__ wslots,
-                          int32_t* __restrict__ wcursor) {
+                          int32_t c_max, int32_t* __restrict__ rep, int32_t* __restrict__ slot_of,
+                          int32_t* __restrict__ slot_c, int32_t* __restrict__ slot_off,
+                          int32_t* __restrict__ wslots, int32_t* __restrict__ wcursor) {
   const int32_t nm = words[CW_MOVES];
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nm; i += gridDim.x * blockDim.x) {
     const int32_t u = mv[i];
     const int32_t C = target[u];
-    if ((long long)cw[C] + gw[C] <= (long long)c_max) {
+    if ((long long)cst[C].x + gw[C] <= (long long)c_max) {
       rep[u] = C;   // fast path: every move into C fits
-      joined[u] = 1;
+      cst[u].y = -1;
     } else if (atomicCAS(&slot_of[C], -1, -2) == -1) {
       const int32_t sl = atomicAdd(wslots, 1);
       slot_c[sl] = C;
@@ -406,7 +631,7 @@ __global__ void k_approve(const int32_t* __restrict__ mv, const int32_t* __restr
 }
 
 __global__ void k_contest_scatter(const int32_t* __restrict__ mv, const int32_t* __restrict__ words,
-                                  const int32_t* __restrict__ target, const int32_t* __restrict__ cw,
+                                  const int32_t* __restrict__ target, const int2* __restrict__ cst,
                                   const int32_t* __restrict__ gw, int32_t c_max,
                                   const int32_t* __restrict__ slot_of,
                                   const int32_t* __restrict__ slot_off,
@@ -415,7 +640,7 @@ __global__ void k_contest_scatter(const int32_t* __restrict__ mv, const int32_t*
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nm; i += gridDim.x * blockDim.x) {
     const int32_t u = mv[i];
     const int32_t C = target[u];
-    if ((long long)cw[C] + gw[C] > (long long)c_max) {
+    if ((long long)cst[C].x + gw[C] > (long long)c_max) {
       const int32_t sl = slot_of[C];
       glist[slot_off[sl] + atomicAdd(&slot_fill[sl], 1)] = u;
     }
@@ -449,19 +674,18 @@ k_contest_group(const int32_t* __restrict__ words, const int32_t* __restrict__ s
                 const int32_t* __restrict__ slot_off, int32_t* __restrict__ slot_fill,
                 int32_t* __restrict__ slot_of, const int32_t* __restrict__ glist,
                 const int32_t* __restrict__ gcnt, const int32_t* __restrict__ c, int32_t c_max,
-                int32_t* __restrict__ cw, int32_t* __restrict__ rep, uint8_t* __restrict__ joined,
-                int32_t* __restrict__ clusters) {
+                int2* __restrict__ cst, int32_t* __restrict__ rep, int32_t* __restrict__ clusters) {
   __shared__ unsigned long long s_keys[GROUP_SMEM_CAP];
   __shared__ long long s_red[32];
-  __shared__ unsigned long long s_tau;
+  __shared__ unsigned long long s_acc;
   const int32_t nslots = words[CW_SLOTS];
   for (int32_t sl = blockIdx.x; sl < nslots; sl += gridDim.x) {
     const int32_t C = slot_c[sl];
     const int32_t cnt = gcnt[C];
     const int32_t off = slot_off[sl];
-    const long long cap = (long long)c_max - cw[C];
-    // accepted = members whose key (c(u) << 32 | u) is <= tau, the largest key
-    // with (sum of c over keys <= tau) <= cap
+    const long long cap = (long long)c_max - cst[C].x;
+    long long added = 0;
+    int32_t acc = 0;
     if (cnt <= GROUP_SMEM_CAP) {
       int P = 1;
       while (P < cnt) P <<= 1;
@@ -473,17 +697,16 @@ k_contest_group(const int32_t* __restrict__ words, const int32_t* __restrict__ s
           s_keys[i] = ~0ull;
         }
       }
+      if (threadIdx.x == 0) s_acc = 0;
       __syncthreads();
       group_bitonic(s_keys, P);
-      // prefix sums in chunks; the accepted count is the number of positions
-      // whose inclusive prefix is <= cap (weights are positive)
+      // the accepted count is the number of positions whose inclusive weight
+      // prefix is <= cap (weights are positive, so these form a prefix)
       long long carry = 0;
-      if (threadIdx.x == 0) s_tau = 0;
-      __syncthreads();
       for (int base = 0; base < cnt; base += blockDim.x) {
         const int i = base + threadIdx.x;
         const long long v = i < cnt ? (long long)(s_keys[i] >> 32) : 0;
-        long long x = warp_inclusive_scan(v);
+        const long long x = warp_inclusive_scan(v);
         if (lane_id() == 31) s_red[warp_in_block()] = x;
         __syncthreads();
         if (warp_in_block() == 0) {
@@ -494,85 +717,68 @@ k_contest_group(const int32_t* __restrict__ words, const int32_t* __restrict__ s
         __syncthreads();
         const long long incl = carry + (warp_in_block() ? s_red[warp_in_block() - 1] : 0) + x;
         const long long chunk_total = s_red[(blockDim.x >> 5) - 1];
-        if (i < cnt && incl <= cap) atomicAdd(&s_tau, 1ull);
+        if (i < cnt && incl <= cap) atomicAdd(&s_acc, 1ull);
         carry += chunk_total;
         __syncthreads();
       }
-      const int32_t acc = (int32_t)s_tau;
-      long long added = 0;
+      acc = (int32_t)s_acc;
       for (int i = threadIdx.x; i < acc; i += blockDim.x) {
         const int32_t u = (int32_t)(s_keys[i] & 0xffffffffu);
         rep[u] = C;
-        joined[u] = 1;
+        cst[u].y = -1;
         added += (long long)(s_keys[i] >> 32);
       }
-      added = block_sum(added, s_red);
-      if (threadIdx.x == 0) {
-        cw[C] += (int32_t)added;
-        if (acc > 0) {
-          joined[C] = 1;
-          atomicSub(clusters, acc);
-        }
-        slot_of[C] = -1;
-        slot_fill[sl] = 0;
-      }
-      __syncthreads();
     } else {
-      // large group: binary search for tau over the 63-bit key space
-      unsigned long long lo = 0, hi = (1ull << 63);  // answer in [lo, hi); lo - 1 = "none"
-      // find the largest tau with F(tau) <= cap, F(tau) = sum of c over keys <= tau
-      // invariant: F(lo - 1) <= cap (F(-1) = 0), F(hi) > cap or hi = 2^63
+      // large group: binary search for the first excluded key x, the largest
+      // x with (sum of c over keys < x) <= cap; all keys < x are accepted
+      unsigned long long lo = 0, hi = (1ull << 63);
       while (hi - lo > 1) {
         const unsigned long long mid = lo + ((hi - lo) >> 1);
         long long f = 0;
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
           const int32_t u = glist[off + i];
           const unsigned long long kk = ((unsigned long long)(uint32_t)c[u] << 32) | (uint32_t)u;
-          if (kk <= mid - 1) f += c[u];
+          if (kk < mid) f += c[u];
         }
         f = block_sum(f, s_red);
         if (f <= cap) lo = mid; else hi = mid;
       }
-      // accepted: keys <= lo - 1 ... written as keys < lo
-      long long added = 0;
-      int32_t acc = 0;
       for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
         const int32_t u = glist[off + i];
         const unsigned long long kk = ((unsigned long long)(uint32_t)c[u] << 32) | (uint32_t)u;
         if (kk < lo) {
           rep[u] = C;
-          joined[u] = 1;
+          cst[u].y = -1;
           added += c[u];
           ++acc;
         }
       }
-      added = block_sum(added, s_red);
-      const long long acc_all = block_sum((long long)acc, s_red);
-      if (threadIdx.x == 0) {
-        cw[C] += (int32_t)added;
-        if (acc_all > 0) {
-          joined[C] = 1;
-          atomicSub(clusters, (int32_t)acc_all);
-        }
-        slot_of[C] = -1;
-        slot_fill[sl] = 0;
-      }
-      __syncthreads();
+      acc = (int32_t)block_sum((long long)acc, s_red);
     }
+    added = block_sum(added, s_red);
+    if (threadIdx.x == 0) {
+      cst[C].x += (int32_t)added;
+      if (acc > 0) {
+        cst[C].y = -1;
+        atomicSub(clusters, acc);
+      }
+      slot_of[C] = -1;
+      slot_fill[sl] = 0;
+    }
+    __syncthreads();
   }
 }
 
 // Uncontested targets: add the summed weight of their movers; reset the sums.
 __global__ void k_finish(const int32_t* __restrict__ touched, const int32_t* __restrict__ words,
-                         int32_t c_max, int32_t* __restrict__ cw, int32_t* __restrict__ gw,
-                         int32_t* __restrict__ gcnt, uint8_t* __restrict__ joined,
-                         int32_t* __restrict__ clusters) {
+                         int32_t c_max, int2* __restrict__ cst, int32_t* __restrict__ gw,
+                         int32_t* __restrict__ gcnt, int32_t* __restrict__ clusters) {
   const int32_t nt = words[CW_TOUCHED];
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += gridDim.x * blockDim.x) {
     const int32_t C = touched[i];
-    if ((long long)cw[C] + gw[C] <= (long long)c_max) {
-      cw[C] += gw[C];
-      joined[C] = 1;
+    const int32_t cw = cst[C].x;
+    if ((long long)cw + gw[C] <= (long long)c_max) {
+      cst[C] = make_int2(cw + gw[C], -1);
       atomicSub(clusters, gcnt[C]);
     }
     gw[C] = 0;
@@ -580,24 +786,222 @@ __global__ void k_finish(const int32_t* __restrict__ touched, const int32_t* __r
   }
 }
 
-__global__ void k_init_cluster(const int32_t* __restrict__ c, int32_t n, int32_t* __restrict__ rep,
-                               int32_t* __restrict__ cw, uint8_t* __restrict__ joined,
+// ------------------------------------------------- rpin maintenance
+
+// Nets of the movers that joined a cluster in this sub-round: one warp per
+// mover marks its rated nets dirty (first marker appends to the list).
+__global__ void k_mark_dirty(const int32_t* __restrict__ mv, const int32_t* __restrict__ words,
+                             const int32_t* __restrict__ rep, const int32_t* __restrict__ ioff,
+                             const int32_t* __restrict__ inets, const int32_t* __restrict__ eoff,
+                             int T, int32_t* __restrict__ dirty, int32_t* __restrict__ dlist,
+                             int32_t* __restrict__ ndirty) {
+  const int32_t nm = words[CW_MOVES];
+  const int wv = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int32_t i = wv; i < nm; i += nwarps) {
+    const int32_t u = mv[i];
+    if (rep[u] == u) continue;  // rejected
+    for (int32_t j = ioff[u] + lane_id(); j < ioff[u + 1]; j += 32) {
+      const int32_t e = inets[j];
+      const int32_t sz = eoff[e + 1] - eoff[e];
+      if (sz < 2 || sz > T) continue;
+      if (atomicExch(&dirty[e], 1) == 0) dlist[atomicAdd(ndirty, 1)] = e;
+    }
+  }
+}
+
+constexpr int REFRESH_WARPS = 2;
+constexpr int REFRESH_SET = 2048;  // per-warp set for nets of up to 1024 pins
+
+// One entry of a per-warp set keyed by cluster: key = gen << 32 | C and
+// pos = ~gen << 32 | position, where gen numbers the nets a warp processes.
+// Entries of earlier nets are stale (other gen) and count as empty; for the
+// current net, atomicMin on pos keeps the smallest position (~gen shrinks as
+// gen grows, so a stale entry is always larger).  No reset pass is needed.
+__device__ __forceinline__ void set_insert_min(unsigned long long* key, unsigned long long* pos,
+                                               uint32_t mask, uint32_t gen, int32_t C, int32_t q,
+                                               int32_t* status) {
+  const unsigned long long mine = ((unsigned long long)gen << 32) | (uint32_t)C;
+  uint32_t h = slot_hash(C) & mask;
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    unsigned long long k = key[h];
+    while ((uint32_t)(k >> 32) != gen) {  // stale: try to claim it
+      const unsigned long long old = atomicCAS(&key[h], k, mine);
+      if (old == k) { k = mine; break; }
+      k = old;
+    }
+    if (k == mine) {
+      atomicMin(&pos[h], ((unsigned long long)(~gen) << 32) | (uint32_t)q);
+      return;
+    }
+    h = (h + 1) & mask;
+  }
+  dev_fail(status, DEV_HASH_FULL);
+}
+
+__device__ __forceinline__ bool set_is_first(const unsigned long long* key,
+                                             const unsigned long long* pos, uint32_t mask,
+                                             uint32_t gen, int32_t C, int32_t q) {
+  const unsigned long long mine = ((unsigned long long)gen << 32) | (uint32_t)C;
+  uint32_t h = slot_hash(C) & mask;
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    if (key[h] == mine) return pos[h] == (((unsigned long long)(~gen) << 32) | (uint32_t)q);
+    h = (h + 1) & mask;
+  }
+  return false;
+}
+
+// Recompute rpin for every dirty net: rpin[q] = rep[pins[q]] for the first
+// pin of each cluster in the net, -1 for its repeats.  Nets of <= 32 pins
+// use a warp match; larger nets a per-warp set (shared memory for up to 1024
+// pins, global memory above that, which only occurs with T > 1024).
+__global__ void __launch_bounds__(REFRESH_WARPS * 32)
+k_refresh_rpin(const int32_t* __restrict__ dlist, const int32_t* __restrict__ ndirty,
+               const int32_t* __restrict__ eoff, const int32_t* __restrict__ pins,
+               const int32_t* __restrict__ rep, int32_t* __restrict__ dirty,
+               int32_t* __restrict__ rpin, unsigned long long* gset, uint32_t gcap,
+               int32_t* status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int wv = warp_in_block(), lane = lane_id();
+  unsigned long long* skey = reinterpret_cast<unsigned long long*>(smem) + (size_t)wv * 2 * REFRESH_SET;
+  unsigned long long* spos = skey + REFRESH_SET;
+  for (int i = lane; i < REFRESH_SET; i += 32) {
+    skey[i] = 0;
+    spos[i] = ~0ull;
+  }
+  __syncwarp();
+  const int32_t nd = *ndirty;
+  const int gw = blockIdx.x * REFRESH_WARPS + wv;
+  const int nwarps = gridDim.x * REFRESH_WARPS;
+  uint32_t gen = 0;
+  for (int32_t i = gw; i < nd; i += nwarps) {
+    const int32_t e = dlist[i];
+    const int32_t b = eoff[e], sz = eoff[e + 1] - b;
+    if (sz <= 32) {
+      const bool act = lane < sz;
+      const int32_t C = act ? rep[pins[b + lane]] : -1 - lane;
+      const unsigned peers = __match_any_sync(FULL, C);
+      if (act) rpin[b + lane] = (__ffs(peers) - 1 == lane) ? C : -1;
+    } else {
+      ++gen;
+      unsigned long long* k2 = skey;
+      unsigned long long* p2 = spos;
+      uint32_t mask = REFRESH_SET - 1;
+      if (sz > REFRESH_SET / 2) {
+        k2 = gset + (size_t)gw * 2 * gcap;
+        p2 = k2 + gcap;
+        mask = gcap - 1;
+      }
+      for (int32_t q = lane; q < sz; q += 32)
+        set_insert_min(k2, p2, mask, gen, rep[pins[b + q]], q, status);
+      __syncwarp();
+      for (int32_t q = lane; q < sz; q += 32) {
+        const int32_t C = rep[pins[b + q]];
+        rpin[b + q] = set_is_first(k2, p2, mask, gen, C, q) ? C : -1;
+      }
+      __syncwarp();
+    }
+    if (lane == 0) dirty[e] = 0;
+  }
+}
+
+__global__ void k_init_cluster(const int32_t* __restrict__ c, int32_t n, uint64_t seed, int level,
+                               int S, int32_t* __restrict__ rep, int2* __restrict__ cst,
                                int32_t* __restrict__ slot_of) {
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
        u += (int64_t)gridDim.x * blockDim.x) {
     rep[u] = (int32_t)u;
-    cw[u] = c[u];
-    joined[u] = 0;
+    cst[u] = make_int2(c[u], subround_of_node_cluster(seed, level, (int)u, S));
     slot_of[u] = -1;
   }
 }
 
-__global__ void k_init_table(int32_t* key, unsigned long long* claim, long long* val, size_t cnt) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
-       i += (size_t)gridDim.x * blockDim.x) {
-    key[i] = EMPTY_KEY;
-    claim[i] = 0;
-    val[i] = 0;
+
+// ---------------------------------------------------------- host side
+
+template <typename F>
+void allow_smem(F* kernel) {
+  HG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)SMEM_BUDGET));
+}
+
+template <typename VT>
+void set_rate_attrs() {
+  static bool done = false;  // attributes belong to the function, once per process
+  if (done) return;
+  allow_smem(k_rate_team<VT, 1, 8>);
+  allow_smem(k_rate_team<VT, 2, 4>);
+  allow_smem(k_rate_team<VT, 8, 1>);
+  allow_smem(k_rate_dense<VT>);
+  done = true;
+}
+
+struct SplitPlan {
+  std::vector<int32_t> lo, hi;          // class-3 node range of every sub-round (in split order)
+  std::vector<int32_t> item_lo, item_hi;
+  std::vector<int64_t> tab_lo;          // first table entry of every sub-round
+  int64_t tab_span = 0;                 // largest table footprint of one sub-round
+  const int32_t* split = nullptr;
+  DBuf<int32_t> item_node, item_off, tnused;
+  DBuf<int64_t> tab_off, tab_cap;
+  DBuf<int8_t> tab_dense;
+  DBuf<int32_t> tkey, tused;
+  DBuf<unsigned char> tval;
+};
+
+template <typename VT, int TW, int TEAMS>
+void launch_team(const Ctx& cx, const RateArgs& A, uint32_t slots) {
+  using H = typename HashOf<VT>::type;
+  const size_t bytes = (size_t)TEAMS * slots * H::BYTES_PER_SLOT;
+  const int per_sm = std::max<int>(1, (int)(SMEM_BUDGET / bytes));
+  k_rate_team<VT, TW, TEAMS><<<grid_for(A.count, TEAMS, cx.num_sms, per_sm), TW * 32 * TEAMS,
+                               bytes, cx.stream>>>(A, slots);
+}
+
+template <typename VT>
+void rate_subround(const Ctx& cx, RateArgs A, const std::vector<int32_t>& hoff, const int32_t* list,
+                   int S, int s, bool dense_block, SplitPlan& sp, KernelTimer& timer,
+                   CoarsenCounters& cc) {
+  set_rate_attrs<VT>();
+  for (int cls = 0; cls < 3; ++cls) {
+    A.count = hoff[cls * S + s + 1] - hoff[cls * S + s];
+    A.list = list + hoff[cls * S + s];
+    if (A.count == 0) continue;
+    timer.begin();
+    if (cls == 0) {
+      launch_team<VT, 1, 8>(cx, A, 2 * D_WARP);
+    } else if (cls == 1) {
+      launch_team<VT, 2, 4>(cx, A, 2 * D_PAIR);
+    } else if (dense_block) {
+      const size_t bytes = (size_t)std::max<int32_t>(A.n, 1) * (sizeof(VT) + 4);
+      const int per_sm = std::max<int>(1, (int)(SMEM_BUDGET / bytes));
+      k_rate_dense<VT><<<grid_for(A.count, 1, cx.num_sms, per_sm), 256, bytes, cx.stream>>>(A);
+    } else {
+      launch_team<VT, 8, 1>(cx, A, 2 * D_BLOCK);
+    }
+    timer.end();
+    check_launch("rate_team");
+    cc.rating_launches += 1;
+  }
+  // class 3
+  if (sp.hi[s] > sp.lo[s]) {
+    const int32_t items = sp.item_hi[s] - sp.item_lo[s];
+    VT* tval = reinterpret_cast<VT*>(sp.tval.p);
+    timer.begin();
+    if (items > 0) {
+      const int g = grid_for(items, SPLIT_WARPS, cx.num_sms, 16);
+      k_rate_split_acc<VT><<<g, SPLIT_WARPS * 32, 0, cx.stream>>>(
+          A, sp.split, sp.item_node.p, sp.item_off.p, sp.tab_off.p, sp.tab_cap.p, sp.tab_dense.p,
+          sp.item_lo[s], sp.item_hi[s], sp.tab_lo[s], sp.tkey.p, tval, sp.tused.p, sp.tnused.p);
+      check_launch("rate_split_acc");
+    }
+    const int g2 = grid_for(sp.hi[s] - sp.lo[s], 1, cx.num_sms, 8);
+    k_rate_split_argmax<VT><<<g2, ARGMAX_THREADS, 0, cx.stream>>>(
+        A, sp.split, sp.lo[s], sp.hi[s], sp.tab_off.p, sp.tab_dense.p, sp.tab_lo[s], sp.tkey.p, tval,
+        sp.tused.p, sp.tnused.p);
+    timer.end();
+    check_launch("rate_split_argmax");
+    cc.rating_launches += 2;
   }
 }
 
@@ -610,12 +1014,12 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   const int nkeys = S * NCLASS;
   L.rep.alloc(&cx.alloc, (size_t)n);
   cw_out.alloc(&cx.alloc, (size_t)n);
-  DBuf<uint8_t> joined;
+  DBuf<int2> cst;
   DBuf<int32_t> target, gw, gcnt, slot_of, slot_c, slot_off, slot_fill, mv, touched, glist, key_of,
-      kcount, kfill, list, words, clusters, max_big;
-  DBuf<unsigned long long> stats;
+      wof, kcount, kfill, list, words, clusters, rpin, dirty, dlist;
+  DBuf<unsigned long long> stats, max_r;
   const size_t ncap = (size_t)n + 1;
-  joined.alloc(&cx.alloc, ncap);
+  cst.alloc(&cx.alloc, ncap);
   target.alloc(&cx.alloc, ncap);
   gw.alloc(&cx.alloc, ncap);
   gcnt.alloc(&cx.alloc, ncap);
@@ -627,28 +1031,41 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   touched.alloc(&cx.alloc, ncap);
   glist.alloc(&cx.alloc, ncap);
   key_of.alloc(&cx.alloc, ncap);
+  wof.alloc(&cx.alloc, ncap);
   list.alloc(&cx.alloc, ncap);
   kcount.alloc(&cx.alloc, (size_t)nkeys);
   kfill.alloc(&cx.alloc, (size_t)nkeys);
   words.alloc(&cx.alloc, (size_t)S * CW_WORDS);
   clusters.alloc(&cx.alloc, 1);
-  max_big.alloc(&cx.alloc, 1);
+  max_r.alloc(&cx.alloc, 1);
   stats.alloc(&cx.alloc, ST_WORDS);
+  rpin.alloc(&cx.alloc, (size_t)std::max<int64_t>(L.p, 1));
+  dirty.alloc(&cx.alloc, (size_t)L.m + 1);
+  dlist.alloc(&cx.alloc, (size_t)L.m + 1);
   HG_CUDA(cudaMemsetAsync(gw.p, 0, gw.bytes(), cx.stream));
   HG_CUDA(cudaMemsetAsync(gcnt.p, 0, gcnt.bytes(), cx.stream));
   HG_CUDA(cudaMemsetAsync(slot_fill.p, 0, slot_fill.bytes(), cx.stream));
   HG_CUDA(cudaMemsetAsync(kcount.p, 0, kcount.bytes(), cx.stream));
   HG_CUDA(cudaMemsetAsync(kfill.p, 0, kfill.bytes(), cx.stream));
   HG_CUDA(cudaMemsetAsync(words.p, 0, words.bytes(), cx.stream));
-  HG_CUDA(cudaMemsetAsync(max_big.p, 0, max_big.bytes(), cx.stream));
+  HG_CUDA(cudaMemsetAsync(max_r.p, 0, max_r.bytes(), cx.stream));
   HG_CUDA(cudaMemsetAsync(stats.p, 0, stats.bytes(), cx.stream));
+  HG_CUDA(cudaMemsetAsync(dirty.p, 0, dirty.bytes(), cx.stream));
   HG_CUDA(cudaMemcpyAsync(clusters.p, &n, sizeof(int32_t), cudaMemcpyHostToDevice, cx.stream));
+  if (L.p > 0)
+    HG_CUDA(cudaMemcpyAsync(rpin.p, L.pins.p, sizeof(int32_t) * (size_t)L.p,
+                            cudaMemcpyDeviceToDevice, cx.stream));
 
+  // block tables are direct-indexed when the level is small enough for the
+  // wider (64-bit) values, so the choice does not depend on the value width
+  const bool dense_block = (size_t)n * 12 <= SMEM_BUDGET;
   const int g_nodes = grid_for(n, 256, cx.num_sms, 4);
-  k_init_cluster<<<g_nodes, 256, 0, cx.stream>>>(L.c.p, n, L.rep.p, cw_out.p, joined.p, slot_of.p);
+  k_init_cluster<<<g_nodes, 256, 0, cx.stream>>>(L.c.p, n, P.seed, P.level, S, L.rep.p, cst.p,
+                                                 slot_of.p);
   check_launch("init_cluster");
-  k_node_work<<<g_nodes, 256, 0, cx.stream>>>(L.ioff.p, L.inets.p, L.eoff.p, n, P.T, P.seed,
-                                               P.level, S, key_of.p, kcount.p, max_big.p);
+  k_node_work<<<g_nodes, 256, 0, cx.stream>>>(L.ioff.p, L.inets.p, L.eoff.p, L.w.p, n, P.T, P.seed,
+                                               P.level, S, dense_block, key_of.p, wof.p, kcount.p,
+                                               max_r.p);
   check_launch("node_work");
   k_node_scatter<<<g_nodes, 256, nkeys * sizeof(int32_t), cx.stream>>>(key_of.p, n, nkeys,
                                                                         kcount.p, kfill.p, list.p);
@@ -658,58 +1075,109 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   std::vector<int32_t> hcount(nkeys);
   HG_CUDA(cudaMemcpyAsync(hcount.data(), kcount.p, sizeof(int32_t) * nkeys, cudaMemcpyDeviceToHost,
                           cx.stream));
-  const int32_t maxW = read_i32(cx, max_big.p);
+  const unsigned long long hmax_r = (unsigned long long)read_i64(cx, (const int64_t*)max_r.p);
   std::vector<int32_t> hoff(nkeys + 1, 0);
   for (int i = 0; i < nkeys; ++i) hoff[i + 1] = hoff[i] + hcount[i];
-  int32_t big_max_count = 0;
-  for (int s = 0; s < S; ++s) big_max_count = std::max(big_max_count, hcount[s * NCLASS + 2]);
+  // 32-bit rating words when no node's total rating can reach 2^31
+  const bool narrow = hmax_r < (1ull << 31);
+  const size_t vbytes = narrow ? 4 : 8;
 
-  // global tables for the largest nodes: one per block, sized for maxW
-  DBuf<int32_t> gkey, gused, gnused;
-  DBuf<unsigned long long> gclaim;
-  DBuf<long long> gval;
-  uint32_t gcap = 0;
-  int g_big = 0;
-  if (big_max_count > 0) {
-    const int64_t want = 2 * (int64_t)std::min<int64_t>(maxW, n) + 2;
-    gcap = 1;
-    while ((int64_t)gcap < want) gcap <<= 1;
-    // at most ~1 GiB of tables; at least one block
-    const int64_t per = (int64_t)gcap * 24;
-    int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)cx.num_sms, (1ll << 30) / per));
-    blocks = std::min<int64_t>(blocks, big_max_count);
-    g_big = (int)blocks;
-    gkey.alloc(&cx.alloc, (size_t)g_big * gcap);
-    gclaim.alloc(&cx.alloc, (size_t)g_big * gcap);
-    gval.alloc(&cx.alloc, (size_t)g_big * gcap);
-    gused.alloc(&cx.alloc, (size_t)g_big * gcap);
-    gnused.alloc(&cx.alloc, (size_t)g_big);
-    HG_CUDA(cudaMemsetAsync(gnused.p, 0, gnused.bytes(), cx.stream));
-    k_init_table<<<grid_for((int64_t)g_big * gcap, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(
-        gkey.p, gclaim.p, gval.p, (size_t)g_big * gcap);
-    check_launch("init_table");
+  // ---- class 3 plan: items, table offsets and footprint per sub-round
+  SplitPlan sp;
+  sp.lo.resize(S);
+  sp.hi.resize(S);
+  sp.item_lo.assign(S, 0);
+  sp.item_hi.assign(S, 0);
+  sp.tab_lo.assign(S, 0);
+  const int32_t split_base = hoff[3 * S];
+  const int32_t nsplit = hoff[4 * S] - split_base;
+  for (int s = 0; s < S; ++s) {
+    sp.lo[s] = hoff[3 * S + s] - split_base;
+    sp.hi[s] = hoff[3 * S + s + 1] - split_base;
   }
-  static bool attr_done = false;
-  const size_t cta_smem = (size_t)CTA_TABLE * (8 + 8 + 4);
-  if (!attr_done) {
-    HG_CUDA(cudaFuncSetAttribute(k_rate_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)cta_smem));
-    attr_done = true;
+  sp.split = list.p + split_base;
+  if (nsplit > 0) {
+    DBuf<int32_t> items, cap32;
+    items.alloc(&cx.alloc, (size_t)nsplit + 1);
+    cap32.alloc(&cx.alloc, (size_t)nsplit + 1);
+    sp.item_off.alloc(&cx.alloc, (size_t)nsplit + 1);
+    sp.tab_off.alloc(&cx.alloc, (size_t)nsplit + 1);
+    sp.tab_cap.alloc(&cx.alloc, (size_t)nsplit + 1);
+    sp.tab_dense.alloc(&cx.alloc, (size_t)nsplit + 1);
+    sp.tnused.alloc(&cx.alloc, (size_t)nsplit + 1);
+    HG_CUDA(cudaMemsetAsync(sp.tnused.p, 0, sp.tnused.bytes(), cx.stream));
+    const int gs = grid_for(nsplit, 256, cx.num_sms, 4);
+    k_split_sizes<<<gs, 256, 0, cx.stream>>>(sp.split, nsplit, L.ioff.p, wof.p, n, items.p,
+                                             cap32.p, sp.tab_dense.p);
+    check_launch("split_sizes");
+    scan_exclusive_i32(cx, items.p, sp.item_off.p, nsplit, sp.item_off.p + nsplit);
+    scan_exclusive_i32_to_i64(cx, cap32.p, sp.tab_off.p, nsplit, sp.tab_off.p + nsplit);
+    k_widen<<<gs, 256, 0, cx.stream>>>(cap32.p, sp.tab_cap.p, nsplit);
+    check_launch("widen");
+    std::vector<int32_t> hio((size_t)nsplit + 1);
+    std::vector<int64_t> hto((size_t)nsplit + 1);
+    HG_CUDA(cudaMemcpyAsync(hio.data(), sp.item_off.p, sizeof(int32_t) * hio.size(),
+                            cudaMemcpyDeviceToHost, cx.stream));
+    HG_CUDA(cudaMemcpyAsync(hto.data(), sp.tab_off.p, sizeof(int64_t) * hto.size(),
+                            cudaMemcpyDeviceToHost, cx.stream));
+    check_status(cx);
+    for (int s = 0; s < S; ++s) {
+      sp.item_lo[s] = hio[sp.lo[s]];
+      sp.item_hi[s] = hio[sp.hi[s]];
+      sp.tab_lo[s] = hto[sp.lo[s]];
+      sp.tab_span = std::max<int64_t>(sp.tab_span, hto[sp.hi[s]] - hto[sp.lo[s]]);
+    }
+    sp.item_node.alloc(&cx.alloc, (size_t)std::max<int32_t>(hio[nsplit], 1));
+    k_split_items<<<gs, 256, 0, cx.stream>>>(sp.item_off.p, nsplit, sp.item_node.p);
+    check_launch("split_items");
+    const size_t span = (size_t)std::max<int64_t>(sp.tab_span, 1);
+    sp.tval.alloc(&cx.alloc, span * vbytes);
+    sp.tkey.alloc(&cx.alloc, span);
+    sp.tused.alloc(&cx.alloc, span);
+    const int gi = grid_for((int64_t)span, 256, cx.num_sms, 8);
+    if (narrow)
+      k_init_table<uint32_t><<<gi, 256, 0, cx.stream>>>(
+          sp.tkey.p, reinterpret_cast<uint32_t*>(sp.tval.p), span);
+    else
+      k_init_table<unsigned long long><<<gi, 256, 0, cx.stream>>>(
+          sp.tkey.p, reinterpret_cast<unsigned long long*>(sp.tval.p), span);
+    check_launch("init_table");
+    if (cx.launches) *cx.launches += 10;
+  }
+
+  // global sets for the rpin refresh of nets above 1024 pins (only with T > 1024)
+  DBuf<unsigned long long> rset;
+  uint32_t rcap = 0;
+  const int g_refresh = cx.num_sms * 3;
+  const size_t refresh_smem = (size_t)REFRESH_WARPS * 2 * REFRESH_SET * sizeof(unsigned long long);
+  {
+    static bool attr = false;
+    if (!attr) {
+      HG_CUDA(cudaFuncSetAttribute(k_refresh_rpin, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)refresh_smem));
+      attr = true;
+    }
+  }
+  if (P.T > REFRESH_SET / 2) {
+    rcap = 1;
+    while (rcap < 2u * (uint32_t)P.T) rcap <<= 1;
+    const size_t cnt = (size_t)g_refresh * REFRESH_WARPS * 2 * rcap;
+    rset.alloc(&cx.alloc, cnt);
+    // key halves 0 (generation 0 is never used), position halves all ones
+    const size_t per = 2 * (size_t)rcap;
+    HG_CUDA(cudaMemsetAsync(rset.p, 0xff, rset.bytes(), cx.stream));
+    for (size_t wv = 0; wv < (size_t)g_refresh * REFRESH_WARPS; ++wv)
+      HG_CUDA(cudaMemsetAsync(rset.p + wv * per, 0, rcap * sizeof(unsigned long long), cx.stream));
   }
 
   RateArgs A;
   A.ioff = L.ioff.p;
   A.inets = L.inets.p;
   A.eoff = L.eoff.p;
-  A.pins = L.pins.p;
+  A.rpin = rpin.p;
   A.w = L.w.p;
   A.c = L.c.p;
-  A.rep = L.rep.p;
-  A.cw = cw_out.p;
-  A.joined = joined.p;
-  A.seed = P.seed;
-  A.level = P.level;
-  A.S = S;
+  A.cst = cst.p;
   A.T = P.T;
   A.c_max = P.c_max;
   A.n = n;
@@ -718,9 +1186,9 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   A.gw = gw.p;
   A.gcnt = gcnt.p;
   A.mv = mv.p;
-  A.touched = touched.p;
+  A.touched_targets = touched.p;
   A.stats = stats.p;
-  A.status = cx.d_status;
+  A.status_word = cx.d_status;
 
   KernelTimer rate_timer(cx);
   for (int s = 0; s < S; ++s) {
@@ -729,48 +1197,49 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
     int32_t* w_s = words.p + (size_t)s * CW_WORDS;
     {
       EventTimer tm(cx, &cc.ms_rating);
-      for (int cls = 0; cls < NCLASS; ++cls) {
-        const int key = s * NCLASS + cls;
-        A.count = hcount[key];
-        if (A.count == 0) continue;
-        A.list = list.p + hoff[key];
-        rate_timer.begin();
-        if (cls == 0) {
-          k_rate_warp<<<grid_for(A.count, RATE_WARPS, cx.num_sms, 8), RATE_WARPS * 32, 0,
-                        cx.stream>>>(A);
-        } else if (cls == 1) {
-          k_rate_cta<<<grid_for(A.count, 1, cx.num_sms, 2), CTA_THREADS, cta_smem, cx.stream>>>(A);
-        } else {
-          k_rate_big<<<std::min<int>(g_big, A.count), BIG_THREADS, 0, cx.stream>>>(
-              A, gkey.p, gclaim.p, gval.p, gused.p, gnused.p, gcap);
-        }
-        rate_timer.end();
-        check_launch("rate");
-        cc.rating_launches += 1;
-        if (cx.launches) *cx.launches += 1;
-      }
+      const int64_t before = cc.rating_launches;
+      if (narrow)
+        rate_subround<uint32_t>(cx, A, hoff, list.p, S, s, dense_block, sp, rate_timer, cc);
+      else
+        rate_subround<unsigned long long>(cx, A, hoff, list.p, S, s, dense_block, sp, rate_timer,
+                                          cc);
+      if (cx.launches) *cx.launches += cc.rating_launches - before;
     }
     {
       EventTimer tm(cx, &cc.ms_approve);
       const int g = grid_for((n + S - 1) / S, 256, cx.num_sms, 4);
-      k_approve<<<g, 256, 0, cx.stream>>>(mv.p, w_s, target.p, cw_out.p, gw.p, gcnt.p, P.c_max,
-                                          L.rep.p, joined.p, slot_of.p, slot_c.p, slot_off.p,
+      k_approve<<<g, 256, 0, cx.stream>>>(mv.p, w_s, target.p, cst.p, gw.p, gcnt.p, P.c_max,
+                                          L.rep.p, slot_of.p, slot_c.p, slot_off.p,
                                           w_s + CW_SLOTS, w_s + CW_CURSOR);
       check_launch("approve");
-      k_contest_scatter<<<g, 256, 0, cx.stream>>>(mv.p, w_s, target.p, cw_out.p, gw.p, P.c_max,
+      k_contest_scatter<<<g, 256, 0, cx.stream>>>(mv.p, w_s, target.p, cst.p, gw.p, P.c_max,
                                                   slot_of.p, slot_off.p, slot_fill.p, glist.p);
       check_launch("contest_scatter");
       k_contest_group<<<cx.num_sms, GROUP_THREADS, 0, cx.stream>>>(
           w_s, slot_c.p, slot_off.p, slot_fill.p, slot_of.p, glist.p, gcnt.p, L.c.p, P.c_max,
-          cw_out.p, L.rep.p, joined.p, clusters.p);
+          cst.p, L.rep.p, clusters.p);
       check_launch("contest_group");
-      k_finish<<<g, 256, 0, cx.stream>>>(touched.p, w_s, P.c_max, cw_out.p, gw.p, gcnt.p,
-                                         joined.p, clusters.p);
+      k_finish<<<g, 256, 0, cx.stream>>>(touched.p, w_s, P.c_max, cst.p, gw.p, gcnt.p, clusters.p);
       check_launch("finish");
       if (cx.launches) *cx.launches += 4;
     }
+    if (s + 1 < S) {
+      EventTimer tm(cx, &cc.ms_refresh);
+      k_mark_dirty<<<grid_for((n + S - 1) / S, 8, cx.num_sms, 8), 256, 0, cx.stream>>>(
+          mv.p, w_s, L.rep.p, L.ioff.p, L.inets.p, L.eoff.p, P.T, dirty.p, dlist.p,
+          w_s + CW_DIRTY);
+      check_launch("mark_dirty");
+      k_refresh_rpin<<<g_refresh, REFRESH_WARPS * 32, refresh_smem, cx.stream>>>(
+          dlist.p, w_s + CW_DIRTY, L.eoff.p, L.pins.p, L.rep.p, dirty.p, rpin.p, rset.p, rcap,
+          cx.d_status);
+      check_launch("refresh_rpin");
+      if (cx.launches) *cx.launches += 2;
+    }
   }
   cc.ms_rating_kernels += rate_timer.flush();
+  // cluster weights for the contraction (valid at representatives)
+  HG_CUDA(cudaMemcpy2DAsync(cw_out.p, sizeof(int32_t), cst.p, sizeof(int2), sizeof(int32_t),
+                            (size_t)n, cudaMemcpyDeviceToDevice, cx.stream));
   unsigned long long hs[ST_WORDS];
   HG_CUDA(cudaMemcpyAsync(hs, stats.p, sizeof(hs), cudaMemcpyDeviceToHost, cx.stream));
   check_status(cx);

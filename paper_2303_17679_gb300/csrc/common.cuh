@@ -269,7 +269,7 @@ struct CoarsenParams {
 
 struct CoarsenCounters {
   int64_t rating_launches = 0, rating_pin_visits = 0, rating_nodes = 0, rating_incidences = 0;
-  double ms_rating = 0, ms_approve = 0, ms_rating_kernels = 0;
+  double ms_rating = 0, ms_approve = 0, ms_refresh = 0, ms_rating_kernels = 0;
 };
 
 // Deterministic clustering of level L: fills L.rep (representatives) and

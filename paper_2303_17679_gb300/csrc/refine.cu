@@ -92,22 +92,33 @@ __global__ void k_objective(const unsigned long long* __restrict__ lam,
 
 // -------------------------------------------- sub-round node lists (a11)
 
+// Nodes of a pass are listed by key = sub-round * 2 + class, class 1 for
+// nodes with more than GAIN_BLOCK_DEG incident nets (a block per node).
+constexpr int GAIN_BLOCK_DEG = 64;
+
+__device__ __forceinline__ int lp_key(const int32_t* ioff, uint64_t seed, int level, int pass,
+                                      int64_t u, int S) {
+  const int32_t deg = ioff[u + 1] - ioff[u];
+  if (deg == 0) return -1;  // isolated nodes never move
+  return subround_of_node_lp(seed, level, pass, (int)u, S) * 2 + (deg > GAIN_BLOCK_DEG ? 1 : 0);
+}
+
 __global__ void k_lp_count(const int32_t* __restrict__ ioff, int32_t n, uint64_t seed, int level,
                            int pass, int S, int32_t* __restrict__ cnt) {
   extern __shared__ int32_t s_cnt[];
-  for (int i = threadIdx.x; i < S; i += blockDim.x) s_cnt[i] = 0;
+  for (int i = threadIdx.x; i < 2 * S; i += blockDim.x) s_cnt[i] = 0;
   __syncthreads();
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
        u += (int64_t)gridDim.x * blockDim.x) {
-    if (ioff[u + 1] == ioff[u]) continue;  // isolated nodes never move
-    atomicAdd(&s_cnt[subround_of_node_lp(seed, level, pass, (int)u, S)], 1);
+    const int key = lp_key(ioff, seed, level, pass, u, S);
+    if (key >= 0) atomicAdd(&s_cnt[key], 1);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < S; i += blockDim.x)
+  for (int i = threadIdx.x; i < 2 * S; i += blockDim.x)
     if (s_cnt[i]) atomicAdd(&cnt[i], s_cnt[i]);
 }
 
-// Every block recomputes the (tiny) exclusive scan of the S counts.
+// Every block recomputes the (tiny) exclusive scan of the 2S counts.
 __global__ void k_lp_scatter(const int32_t* __restrict__ ioff, int32_t n, uint64_t seed, int level,
                              int pass, int S, const int32_t* __restrict__ cnt,
                              int32_t* __restrict__ fill, int32_t* __restrict__ off,
@@ -115,20 +126,19 @@ __global__ void k_lp_scatter(const int32_t* __restrict__ ioff, int32_t n, uint64
   extern __shared__ int32_t s_off[];
   if (threadIdx.x == 0) {
     int32_t run = 0;
-    for (int i = 0; i < S; ++i) {
+    for (int i = 0; i < 2 * S; ++i) {
       s_off[i] = run;
       run += cnt[i];
     }
-    s_off[S] = run;
+    s_off[2 * S] = run;
     if (blockIdx.x == 0)
-      for (int i = 0; i <= S; ++i) off[i] = s_off[i];
+      for (int i = 0; i <= 2 * S; ++i) off[i] = s_off[i];
   }
   __syncthreads();
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
        u += (int64_t)gridDim.x * blockDim.x) {
-    if (ioff[u + 1] == ioff[u]) continue;
-    const int s = subround_of_node_lp(seed, level, pass, (int)u, S);
-    list[s_off[s] + atomicAdd(&fill[s], 1)] = (int32_t)u;
+    const int key = lp_key(ioff, seed, level, pass, u, S);
+    if (key >= 0) list[s_off[key] + atomicAdd(&fill[key], 1)] = (int32_t)u;
   }
 }
 
@@ -137,82 +147,166 @@ enum SubroundWord { SW_MOVES = 0, SW_APPROVED = 1, SW_WORDS = 4 };
 
 // ------------------------------------------------- best moves (a11)
 
-// One warp per node u of the sub-round.  With b(u) = w(nets where u is the
-// only pin of its block) and W_I = w(I(u)), the gain of Sec. 6 is
+// With b(u) = w(nets where u is the only pin of its block) and W_I = w(I(u)),
+// the gain of Sec. 6 is
 //   g(u, t) = b(u) - W_I + w({e in I(u) : t in Lambda(e)}),
 // evaluated for all t at once: lane L accumulates blocks L and L + 32 while
-// the warp broadcasts each incident net's (weight, Lambda) in turn.  The
-// best t != Pi[u] by (gain desc, t asc) is proposed if its gain is positive.
-__global__ void __launch_bounds__(WARPS * 32)
-k_lp_gain(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
-          const int32_t* __restrict__ w, const int32_t* __restrict__ phi,
-          const unsigned long long* __restrict__ lam, const int32_t* __restrict__ part, int k,
-          const int32_t* __restrict__ list, const int32_t* __restrict__ sr_off, int s,
-          int32_t* __restrict__ mv_u, int32_t* __restrict__ mv_to, long long* __restrict__ mv_g,
-          int32_t* __restrict__ dcount, int32_t* __restrict__ words,
-          unsigned long long* __restrict__ work) {
+// the warp broadcasts each incident net's (weight, Lambda) in turn.  A warp
+// handles the chunks c0 = beg + 32 * (first + i * stride) of I(u).
+struct GainPart {
+  long long acc0, acc1, ben, wsum;
+};
+
+__device__ __forceinline__ GainPart gain_partial(const int32_t* __restrict__ inets,
+                                                 const int32_t* __restrict__ w,
+                                                 const int32_t* __restrict__ phi,
+                                                 const unsigned long long* __restrict__ lam, int k,
+                                                 int from, int32_t beg, int32_t end, int first,
+                                                 int stride) {
   const int lane = lane_id();
-  const int32_t lo = sr_off[s], hi = sr_off[s + 1];
-  int64_t incid = 0;
-  for (int32_t i = lo + blockIdx.x * WARPS + warp_in_block(); i < hi; i += gridDim.x * WARPS) {
-    const int32_t u = list[i];
-    const int from = part[u];
-    const int32_t beg = ioff[u], end = ioff[u + 1];
-    int64_t acc0 = 0, acc1 = 0, ben = 0, wsum = 0;
-    for (int32_t c0 = beg; c0 < end; c0 += 32) {
-      const int32_t j = c0 + lane;
-      int32_t we = 0;
-      unsigned long long le = 0;
-      if (j < end) {
-        const int32_t e = inets[j];
-        we = w[e];
-        le = lam[e];
-        if (phi[(int64_t)e * k + from] == 1) ben += we;
-        wsum += we;
-      }
-      const int cnt = min(32, end - c0);
-      for (int jj = 0; jj < cnt; ++jj) {
-        const int32_t wj = __shfl_sync(FULL, we, jj);
-        const unsigned long long lj = __shfl_sync(FULL, le, jj);
-        if ((lj >> lane) & 1ull) acc0 += wj;
-        if ((lj >> (lane + 32)) & 1ull) acc1 += wj;
-      }
+  GainPart g{0, 0, 0, 0};
+  for (int32_t c0 = beg + 32 * first; c0 < end; c0 += 32 * stride) {
+    const int32_t j = c0 + lane;
+    int32_t we = 0;
+    unsigned long long le = 0;
+    if (j < end) {
+      const int32_t e = inets[j];
+      we = w[e];
+      le = lam[e];
+      if (phi[(int64_t)e * k + from] == 1) g.ben += we;
+      g.wsum += we;
     }
-    incid += end - beg;
-    ben = warp_sum(ben);
-    wsum = warp_sum(wsum);
-    // candidate value: (gain, -t) packed so that a max picks the smaller t on ties
-    long long best_g = LLONG_MIN;
-    int best_t = -1;
-    if (lane < k && lane != from) {
-      best_g = ben - wsum + acc0;
-      best_t = lane;
-    }
-    if (lane + 32 < k && lane + 32 != from) {
-      const long long g1 = ben - wsum + acc1;
-      if (g1 > best_g) {
-        best_g = g1;
-        best_t = lane + 32;
-      }
-    }
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-      const long long og = __shfl_xor_sync(FULL, best_g, d);
-      const int ot = __shfl_xor_sync(FULL, best_t, d);
-      if (og > best_g || (og == best_g && ot >= 0 && (best_t < 0 || ot < best_t))) {
-        best_g = og;
-        best_t = ot;
-      }
-    }
-    if (lane == 0 && best_g > 0) {
-      const int32_t slot = atomicAdd(&words[SW_MOVES], 1);
-      mv_u[slot] = u;
-      mv_to[slot] = best_t;
-      mv_g[slot] = best_g;
-      atomicAdd(&dcount[from * k + best_t], 1);
+    const int cnt = min(32, end - c0);
+    for (int jj = 0; jj < cnt; ++jj) {
+      const int32_t wj = __shfl_sync(FULL, we, jj);
+      const unsigned long long lj = __shfl_sync(FULL, le, jj);
+      if ((lj >> lane) & 1ull) g.acc0 += wj;
+      if ((lj >> (lane + 32)) & 1ull) g.acc1 += wj;
     }
   }
-  if (lane == 0 && incid) atomicAdd(work, (unsigned long long)incid);
+  return g;
+}
+
+// Best target of the warp's complete accumulators: (gain desc, t asc), t != from.
+__device__ __forceinline__ void gain_best(const GainPart& g, int k, int from, long long& best_g,
+                                          int& best_t) {
+  const int lane = lane_id();
+  const long long ben = warp_sum(g.ben), wsum = warp_sum(g.wsum);
+  best_g = LLONG_MIN;
+  best_t = -1;
+  if (lane < k && lane != from) {
+    best_g = ben - wsum + g.acc0;
+    best_t = lane;
+  }
+  if (lane + 32 < k && lane + 32 != from) {
+    const long long g1 = ben - wsum + g.acc1;
+    if (g1 > best_g) {
+      best_g = g1;
+      best_t = lane + 32;
+    }
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    const long long og = __shfl_xor_sync(FULL, best_g, d);
+    const int ot = __shfl_xor_sync(FULL, best_t, d);
+    if (og > best_g || (og == best_g && ot >= 0 && (best_t < 0 || ot < best_t))) {
+      best_g = og;
+      best_t = ot;
+    }
+  }
+}
+
+struct GainArgs {
+  const int32_t* ioff;
+  const int32_t* inets;
+  const int32_t* w;
+  const int32_t* phi;
+  const unsigned long long* lam;
+  const int32_t* part;
+  int k;
+  const int32_t* list;
+  const int32_t* sr_off;
+  int s;
+  int32_t* mv_u;
+  int32_t* mv_to;
+  long long* mv_g;
+  int32_t* dcount;
+  int32_t* words;
+  unsigned long long* work;
+};
+
+__device__ __forceinline__ void gain_emit(const GainArgs& A, int32_t u, int from, long long g,
+                                          int t) {
+  if (g > 0) {
+    const int32_t slot = atomicAdd(&A.words[SW_MOVES], 1);
+    A.mv_u[slot] = u;
+    A.mv_to[slot] = t;
+    A.mv_g[slot] = g;
+    atomicAdd(&A.dcount[from * A.k + t], 1);
+  }
+}
+
+// class 0 (at most GAIN_BLOCK_DEG incident nets): one warp per node
+__global__ void __launch_bounds__(WARPS * 32) k_lp_gain_warp(GainArgs A) {
+  const int lane = lane_id();
+  const int32_t lo = A.sr_off[2 * A.s], hi = A.sr_off[2 * A.s + 1];
+  int64_t incid = 0;
+  for (int32_t i = lo + blockIdx.x * WARPS + warp_in_block(); i < hi; i += gridDim.x * WARPS) {
+    const int32_t u = A.list[i];
+    const int from = A.part[u];
+    const int32_t beg = A.ioff[u], end = A.ioff[u + 1];
+    const GainPart g = gain_partial(A.inets, A.w, A.phi, A.lam, A.k, from, beg, end, 0, 1);
+    long long bg;
+    int bt;
+    gain_best(g, A.k, from, bg, bt);
+    if (lane == 0) gain_emit(A, u, from, bg, bt);
+    incid += end - beg;
+  }
+  if (lane == 0 && incid) atomicAdd(A.work, (unsigned long long)incid);
+}
+
+// class 1: one block (WARPS warps) per node; the warps split I(u) and their
+// partial accumulators are summed in shared memory before the argmax
+__global__ void __launch_bounds__(WARPS * 32) k_lp_gain_block(GainArgs A) {
+  __shared__ long long s_acc[WARPS][64];
+  __shared__ long long s_bw[WARPS][2];
+  const int lane = lane_id(), wv = warp_in_block();
+  const int32_t lo = A.sr_off[2 * A.s + 1], hi = A.sr_off[2 * A.s + 2];
+  int64_t incid = 0;
+  for (int32_t i = lo + blockIdx.x; i < hi; i += gridDim.x) {
+    const int32_t u = A.list[i];
+    const int from = A.part[u];
+    const int32_t beg = A.ioff[u], end = A.ioff[u + 1];
+    GainPart g = gain_partial(A.inets, A.w, A.phi, A.lam, A.k, from, beg, end, wv, WARPS);
+    s_acc[wv][lane] = g.acc0;
+    s_acc[wv][lane + 32] = g.acc1;
+    const long long b = warp_sum(g.ben), ws = warp_sum(g.wsum);
+    if (lane == 0) {
+      s_bw[wv][0] = b;
+      s_bw[wv][1] = ws;
+    }
+    __syncthreads();
+    if (wv == 0) {
+      GainPart t{0, 0, 0, 0};
+      for (int x = 0; x < WARPS; ++x) {
+        t.acc0 += s_acc[x][lane];
+        t.acc1 += s_acc[x][lane + 32];
+      }
+      // ben and wsum enter gain_best through warp sums: put them on lane 0
+      if (lane == 0)
+        for (int x = 0; x < WARPS; ++x) {
+          t.ben += s_bw[x][0];
+          t.wsum += s_bw[x][1];
+        }
+      long long bg;
+      int bt;
+      gain_best(t, A.k, from, bg, bt);
+      if (lane == 0) gain_emit(A, u, from, bg, bt);
+    }
+    __syncthreads();
+    incid += end - beg;
+  }
+  if (threadIdx.x == 0 && incid) atomicAdd(A.work, (unsigned long long)incid);
 }
 
 // ------------------------------------- pair bucketing + selection (a12)
@@ -312,7 +406,8 @@ __device__ void block_weight_prefix(const unsigned long long* keys, int cnt,
 // B[0..nb-1] (ties to A) with -slack_a <= A[i] - B[j] <= slack_b.  Moves in
 // the chosen prefixes are approved.
 __global__ void __launch_bounds__(SEL_THREADS)
-k_lp_select(const int32_t* __restrict__ bucket, const int32_t* __restrict__ doff,
+k_lp_select(const int32_t* __restrict__ ioff, const int32_t* __restrict__ bucket,
+            const int32_t* __restrict__ doff,
             const int32_t* __restrict__ dcount, const int32_t* __restrict__ mv_u,
             const int32_t* __restrict__ mv_to, const long long* __restrict__ mv_g,
             const int32_t* __restrict__ c, const long long* __restrict__ bw, long long lmax, int k,
@@ -395,24 +490,32 @@ k_lp_select(const int32_t* __restrict__ bucket, const int32_t* __restrict__ doff
     if (A[mid] <= B[r - 1 - mid]) lo = mid + 1; else hi = mid;
   }
   const int ia = lo, jb = r - lo;
+  // every approved move becomes ceil(deg/32) work items of at most 32
+  // incident nets each, so the application is balanced across warps; the
+  // item's chunk index is packed above the 6 bits of the source block
   for (int i = threadIdx.x; i < ia + jb; i += blockDim.x) {
     const bool fromA = i < ia;
     const unsigned long long key = fromA ? ka[i] : kb[i - ia];
     const int32_t u = (int32_t)(key & 0xffffffffu);
-    const int32_t slot = atomicAdd(&words[SW_APPROVED], 1);
-    ap_u[slot] = u;
-    ap_from[slot] = fromA ? a : b;
-    ap_to[slot] = fromA ? b : a;
+    const int32_t deg = ioff[u + 1] - ioff[u];
+    const int32_t nch = deg > 0 ? (deg + 31) / 32 : 1;
+    const int32_t slot = atomicAdd(&words[SW_APPROVED], nch);
+    for (int32_t ch = 0; ch < nch; ++ch) {
+      ap_u[slot + ch] = u;
+      ap_from[slot + ch] = (fromA ? a : b) | (ch << 6);
+      ap_to[slot + ch] = fromA ? b : a;
+    }
   }
 }
 
 // ------------------------------------------------------- apply (a13)
 
-// One warp per approved move (u, s, t): Pi[u] = t, block weights, and for
-// each e in I(u): Phi(e, s) -= 1, Phi(e, t) += 1, clearing bit s of Lambda(e)
-// when Phi(e, s) reaches 0 and setting bit t when Phi(e, t) leaves 0
-// (Algorithm 3's updates; the atomic xor flips commute, so the final masks
-// equal {i : Phi(e, i) > 0} whatever the order of the moves).
+// One warp per work item (u, s, t, chunk): for the <= 32 nets e of the
+// chunk: Phi(e, s) -= 1, Phi(e, t) += 1, clearing bit s of Lambda(e) when
+// Phi(e, s) reaches 0 and setting bit t when Phi(e, t) leaves 0 (Algorithm
+// 3's updates; the atomic xor flips commute, so the final masks equal
+// {i : Phi(e, i) > 0} whatever the order of the moves).  The chunk-0 item
+// also sets Pi[u] = t and moves c(u) between the block weights.
 __global__ void __launch_bounds__(WARPS * 32)
 k_lp_apply(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
            const int32_t* __restrict__ c, int k, const int32_t* __restrict__ ap_u,
@@ -421,21 +524,27 @@ k_lp_apply(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
            int32_t* __restrict__ phi, unsigned long long* __restrict__ lam,
            long long* __restrict__ bw, unsigned long long* __restrict__ moved) {
   const int32_t na = words[SW_APPROVED];
+  const int lane = lane_id();
+  unsigned long long nodes = 0;
   for (int32_t i = blockIdx.x * WARPS + warp_in_block(); i < na; i += gridDim.x * WARPS) {
     const int32_t u = ap_u[i];
-    const int s = ap_from[i], t = ap_to[i];
-    for (int32_t j = ioff[u] + lane_id(); j < ioff[u + 1]; j += 32) {
+    const int32_t fw = ap_from[i];
+    const int s = fw & 63, ch = fw >> 6, t = ap_to[i];
+    const int32_t j0 = ioff[u] + 32 * ch, j1 = min(ioff[u + 1], j0 + 32);
+    const int32_t j = j0 + lane;
+    if (j < j1) {
       const int32_t e = inets[j];
       if (atomicSub(&phi[(int64_t)e * k + s], 1) == 1) atomicXor(&lam[e], 1ull << s);
       if (atomicAdd(&phi[(int64_t)e * k + t], 1) == 0) atomicXor(&lam[e], 1ull << t);
     }
-    if (lane_id() == 0) {
+    if (ch == 0 && lane == 0) {
       part[u] = t;
       atomic_add_i64(&bw[s], -(long long)c[u]);
       atomic_add_i64(&bw[t], (long long)c[u]);
+      ++nodes;
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && na) atomicAdd(moved, (unsigned long long)na);
+  if (lane == 0 && nodes) atomicAdd(moved, nodes);
 }
 
 }  // namespace
@@ -536,17 +645,19 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   DBuf<long long> mv_g, gpre;
   DBuf<unsigned long long> gkeys, counters;
   const size_t ncap = (size_t)n + 1;
+  // work items of the application: one per 32 incident nets of a moved node
+  const size_t acap = ncap + (size_t)(L.p / 32) + 1;
   list.alloc(&cx.alloc, ncap);
-  sr_cnt.alloc(&cx.alloc, (size_t)S);
-  sr_fill.alloc(&cx.alloc, (size_t)S);
-  sr_off.alloc(&cx.alloc, (size_t)S + 1);
+  sr_cnt.alloc(&cx.alloc, (size_t)2 * S);
+  sr_fill.alloc(&cx.alloc, (size_t)2 * S);
+  sr_off.alloc(&cx.alloc, (size_t)2 * S + 1);
   mv_u.alloc(&cx.alloc, ncap);
   mv_to.alloc(&cx.alloc, ncap);
   mv_g.alloc(&cx.alloc, ncap);
   bucket.alloc(&cx.alloc, ncap);
-  ap_u.alloc(&cx.alloc, ncap);
-  ap_from.alloc(&cx.alloc, ncap);
-  ap_to.alloc(&cx.alloc, ncap);
+  ap_u.alloc(&cx.alloc, acap);
+  ap_from.alloc(&cx.alloc, acap);
+  ap_to.alloc(&cx.alloc, acap);
   gkeys.alloc(&cx.alloc, 2 * ncap + 2);
   gpre.alloc(&cx.alloc, ncap + (size_t)kk + 2);
   dcnt.alloc(&cx.alloc, (size_t)S * kk);
@@ -554,13 +665,31 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   doff.alloc(&cx.alloc, (size_t)kk + 1);
   words.alloc(&cx.alloc, (size_t)S * SW_WORDS);
   counters.alloc(&cx.alloc, 2);  // [0] moved in the pass, [1] incidences read
+  HG_CUDA(cudaMemsetAsync(counters.p, 0, counters.bytes(), cx.stream));
 
   const int nodes_per_sr = (int)((n + S - 1) / S);
   const int g_gain = grid_for(nodes_per_sr, WARPS, cx.num_sms, 16);
+  const int g_gain_block = grid_for(nodes_per_sr, 1, cx.num_sms, 8);
+  const int g_apply = grid_for((int64_t)acap / S + 1, WARPS, cx.num_sms, 16);
   const int g_bucket = grid_for(nodes_per_sr, 256, cx.num_sms, 4);
   const int g_sel = k * (k - 1) / 2;
   const int g_nodes = grid_for(n, 256, cx.num_sms, 4);
   KernelTimer gain_timer(cx);
+  // nodes above the warp class exist at this level?
+  GainArgs G;
+  G.ioff = L.ioff.p;
+  G.inets = L.inets.p;
+  G.w = L.w.p;
+  G.phi = st.phi.p;
+  G.lam = st.lam.p;
+  G.part = part;
+  G.k = k;
+  G.list = list.p;
+  G.sr_off = sr_off.p;
+  G.mv_u = mv_u.p;
+  G.mv_to = mv_to.p;
+  G.mv_g = mv_g.p;
+  G.work = counters.p + 1;
 
   for (int pass = 0; pass < max_passes; ++pass) {
     HG_CUDA(cudaMemsetAsync(sr_cnt.p, 0, sr_cnt.bytes(), cx.stream));
@@ -569,27 +698,47 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
     HG_CUDA(cudaMemsetAsync(dfill.p, 0, dfill.bytes(), cx.stream));
     HG_CUDA(cudaMemsetAsync(words.p, 0, words.bytes(), cx.stream));
     HG_CUDA(cudaMemsetAsync(counters.p, 0, sizeof(unsigned long long), cx.stream));
+    std::vector<int32_t> hcnt(2 * S);
     {
       EventTimer tm(cx, &rc.ms_gain);
-      k_lp_count<<<g_nodes, 256, S * sizeof(int32_t), cx.stream>>>(L.ioff.p, n, seed, level_index,
-                                                                  pass, S, sr_cnt.p);
+      k_lp_count<<<g_nodes, 256, 2 * S * sizeof(int32_t), cx.stream>>>(L.ioff.p, n, seed,
+                                                                      level_index, pass, S,
+                                                                      sr_cnt.p);
       check_launch("lp_count");
-      k_lp_scatter<<<g_nodes, 256, (S + 1) * sizeof(int32_t), cx.stream>>>(
+      k_lp_scatter<<<g_nodes, 256, (2 * S + 1) * sizeof(int32_t), cx.stream>>>(
           L.ioff.p, n, seed, level_index, pass, S, sr_cnt.p, sr_fill.p, sr_off.p, list.p);
       check_launch("lp_scatter");
+      HG_CUDA(cudaMemcpyAsync(hcnt.data(), sr_cnt.p, sizeof(int32_t) * 2 * S,
+                              cudaMemcpyDeviceToHost, cx.stream));
+      HG_CUDA(cudaStreamSynchronize(cx.stream));
     }
     for (int s = 0; s < S; ++s) {
       int32_t* w_s = words.p + (size_t)s * SW_WORDS;
       int32_t* dc_s = dcnt.p + (size_t)s * kk;
       int32_t* df_s = dfill.p + (size_t)s * kk;
+      G.s = s;
+      G.dcount = dc_s;
+      G.words = w_s;
       {
         EventTimer tm(cx, &rc.ms_gain);
-        gain_timer.begin();
-        k_lp_gain<<<g_gain, WARPS * 32, 0, cx.stream>>>(
-            L.ioff.p, L.inets.p, L.w.p, st.phi.p, st.lam.p, part, k, list.p, sr_off.p, s, mv_u.p,
-            mv_to.p, mv_g.p, dc_s, w_s, counters.p + 1);
-        gain_timer.end();
-        check_launch("lp_gain");
+        if (hcnt[2 * s] > 0) {
+          gain_timer.begin();
+          k_lp_gain_warp<<<grid_for(hcnt[2 * s], WARPS, cx.num_sms, 16), WARPS * 32, 0,
+                           cx.stream>>>(G);
+          gain_timer.end();
+          check_launch("lp_gain_warp");
+          rc.lp_gain_launches += 1;
+          if (cx.launches) *cx.launches += 1;
+        }
+        if (hcnt[2 * s + 1] > 0) {
+          gain_timer.begin();
+          k_lp_gain_block<<<grid_for(hcnt[2 * s + 1], 1, cx.num_sms, 8), WARPS * 32, 0,
+                            cx.stream>>>(G);
+          gain_timer.end();
+          check_launch("lp_gain_block");
+          rc.lp_gain_launches += 1;
+          if (cx.launches) *cx.launches += 1;
+        }
       }
       {
         EventTimer tm(cx, &rc.ms_select);
@@ -597,20 +746,21 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
             mv_u.p, mv_to.p, part, k, dc_s, df_s, doff.p, w_s, bucket.p);
         check_launch("lp_bucket");
         k_lp_select<<<g_sel, SEL_THREADS, 0, cx.stream>>>(
-            bucket.p, doff.p, dc_s, mv_u.p, mv_to.p, mv_g.p, L.c.p, st.bw.p, lmax, k, gkeys.p,
-            gpre.p, ap_u.p, ap_from.p, ap_to.p, w_s);
+            L.ioff.p, bucket.p, doff.p, dc_s, mv_u.p, mv_to.p, mv_g.p, L.c.p, st.bw.p, lmax, k,
+            gkeys.p, gpre.p, ap_u.p, ap_from.p, ap_to.p, w_s);
         check_launch("lp_select");
       }
       {
         EventTimer tm(cx, &rc.ms_apply);
-        k_lp_apply<<<g_gain, WARPS * 32, 0, cx.stream>>>(L.ioff.p, L.inets.p, L.c.p, k, ap_u.p,
-                                                         ap_from.p, ap_to.p, w_s, part, st.phi.p,
-                                                         st.lam.p, st.bw.p, counters.p);
+        k_lp_apply<<<g_apply, WARPS * 32, 0, cx.stream>>>(L.ioff.p, L.inets.p, L.c.p, k, ap_u.p,
+                                                          ap_from.p, ap_to.p, w_s, part, st.phi.p,
+                                                          st.lam.p, st.bw.p, counters.p);
         check_launch("lp_apply");
       }
-      rc.lp_gain_launches += 1;
-      if (cx.launches) *cx.launches += 4;
+      if (cx.launches) *cx.launches += 3;
     }
+    (void)g_gain;
+    (void)g_gain_block;
     if (cx.launches) *cx.launches += 2;
     unsigned long long hc[2];
     HG_CUDA(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, cx.stream));

@@ -53,7 +53,8 @@ class hg_stats(ctypes.Structure):
         (name, ctypes.c_int64) for name in (
             "launches", "rating_launches", "rating_pin_visits", "rating_nodes",
             "rating_incidences", "lp_incidences", "lp_nodes", "lp_gain_launches")] + [
-        ("ms_rating_kernels", ctypes.c_double), ("ms_lp_gain_kernels", ctypes.c_double)]
+        ("ms_rating_kernels", ctypes.c_double), ("ms_lp_gain_kernels", ctypes.c_double),
+        ("ms_rating_refresh", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
