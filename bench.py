@@ -237,7 +237,10 @@ def run_ours(args, world, rank, local):
         step_ms.append(e0.elapsed_time(e1))
         launches += st["launches"]
         for key, val in st.items():
-            agg[key] = agg.get(key, 0) + val
+            if isinstance(val, list):
+                agg[key] = [a + b for a, b in zip(agg.get(key, [0] * len(val)), val)]
+            else:
+                agg[key] = agg.get(key, 0) + val
         if obj is None:
             obj, levels = obj_k, lv_k
         assert obj_k == obj and lv_k == levels, "non-deterministic result"
@@ -303,12 +306,19 @@ def run_ours(args, world, rank, local):
         "phase_ms": {"rating_kernels": rating_ms / args.steps, "lp_gain_kernels": gain_ms / args.steps},
         "work_per_step": {key: int(agg[key] // args.steps) for key in (
             "rating_nodes", "rating_incidences", "rating_pin_visits", "lp_nodes", "lp_incidences")},
+        "rating_classes": [
+            {"class": c, "ms": round(agg["ms_rating_class"][c] / args.steps, 3),
+             "visits": int(agg["rating_visits_class"][c] // args.steps),
+             "Gvisits_per_s": round(agg["rating_visits_class"][c] / agg["ms_rating_class"][c] / 1e6, 2)
+             if agg["ms_rating_class"][c] > 0 else None}
+            for c in range(5)],
         "level_sizes": [list(x) for x in levels],
     }
     if args.phases:
         # one extra, untimed step with synchronizing per-phase events
         _, _, pst = step(phases=True)
-        line["phase_breakdown_ms"] = {k: round(v, 3) for k, v in pst.items() if k.startswith("ms_")}
+        line["phase_breakdown_ms"] = {k: round(v, 3) for k, v in pst.items()
+                                      if k.startswith("ms_") and not isinstance(v, list)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_sample()
         line["cpu_baseline"] = {"value": cb["value"], "unit": "pins/s", "cores": 1, "kind": "oracle",

@@ -109,6 +109,8 @@ typedef struct {
   double ms_rating_kernels;   /* sum of rating kernel durations (timing on) */
   double ms_lp_gain_kernels;  /* sum of gain kernel durations (timing on) */
   double ms_rating_refresh;   /* per-sub-round refresh of the deduplicated pin clusters */
+  double ms_rating_class[8];  /* rating kernel time per node class (timing flag 2) */
+  int64_t rating_visits_class[8]; /* pin visits per node class */
 } hg_stats;
 
 /* Fills *opt with the defaults listed above (seed 1). */

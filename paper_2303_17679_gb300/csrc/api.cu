@@ -260,6 +260,10 @@ int hg_coarsen_level(hg_t* h, int32_t k, int32_t* out_level, int32_t* out_n, int
     h->stats.ms_rating += cc.ms_rating;
     h->stats.ms_approve += cc.ms_approve;
     h->stats.ms_rating_refresh += cc.ms_refresh;
+    for (int c = 0; c < 8; ++c) {
+      h->stats.ms_rating_class[c] += cc.class_ms[c];
+      h->stats.rating_visits_class[c] += cc.class_visits[c];
+    }
     h->stats.ms_rating_kernels += cc.ms_rating_kernels;
     h->stats.rating_launches += cc.rating_launches;
     h->stats.rating_pin_visits += cc.rating_pin_visits;

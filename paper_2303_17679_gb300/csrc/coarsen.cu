@@ -20,8 +20,9 @@
 //              every repeat of a cluster inside its net replaced by -1, so a
 //              net contributes once per cluster without any per-visit check.
 //              At the start of a level every cluster is a singleton and rpin
-//              is a copy of the pins; after each sub-round only the nets of
-//              nodes that joined a cluster are recomputed.
+//              is a copy of the pins; after each sub-round the incidences of
+//              the nodes that joined a cluster update it through a map from
+//              (net, cluster) to the cluster's first pin index in the net.
 //   cst[C]   = {cw[C], status[C]}: cluster weight and status (the node's
 //              sub-round while it is unclustered, -1 once clustered), read by
 //              the rating with one 8-byte load.
@@ -45,16 +46,21 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "pintile.cuh"
 
 namespace hgk {
 
 namespace {
 
-constexpr int NCLASS = 4;
+constexpr int NCLASS = 5;
+constexpr int SPLIT_CLASS = NCLASS - 1;
 constexpr int32_t D_WARP = 256;
 constexpr int32_t D_PAIR = 1024;
 constexpr int32_t D_BLOCK = 4096;
-constexpr int32_t SPLIT_W = 16384;       // class 3 above this many pin visits
+constexpr int32_t D_WIDE = 8192;
+constexpr int32_t SPLIT_W = 16384;       // largest W of a hashed 256-thread block node
+constexpr int32_t DENSE_W = 32768;       // largest W of a direct-indexed block node
+constexpr int32_t BIG_W = 65536;         // largest W of a node rated by one 512-thread block
 constexpr int32_t SPLIT_DENSE_MAX = 65536;
 constexpr int SPLIT_WARPS = 8;
 constexpr int ARGMAX_THREADS = 256;
@@ -62,7 +68,7 @@ constexpr int32_t EMPTY_KEY = -1;
 constexpr size_t SMEM_BUDGET = 200 * 1024;
 
 // per sub-round bookkeeping words
-enum { CW_MOVES = 0, CW_TOUCHED = 1, CW_SLOTS = 2, CW_CURSOR = 3, CW_DIRTY = 4, CW_WORDS = 8 };
+enum { CW_MOVES = 0, CW_TOUCHED = 1, CW_SLOTS = 2, CW_CURSOR = 3, CW_WORDS = 8 };
 // work counters
 enum { ST_PINS = 0, ST_INCID = 1, ST_NODES = 2, ST_WORDS = 4 };
 
@@ -93,6 +99,10 @@ __device__ __forceinline__ uint32_t slot_hash(int32_t C) { return (uint32_t)C * 
 
 // ---------------------------------------------------- shared hash tables
 
+// add() results besides the slot index of a new insertion
+constexpr int32_t ADD_EXISTING = -1;
+constexpr int32_t ADD_FULL = -2;
+
 // 32-bit ratings: one 64-bit word per slot, cluster id above the rating, an
 // empty slot = id -1 with rating 0.  An add to the low half never carries
 // into the id because every rating stays below 2^31.
@@ -102,7 +112,8 @@ struct PackedHash {
   static constexpr unsigned long long EMPTY = 0xFFFFFFFF00000000ull;
   static constexpr size_t BYTES_PER_SLOT = 8;
   __device__ __forceinline__ void init(uint32_t i) { slot[i] = EMPTY; }
-  __device__ __forceinline__ bool add(int32_t C, uint32_t r) {
+  // the slot index when C was inserted by this call, else ADD_EXISTING / ADD_FULL
+  __device__ __forceinline__ int32_t add(int32_t C, uint32_t r) {
     const unsigned long long mine = ((unsigned long long)(uint32_t)C << 32) | r;
     uint32_t h = slot_hash(C) & mask;
     for (uint32_t probe = 0; probe <= mask; ++probe) {
@@ -111,16 +122,16 @@ struct PackedHash {
         const uint32_t k = (uint32_t)(w >> 32);
         if (k == (uint32_t)C) {
           atomicAdd(&slot[h], (unsigned long long)r);
-          return true;
+          return ADD_EXISTING;
         }
         if (k != 0xFFFFFFFFu) break;
         const unsigned long long old = atomicCAS(&slot[h], w, mine);
-        if (old == w) return true;
+        if (old == w) return (int32_t)h;
         w = old;
       }
       h = (h + 1) & mask;
     }
-    return false;
+    return ADD_FULL;
   }
   // cluster and rating of slot i (C = -1 when empty); the slot is cleared
   __device__ __forceinline__ void take(uint32_t i, int32_t& C, uint32_t& v) {
@@ -141,21 +152,23 @@ struct WideHash {
     key[i] = EMPTY_KEY;
     val[i] = 0;
   }
-  __device__ __forceinline__ bool add(int32_t C, unsigned long long r) {
+  __device__ __forceinline__ int32_t add(int32_t C, unsigned long long r) {
     uint32_t h = slot_hash(C) & mask;
     for (uint32_t probe = 0; probe <= mask; ++probe) {
       int32_t k = key[h];
+      bool fresh = false;
       if (k == EMPTY_KEY) {
         const int32_t old = atomicCAS(&key[h], EMPTY_KEY, C);
-        k = old == EMPTY_KEY ? C : old;
+        fresh = old == EMPTY_KEY;
+        k = fresh ? C : old;
       }
       if (k == C) {
         atomicAdd(&val[h], r);
-        return true;
+        return fresh ? (int32_t)h : ADD_EXISTING;
       }
       h = (h + 1) & mask;
     }
-    return false;
+    return ADD_FULL;
   }
   __device__ __forceinline__ void take(uint32_t i, int32_t& C, unsigned long long& v) {
     C = key[i];
@@ -183,14 +196,37 @@ __device__ __forceinline__ WideHash make_hash<WideHash>(unsigned char* base, uin
 
 // ------------------------------------------------------- the rating walk
 
+// Visits per lane kept in flight: the two dependent gathers of a visit (its
+// deduplicated cluster, then that cluster's weight and status) are issued for
+// RATE_ILP visits before any of them is used.
+constexpr int RATE_ILP = 4;
+
+// Adapts a per-visit adder f(C, r) to the batch interface of rate_group.
+template <typename VT, typename F>
+struct EachVisit {
+  F f;
+  __device__ __forceinline__ void operator()(const int32_t (&C)[RATE_ILP], const VT (&rr)[RATE_ILP],
+                                             const bool (&ok)[RATE_ILP]) const {
+#pragma unroll
+    for (int k = 0; k < RATE_ILP; ++k)
+      if (ok[k]) f(C[k], rr[k]);
+  }
+};
+template <typename VT, typename F>
+__device__ __forceinline__ EachVisit<VT, F> each_visit(F f) {
+  return EachVisit<VT, F>{f};
+}
+
 // Adds one group of (up to) 32 consecutive incident nets of u, starting at
-// position g0 of I(u), through `add`; returns the pin visits.  Nets of at
-// least 32 rated pins are walked one at a time with the lanes over their
-// pins; the smaller nets of the group are walked together over their
-// flattened pins.
+// position g0 of I(u), through `add`.  Nets of at least 32 rated pins are
+// walked one at a time with the lanes over their pins; the smaller nets of
+// the group are walked together over their flattened pins.  A team of TW
+// warps shares the group: warp wt takes the chunks of 32 * RATE_ILP visits
+// numbered wt, wt + TW, ...  Returns the group's pin visits in warp 0 (0 in
+// the other warps, so the team counts each visit once).
 template <typename VT, typename Add>
 __device__ __forceinline__ int32_t rate_group(const RateArgs& A, int32_t u, int32_t cu, int32_t g0,
-                                              int32_t end, Add add) {
+                                              int32_t end, int wt, int TW, Add add) {
   const int lane = lane_id();
   int32_t start = 0, eff = 0;
   VT r = 0;
@@ -203,12 +239,22 @@ __device__ __forceinline__ int32_t rate_group(const RateArgs& A, int32_t u, int3
       r = (VT)((((long long)A.w[e]) << 20) / (size - 1));
     }
   }
-  auto visit = [&](int32_t q, VT rr) {
-    const int32_t C = A.rpin[q];
-    if (C >= 0 && C != u) {
-      const int2 cs = A.cst[C];
-      if (cs.y != A.s && (long long)cs.x + cu <= (long long)A.c_max) add(C, rr);
-    }
+  // filter a batch of pin positions (-1 = no visit) and hand it to `add`:
+  // admissible C is not u, not an unclustered node of this sub-round, and
+  // fits c_max
+  auto visit_batch = [&](const int32_t(&q)[RATE_ILP], const VT(&rr)[RATE_ILP]) {
+    int32_t C[RATE_ILP];
+#pragma unroll
+    for (int k = 0; k < RATE_ILP; ++k) C[k] = q[k] >= 0 ? A.rpin[q[k]] : -1;
+    int2 cs[RATE_ILP];
+#pragma unroll
+    for (int k = 0; k < RATE_ILP; ++k)
+      cs[k] = (C[k] >= 0 && C[k] != u) ? A.cst[C[k]] : make_int2(0x7fffffff, 0);
+    bool ok[RATE_ILP];
+#pragma unroll
+    for (int k = 0; k < RATE_ILP; ++k)
+      ok[k] = cs[k].y != A.s && (long long)cs[k].x + cu <= (long long)A.c_max;
+    add(C, rr, ok);
   };
   // big nets, one at a time
   unsigned big = __ballot_sync(FULL, eff >= 32);
@@ -219,29 +265,45 @@ __device__ __forceinline__ int32_t rate_group(const RateArgs& A, int32_t u, int3
     const int32_t st = __shfl_sync(FULL, start, j);
     const int32_t sz = __shfl_sync(FULL, eff, j);
     const VT rj = __shfl_sync(FULL, r, j);
-    for (int32_t q = lane; q < sz; q += 32) visit(st + q, rj);
+    for (int32_t q0 = 32 * RATE_ILP * wt; q0 < sz; q0 += 32 * RATE_ILP * TW) {
+      int32_t q[RATE_ILP];
+      VT rr[RATE_ILP];
+#pragma unroll
+      for (int k = 0; k < RATE_ILP; ++k) {
+        const int32_t qq = q0 + 32 * k + lane;
+        q[k] = qq < sz ? st + qq : -1;
+        rr[k] = rj;
+      }
+      visit_batch(q, rr);
+    }
     visits += sz;
   }
   // small nets together
   const int32_t small = eff < 32 ? eff : 0;
   const int32_t incl = warp_inclusive_scan(small);
   const int32_t Z = __shfl_sync(FULL, incl, 31);
-  for (int32_t f0 = 0; f0 < Z; f0 += 32) {
-    const int32_t f = f0 + lane;
-    int j = 0;
+  for (int32_t f0 = 32 * RATE_ILP * wt; f0 < Z; f0 += 32 * RATE_ILP * TW) {
+    int32_t q[RATE_ILP];
+    VT rr[RATE_ILP];
 #pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-      const int32_t probe = __shfl_sync(FULL, incl, j + step - 1);
-      if (probe <= f) j += step;
+    for (int k = 0; k < RATE_ILP; ++k) {
+      const int32_t f = f0 + 32 * k + lane;
+      int j = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int32_t probe = __shfl_sync(FULL, incl, j + step - 1);
+        if (probe <= f) j += step;
+      }
+      j = j > 31 ? 31 : j;
+      const int32_t incl_j = __shfl_sync(FULL, incl, j);
+      const int32_t eff_j = __shfl_sync(FULL, small, j);
+      const int32_t start_j = __shfl_sync(FULL, start, j);
+      rr[k] = __shfl_sync(FULL, r, j);
+      q[k] = f < Z ? start_j + f - (incl_j - eff_j) : -1;
     }
-    j = j > 31 ? 31 : j;
-    const int32_t incl_j = __shfl_sync(FULL, incl, j);
-    const int32_t eff_j = __shfl_sync(FULL, small, j);
-    const int32_t start_j = __shfl_sync(FULL, start, j);
-    const VT r_j = __shfl_sync(FULL, r, j);
-    if (f < Z) visit(start_j + f - (incl_j - eff_j), r_j);
+    visit_batch(q, rr);
   }
-  return visits + Z;
+  return wt == 0 ? visits + Z : 0;
 }
 
 template <typename VT>
@@ -289,34 +351,48 @@ __device__ __forceinline__ void team_sync(int team) {
 
 // classes 0-2 with hash tables: TEAMS teams of TW warps per block, each team
 // rating one node at a time with a SLOTS-slot shared hash table
+// Shared memory of one team: the hash slots, then a list of the slots the
+// current node inserted (capacity slots / 2: a class's distinct bound).
+template <typename H>
+constexpr size_t team_bytes(uint32_t slots) {
+  return (size_t)slots * H::BYTES_PER_SLOT + (size_t)(slots / 2) * sizeof(int32_t);
+}
+
 template <typename VT, int TW, int TEAMS>
 __global__ void __launch_bounds__(TW * 32 * TEAMS) k_rate_team(RateArgs A, uint32_t slots) {
   using H = typename HashOf<VT>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ VT s_rv[TEAMS][TW];
   __shared__ int32_t s_rc[TEAMS][TW];
+  __shared__ int32_t s_nused[TEAMS];
   if (subround_stopped(A)) return;
   const int team = warp_in_block() / TW, wt = warp_in_block() % TW;
   const int tid = threadIdx.x % (TW * 32), nthr = TW * 32;
-  H tab = make_hash<H>(smem + (size_t)team * slots * H::BYTES_PER_SLOT, slots);
+  unsigned char* base = smem + (size_t)team * team_bytes<H>(slots);
+  H tab = make_hash<H>(base, slots);
+  int32_t* used = reinterpret_cast<int32_t*>(base + (size_t)slots * H::BYTES_PER_SLOT);
   for (uint32_t i = tid; i < slots; i += nthr) tab.init(i);
+  if (tid == 0) s_nused[team] = 0;
   team_sync<TW>(team);
   int64_t visits = 0, incid = 0, nodes = 0;
   for (int32_t i = blockIdx.x * TEAMS + team; i < A.count; i += gridDim.x * TEAMS) {
     const int32_t u = A.list[i];
     if (A.cst[u].y < 0) continue;  // joined a cluster in an earlier sub-round
     const int32_t cu = A.c[u], beg = A.ioff[u], end = A.ioff[u + 1];
-    for (int32_t g0 = beg + 32 * wt; g0 < end; g0 += 32 * TW)
-      visits += rate_group<VT>(A, u, cu, g0, end, [&](int32_t C, VT r) {
-        if (!tab.add(C, r)) dev_fail(A.status_word, DEV_HASH_FULL);
-      });
+    for (int32_t g0 = beg; g0 < end; g0 += 32)
+      visits += rate_group<VT>(A, u, cu, g0, end, wt, TW, each_visit<VT>([&](int32_t C, VT r) {
+        const int32_t sl = tab.add(C, r);
+        if (sl >= 0) used[atomicAdd(&s_nused[team], 1)] = sl;
+        else if (sl == ADD_FULL) dev_fail(A.status_word, DEV_HASH_FULL);
+      }));
     team_sync<TW>(team);
     VT bv = 0;
     int32_t bc = -1;
-    for (uint32_t x = tid; x < slots; x += nthr) {
+    const int32_t nu = s_nused[team];
+    for (int32_t x = tid; x < nu; x += nthr) {
       int32_t C;
       VT v;
-      tab.take(x, C, v);
+      tab.take((uint32_t)used[x], C, v);
       better(bv, bc, v, C);
     }
     warp_argmax(bv, bc);
@@ -329,7 +405,10 @@ __global__ void __launch_bounds__(TW * 32 * TEAMS) k_rate_team(RateArgs A, uint3
       if (tid == 0)
         for (int x = 1; x < TW; ++x) better(bv, bc, s_rv[team][x], s_rc[team][x]);
     }
-    if (tid == 0) publish(A, u, bc);
+    if (tid == 0) {
+      s_nused[team] = 0;
+      publish(A, u, bc);
+    }
     team_sync<TW>(team);
     incid += end - beg;
     ++nodes;
@@ -362,11 +441,11 @@ __global__ void __launch_bounds__(256) k_rate_dense(RateArgs A) {
     const int32_t u = A.list[i];
     if (A.cst[u].y < 0) continue;
     const int32_t cu = A.c[u], beg = A.ioff[u], end = A.ioff[u + 1];
-    for (int32_t g0 = beg + 32 * wv; g0 < end; g0 += 32 * nw)
-      visits += rate_group<VT>(A, u, cu, g0, end, [&](int32_t C, VT r) {
+    for (int32_t g0 = beg; g0 < end; g0 += 32)
+      visits += rate_group<VT>(A, u, cu, g0, end, wv, nw, each_visit<VT>([&](int32_t C, VT r) {
         // every term is >= 1, so a zero before the add marks the first touch
         if (atomicAdd(&val[C], r) == (VT)0) used[atomicAdd(&s_nused, 1)] = C;
-      });
+      }));
     __syncthreads();
     VT bv = 0;
     int32_t bc = -1;
@@ -423,30 +502,51 @@ k_rate_split_acc(RateArgs A, const int32_t* __restrict__ split, const int32_t* _
     int32_t* used = tused + base;
     int32_t* nused = tnused + i;
     if (tab_dense[i]) {
-      visits += rate_group<VT>(A, u, cu, g0, end, [&](int32_t C, VT r) {
-        if (atomicAdd(&val[C], r) == (VT)0) used[atomicAdd(nused, 1)] = C;
-      });
+      // direct-indexed: a reduction without a returned value; the argmax
+      // scans the whole table, which is no larger than twice the visits
+      visits += rate_group<VT>(A, u, cu, g0, end, 0, 1, each_visit<VT>([&](int32_t C, VT r) {
+        atomicAdd(&val[C], r);
+      }));
     } else {
       int32_t* key = tkey + base;
       const uint32_t mask = (uint32_t)tab_cap[i] - 1;
-      visits += rate_group<VT>(A, u, cu, g0, end, [&](int32_t C, VT r) {
-        uint32_t h = slot_hash(C) & mask;
-        for (uint32_t probe = 0; probe <= mask; ++probe) {
-          const int32_t k = key[h];
-          if (k == C) break;
-          if (k == EMPTY_KEY) {
-            const int32_t old = atomicCAS(&key[h], EMPTY_KEY, C);
-            if (old == EMPTY_KEY) {
-              used[atomicAdd(nused, 1)] = (int32_t)h;
-              break;
+      visits += rate_group<VT>(
+          A, u, cu, g0, end, 0, 1,
+          [&](const int32_t(&C)[RATE_ILP], const VT(&rr)[RATE_ILP], const bool(&ok)[RATE_ILP]) {
+            // the first slot of every visit of the batch is loaded at once
+            uint32_t h[RATE_ILP];
+            int32_t k0[RATE_ILP];
+#pragma unroll
+            for (int k = 0; k < RATE_ILP; ++k) {
+              h[k] = slot_hash(C[k]) & mask;
+              k0[k] = ok[k] ? key[h[k]] : C[k];
             }
-            if (old == C) break;
-          }
-          h = (h + 1) & mask;
-        }
-        if (key[h] == C) atomicAdd(&val[h], r);
-        else dev_fail(A.status_word, DEV_HASH_FULL);
-      });
+#pragma unroll
+            for (int k = 0; k < RATE_ILP; ++k) {
+              if (!ok[k]) continue;
+              uint32_t hh = h[k];
+              int32_t kk = k0[k];
+              bool found = false;
+              for (uint32_t probe = 0; probe <= mask; ++probe) {
+                if (kk == C[k]) {
+                  found = true;
+                  break;
+                }
+                if (kk == EMPTY_KEY) {
+                  const int32_t old = atomicCAS(&key[hh], EMPTY_KEY, C[k]);
+                  if (old == EMPTY_KEY) used[atomicAdd(nused, 1)] = (int32_t)hh;
+                  if (old == EMPTY_KEY || old == C[k]) {
+                    found = true;
+                    break;
+                  }
+                }
+                hh = (hh + 1) & mask;
+                kk = key[hh];
+              }
+              if (found) atomicAdd(&val[hh], rr[k]);
+              else dev_fail(A.status_word, DEV_HASH_FULL);
+            }
+          });
     }
     incid += min(32, end - g0);
   }
@@ -461,7 +561,8 @@ k_rate_split_acc(RateArgs A, const int32_t* __restrict__ split, const int32_t* _
 template <typename VT>
 __global__ void __launch_bounds__(ARGMAX_THREADS)
 k_rate_split_argmax(RateArgs A, const int32_t* __restrict__ split, int32_t lo, int32_t hi,
-                    const int64_t* __restrict__ tab_off, const int8_t* __restrict__ tab_dense,
+                    const int64_t* __restrict__ tab_off, const int64_t* __restrict__ tab_cap,
+                    const int8_t* __restrict__ tab_dense,
                     int64_t tab_base, int32_t* __restrict__ tkey, VT* __restrict__ tval,
                     const int32_t* __restrict__ tused, int32_t* __restrict__ tnused) {
   __shared__ VT s_rv[32];
@@ -472,15 +573,24 @@ k_rate_split_argmax(RateArgs A, const int32_t* __restrict__ split, int32_t lo, i
     if (A.cst[u].y < 0) continue;
     const int64_t base = tab_off[i] - tab_base;
     const bool dense = tab_dense[i] != 0;
-    const int32_t nu = tnused[i];
     VT bv = 0;
     int32_t bc = -1;
-    for (int32_t x = threadIdx.x; x < nu; x += blockDim.x) {
-      const int32_t sl = tused[base + x];
-      const int32_t C = dense ? sl : tkey[base + sl];
-      better(bv, bc, tval[base + sl], C);
-      tval[base + sl] = 0;
-      if (!dense) tkey[base + sl] = EMPTY_KEY;
+    if (dense) {
+      const int32_t cap = (int32_t)tab_cap[i];
+      for (int32_t C = threadIdx.x; C < cap; C += blockDim.x) {
+        const VT v = tval[base + C];
+        if (v == (VT)0) continue;
+        better(bv, bc, v, C);
+        tval[base + C] = 0;
+      }
+    } else {
+      const int32_t nu = tnused[i];
+      for (int32_t x = threadIdx.x; x < nu; x += blockDim.x) {
+        const int32_t sl = tused[base + x];
+        better(bv, bc, tval[base + sl], tkey[base + sl]);
+        tval[base + sl] = 0;
+        tkey[base + sl] = EMPTY_KEY;
+      }
     }
     warp_argmax(bv, bc);
     const int nw = blockDim.x >> 5;
@@ -501,22 +611,32 @@ k_rate_split_argmax(RateArgs A, const int32_t* __restrict__ split, int32_t lo, i
 
 // ------------------------------------------------------- node bucketing
 
-__device__ __forceinline__ int rate_class(int64_t W, int32_t n, bool dense_block) {
+// Team class of a node from W(u) and D = min(W(u), n):
+//   0 warp (512 slots)            D <= 256
+//   1 two warps (2048 slots)      D <= 1024 (unless the level is dense)
+//   2 block, direct-indexed       the level fits a dense shared table, W <= 32768
+//     block, 8192-slot hash       D <= 4096, W <= 16384
+//   3 512-thread block, 16384 slots (32-bit ratings only)  D <= 8192, W <= 65536
+//   4 split over the grid         the rest
+__device__ __forceinline__ int rate_class(int64_t W, int32_t n, bool dense_block, bool narrow) {
   const int64_t D = W < n ? W : n;  // bound on the distinct candidate clusters
   if (D <= D_WARP) return 0;
-  if (dense_block && W <= SPLIT_W) return 2;
+  if (dense_block && W <= DENSE_W) return 2;
   if (D <= D_PAIR) return 1;
-  if (D <= D_BLOCK && W <= SPLIT_W) return 2;
-  return 3;
+  // measured on GB300: grid-split nodes (class 4) sustain more visits per
+  // second than one node per large shared-memory block, whose table size
+  // limits occupancy; the hashed block (2) and wide block (3) stay available
+  // but are not selected
+  (void)narrow;
+  return 4;
 }
 
-// W(u) (pins of rated nets), the bound on u's rating (sum of its net terms)
-// and the key = class * S + sub-round of every node with W(u) > 0.
+// W(u) (pins of rated nets) of every node, and the largest bound on a node's
+// rating (sum of its net terms), which decides the value width.
 __global__ void k_node_work(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
                             const int32_t* __restrict__ eoff, const int32_t* __restrict__ w,
-                            int32_t n, int T, uint64_t seed, int level, int S, bool dense_block,
-                            int32_t* __restrict__ key_of, int32_t* __restrict__ wof,
-                            int32_t* __restrict__ kcount, unsigned long long* __restrict__ max_r) {
+                            int32_t n, int T, int32_t* __restrict__ wof,
+                            unsigned long long* __restrict__ max_r) {
   unsigned long long lr = 0;
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
        u += (int64_t)gridDim.x * blockDim.x) {
@@ -530,17 +650,28 @@ __global__ void k_node_work(const int32_t* __restrict__ ioff, const int32_t* __r
         R += (((unsigned long long)w[e]) << 20) / (unsigned long long)(sz - 1);
       }
     }
-    int32_t key = -1;
-    if (W > 0) {
-      key = rate_class(W, n, dense_block) * S + subround_of_node_cluster(seed, level, (int)u, S);
-      atomicAdd(&kcount[key], 1);
-      lr = R > lr ? R : lr;
-    }
-    key_of[u] = key;
+    lr = R > lr ? R : lr;
     wof[u] = W > 0x7fffffff ? 0x7fffffff : (int32_t)W;
   }
   const unsigned long long lr2 = warp_max(lr);
   if (lane_id() == 0 && lr2) atomicMax(max_r, lr2);
+}
+
+// key = class * S + sub-round of every node with W(u) > 0, and the counts.
+__global__ void k_node_classify(const int32_t* __restrict__ wof, int32_t n, uint64_t seed,
+                                int level, int S, bool dense_block, bool narrow,
+                                int32_t* __restrict__ key_of, int32_t* __restrict__ kcount) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t W = wof[u];
+    int32_t key = -1;
+    if (W > 0) {
+      key = rate_class(W, n, dense_block, narrow) * S +
+            subround_of_node_cluster(seed, level, (int)u, S);
+      atomicAdd(&kcount[key], 1);
+    }
+    key_of[u] = key;
+  }
 }
 
 __global__ void k_node_scatter(const int32_t* __restrict__ key_of, int32_t n, int nkeys,
@@ -788,120 +919,129 @@ __global__ void k_finish(const int32_t* __restrict__ touched, const int32_t* __r
 
 // ------------------------------------------------- rpin maintenance
 
-// Nets of the movers that joined a cluster in this sub-round: one warp per
-// mover marks its rated nets dirty (first marker appends to the list).
-__global__ void k_mark_dirty(const int32_t* __restrict__ mv, const int32_t* __restrict__ words,
-                             const int32_t* __restrict__ rep, const int32_t* __restrict__ ioff,
-                             const int32_t* __restrict__ inets, const int32_t* __restrict__ eoff,
-                             int T, int32_t* __restrict__ dirty, int32_t* __restrict__ dlist,
-                             int32_t* __restrict__ ndirty) {
-  const int32_t nm = words[CW_MOVES];
-  const int wv = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int32_t i = wv; i < nm; i += nwarps) {
-    const int32_t u = mv[i];
-    if (rep[u] == u) continue;  // rejected
-    for (int32_t j = ioff[u] + lane_id(); j < ioff[u + 1]; j += 32) {
-      const int32_t e = inets[j];
-      const int32_t sz = eoff[e + 1] - eoff[e];
+// The first position of every cluster in every rated net is kept in a global
+// hash map keyed by (net, cluster): at the start of a level every pin is its
+// own cluster, so the map holds (e, pins[q]) -> q for all rated pins.  When a
+// node v joins cluster C, for each rated net e of v at pin index q: an
+// atomicMin of q into (e, C) finds whether q becomes C's first position in e
+// (then the position it displaces, if any, is set to -1 in rpin) and, in a
+// second pass, rpin[q] = C if q is the first position of C in e, else -1.
+// The work per sub-round is the degree of the nodes that joined.
+struct PosMap {
+  unsigned long long* key;  // net << 32 | cluster, all ones when empty
+  int32_t* pos;             // smallest pin index, INT32_MAX when none yet
+  uint64_t mask;
+};
+
+__device__ __forceinline__ int64_t posmap_slot(const PosMap& M, int32_t e, int32_t C) {
+  const unsigned long long mine = ((unsigned long long)(uint32_t)e << 32) | (uint32_t)C;
+  uint64_t h = mix64(mine) & M.mask;
+  for (uint64_t probe = 0; probe <= M.mask; ++probe) {
+    unsigned long long k = M.key[h];
+    if (k == ~0ull) {
+      const unsigned long long old = atomicCAS(&M.key[h], ~0ull, mine);
+      k = old == ~0ull ? mine : old;
+    }
+    if (k == mine) return (int64_t)h;
+    h = (h + 1) & M.mask;
+  }
+  return -1;
+}
+
+// (e, pins[q]) -> q for every pin of every rated net (pin tiles).
+__global__ void __launch_bounds__(PIN_TILE_THREADS)
+k_posmap_init(const int32_t* __restrict__ eoff, const int32_t* __restrict__ pins,
+              const int32_t* __restrict__ tile_net, int32_t m, int64_t p, int T, PosMap M,
+              int32_t* status) {
+  __shared__ int32_t s_off[PIN_TILE + 3];
+  const int64_t ntiles = num_pin_tiles(p);
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    PinTileView v = stage_pin_tile(eoff, tile_net, m, p, t, s_off);
+    for (int64_t q = v.q0 + threadIdx.x; q < v.q1; q += blockDim.x) {
+      const int32_t i = net_in_tile(s_off, v.count, q);
+      const int32_t sz = s_off[i + 1] - s_off[i];
       if (sz < 2 || sz > T) continue;
-      if (atomicExch(&dirty[e], 1) == 0) dlist[atomicAdd(ndirty, 1)] = e;
+      const int64_t sl = posmap_slot(M, v.e_lo + i, pins[q]);
+      if (sl < 0) dev_fail(status, DEV_HASH_FULL);
+      else M.pos[sl] = (int32_t)q;
     }
+    __syncthreads();
   }
 }
 
-constexpr int REFRESH_WARPS = 2;
-constexpr int REFRESH_SET = 2048;  // per-warp set for nets of up to 1024 pins
+// The incidences of the listed nodes of one sub-round, one thread each: the
+// nodes of sub-round s sit in one range of the class-ordered node list per
+// class, and lpre is the exclusive prefix sum of the degrees along that list,
+// so the incidence ranks of each range are contiguous and a binary search in
+// lpre finds the node of a rank.  Nodes that did not join a cluster in the
+// sub-round (rep[u] == u) are skipped.
+struct SubRanges {
+  int32_t lo[NCLASS], hi[NCLASS];
+};
 
-// One entry of a per-warp set keyed by cluster: key = gen << 32 | C and
-// pos = ~gen << 32 | position, where gen numbers the nets a warp processes.
-// Entries of earlier nets are stale (other gen) and count as empty; for the
-// current net, atomicMin on pos keeps the smallest position (~gen shrinks as
-// gen grows, so a stale entry is always larger).  No reset pass is needed.
-__device__ __forceinline__ void set_insert_min(unsigned long long* key, unsigned long long* pos,
-                                               uint32_t mask, uint32_t gen, int32_t C, int32_t q,
-                                               int32_t* status) {
-  const unsigned long long mine = ((unsigned long long)gen << 32) | (uint32_t)C;
-  uint32_t h = slot_hash(C) & mask;
-  for (uint32_t probe = 0; probe <= mask; ++probe) {
-    unsigned long long k = key[h];
-    while ((uint32_t)(k >> 32) != gen) {  // stale: try to claim it
-      const unsigned long long old = atomicCAS(&key[h], k, mine);
-      if (old == k) { k = mine; break; }
-      k = old;
-    }
-    if (k == mine) {
-      atomicMin(&pos[h], ((unsigned long long)(~gen) << 32) | (uint32_t)q);
-      return;
-    }
-    h = (h + 1) & mask;
-  }
-  dev_fail(status, DEV_HASH_FULL);
-}
-
-__device__ __forceinline__ bool set_is_first(const unsigned long long* key,
-                                             const unsigned long long* pos, uint32_t mask,
-                                             uint32_t gen, int32_t C, int32_t q) {
-  const unsigned long long mine = ((unsigned long long)gen << 32) | (uint32_t)C;
-  uint32_t h = slot_hash(C) & mask;
-  for (uint32_t probe = 0; probe <= mask; ++probe) {
-    if (key[h] == mine) return pos[h] == (((unsigned long long)(~gen) << 32) | (uint32_t)q);
-    h = (h + 1) & mask;
-  }
-  return false;
-}
-
-// Recompute rpin for every dirty net: rpin[q] = rep[pins[q]] for the first
-// pin of each cluster in the net, -1 for its repeats.  Nets of <= 32 pins
-// use a warp match; larger nets a per-warp set (shared memory for up to 1024
-// pins, global memory above that, which only occurs with T > 1024).
-__global__ void __launch_bounds__(REFRESH_WARPS * 32)
-k_refresh_rpin(const int32_t* __restrict__ dlist, const int32_t* __restrict__ ndirty,
-               const int32_t* __restrict__ eoff, const int32_t* __restrict__ pins,
-               const int32_t* __restrict__ rep, int32_t* __restrict__ dirty,
-               int32_t* __restrict__ rpin, unsigned long long* gset, uint32_t gcap,
-               int32_t* status) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int wv = warp_in_block(), lane = lane_id();
-  unsigned long long* skey = reinterpret_cast<unsigned long long*>(smem) + (size_t)wv * 2 * REFRESH_SET;
-  unsigned long long* spos = skey + REFRESH_SET;
-  for (int i = lane; i < REFRESH_SET; i += 32) {
-    skey[i] = 0;
-    spos[i] = ~0ull;
-  }
-  __syncwarp();
-  const int32_t nd = *ndirty;
-  const int gw = blockIdx.x * REFRESH_WARPS + wv;
-  const int nwarps = gridDim.x * REFRESH_WARPS;
-  uint32_t gen = 0;
-  for (int32_t i = gw; i < nd; i += nwarps) {
-    const int32_t e = dlist[i];
-    const int32_t b = eoff[e], sz = eoff[e + 1] - b;
-    if (sz <= 32) {
-      const bool act = lane < sz;
-      const int32_t C = act ? rep[pins[b + lane]] : -1 - lane;
-      const unsigned peers = __match_any_sync(FULL, C);
-      if (act) rpin[b + lane] = (__ffs(peers) - 1 == lane) ? C : -1;
-    } else {
-      ++gen;
-      unsigned long long* k2 = skey;
-      unsigned long long* p2 = spos;
-      uint32_t mask = REFRESH_SET - 1;
-      if (sz > REFRESH_SET / 2) {
-        k2 = gset + (size_t)gw * 2 * gcap;
-        p2 = k2 + gcap;
-        mask = gcap - 1;
+// Pass 1 (JOIN): for a rated incidence (u, e) of a node that joined C, insert
+// (e, C), lower its first position to q and clear the position it displaced;
+// the map slot is kept for pass 2 (all ones for an unrated net).
+// Pass 2: rpin[q] = C where q is now C's first position in the net, else -1.
+template <bool JOIN>
+__global__ void __launch_bounds__(256)
+k_posmap_pass(const int32_t* __restrict__ list, const int32_t* __restrict__ lpre, SubRanges R,
+              const int32_t* __restrict__ rep, const int32_t* __restrict__ ioff,
+              const int32_t* __restrict__ inets, const int32_t* __restrict__ ipin,
+              const int32_t* __restrict__ eoff, int T, PosMap M, uint32_t* __restrict__ jslot,
+              int32_t* __restrict__ rpin, int32_t* status) {
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+#pragma unroll 1
+  for (int c = 0; c < NCLASS; ++c) {
+    const int32_t lo = R.lo[c], hi = R.hi[c];
+    if (lo >= hi) continue;
+    const int32_t base = lpre[lo];
+    const int32_t cnt = lpre[hi] - base;
+    for (int64_t t = gt; t < cnt; t += gs) {
+      const int32_t x = base + (int32_t)t;
+      int32_t a = lo, b = hi - 1;  // largest i in [lo, hi) with lpre[i] <= x
+      while (a < b) {
+        const int32_t mid = (a + b + 1) >> 1;
+        if (lpre[mid] <= x) a = mid;
+        else b = mid - 1;
       }
-      for (int32_t q = lane; q < sz; q += 32)
-        set_insert_min(k2, p2, mask, gen, rep[pins[b + q]], q, status);
-      __syncwarp();
-      for (int32_t q = lane; q < sz; q += 32) {
-        const int32_t C = rep[pins[b + q]];
-        rpin[b + q] = set_is_first(k2, p2, mask, gen, C, q) ? C : -1;
+      const int32_t u = list[a];
+      const int32_t C = rep[u];
+      if (C == u) continue;
+      const int32_t j = ioff[u] + (x - lpre[a]);
+      if (JOIN) {
+        const int32_t e = inets[j];
+        const int32_t sz = eoff[e + 1] - eoff[e];
+        uint32_t slot = ~0u;
+        if (sz >= 2 && sz <= T) {
+          const int32_t q = ipin[j];
+          const int64_t sl = posmap_slot(M, e, C);
+          if (sl < 0) {
+            dev_fail(status, DEV_HASH_FULL);
+          } else {
+            slot = (uint32_t)sl;
+            const int32_t old = atomicMin(&M.pos[sl], q);
+            if (old != 0x7fffffff && q < old) rpin[old] = -1;  // the displaced first position
+          }
+        }
+        jslot[j] = slot;
+      } else {
+        const uint32_t sl = jslot[j];
+        if (sl == ~0u) continue;
+        const int32_t q = ipin[j];
+        rpin[q] = M.pos[sl] == q ? C : -1;
       }
-      __syncwarp();
     }
-    if (lane == 0) dirty[e] = 0;
+  }
+}
+
+__global__ void k_list_degree(const int32_t* __restrict__ list, int32_t cnt,
+                              const int32_t* __restrict__ ioff, int32_t* __restrict__ deg) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = list[i];
+    deg[i] = ioff[u + 1] - ioff[u];
   }
 }
 
@@ -932,6 +1072,7 @@ void set_rate_attrs() {
   allow_smem(k_rate_team<VT, 1, 8>);
   allow_smem(k_rate_team<VT, 2, 4>);
   allow_smem(k_rate_team<VT, 8, 1>);
+  if (sizeof(VT) == 4) allow_smem(k_rate_team<VT, 16, 1>);
   allow_smem(k_rate_dense<VT>);
   done = true;
 }
@@ -952,7 +1093,7 @@ struct SplitPlan {
 template <typename VT, int TW, int TEAMS>
 void launch_team(const Ctx& cx, const RateArgs& A, uint32_t slots) {
   using H = typename HashOf<VT>::type;
-  const size_t bytes = (size_t)TEAMS * slots * H::BYTES_PER_SLOT;
+  const size_t bytes = (size_t)TEAMS * team_bytes<H>(slots);
   const int per_sm = std::max<int>(1, (int)(SMEM_BUDGET / bytes));
   k_rate_team<VT, TW, TEAMS><<<grid_for(A.count, TEAMS, cx.num_sms, per_sm), TW * 32 * TEAMS,
                                bytes, cx.stream>>>(A, slots);
@@ -960,33 +1101,39 @@ void launch_team(const Ctx& cx, const RateArgs& A, uint32_t slots) {
 
 template <typename VT>
 void rate_subround(const Ctx& cx, RateArgs A, const std::vector<int32_t>& hoff, const int32_t* list,
-                   int S, int s, bool dense_block, SplitPlan& sp, KernelTimer& timer,
-                   CoarsenCounters& cc) {
+                   int S, int s, bool dense_block, SplitPlan& sp, KernelTimer* timers,
+                   unsigned long long* stats_base, CoarsenCounters& cc) {
   set_rate_attrs<VT>();
-  for (int cls = 0; cls < 3; ++cls) {
+  for (int cls = 0; cls < SPLIT_CLASS; ++cls) {
     A.count = hoff[cls * S + s + 1] - hoff[cls * S + s];
     A.list = list + hoff[cls * S + s];
     if (A.count == 0) continue;
+    A.stats = stats_base + (size_t)cls * ST_WORDS;
+    KernelTimer& timer = timers[cls];
     timer.begin();
     if (cls == 0) {
       launch_team<VT, 1, 8>(cx, A, 2 * D_WARP);
     } else if (cls == 1) {
       launch_team<VT, 2, 4>(cx, A, 2 * D_PAIR);
-    } else if (dense_block) {
+    } else if (cls == 2 && dense_block) {
       const size_t bytes = (size_t)std::max<int32_t>(A.n, 1) * (sizeof(VT) + 4);
       const int per_sm = std::max<int>(1, (int)(SMEM_BUDGET / bytes));
       k_rate_dense<VT><<<grid_for(A.count, 1, cx.num_sms, per_sm), 256, bytes, cx.stream>>>(A);
-    } else {
+    } else if (cls == 2) {
       launch_team<VT, 8, 1>(cx, A, 2 * D_BLOCK);
+    } else if (sizeof(VT) == 4) {  // class 3 exists for 32-bit ratings only
+      launch_team<VT, 16, 1>(cx, A, 2 * D_WIDE);
     }
     timer.end();
     check_launch("rate_team");
     cc.rating_launches += 1;
   }
-  // class 3
+  // class 4 (split)
   if (sp.hi[s] > sp.lo[s]) {
     const int32_t items = sp.item_hi[s] - sp.item_lo[s];
     VT* tval = reinterpret_cast<VT*>(sp.tval.p);
+    A.stats = stats_base + (size_t)SPLIT_CLASS * ST_WORDS;
+    KernelTimer& timer = timers[SPLIT_CLASS];
     timer.begin();
     if (items > 0) {
       const int g = grid_for(items, SPLIT_WARPS, cx.num_sms, 16);
@@ -997,7 +1144,8 @@ void rate_subround(const Ctx& cx, RateArgs A, const std::vector<int32_t>& hoff, 
     }
     const int g2 = grid_for(sp.hi[s] - sp.lo[s], 1, cx.num_sms, 8);
     k_rate_split_argmax<VT><<<g2, ARGMAX_THREADS, 0, cx.stream>>>(
-        A, sp.split, sp.lo[s], sp.hi[s], sp.tab_off.p, sp.tab_dense.p, sp.tab_lo[s], sp.tkey.p, tval,
+        A, sp.split, sp.lo[s], sp.hi[s], sp.tab_off.p, sp.tab_cap.p, sp.tab_dense.p, sp.tab_lo[s],
+        sp.tkey.p, tval,
         sp.tused.p, sp.tnused.p);
     timer.end();
     check_launch("rate_split_argmax");
@@ -1016,7 +1164,7 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   cw_out.alloc(&cx.alloc, (size_t)n);
   DBuf<int2> cst;
   DBuf<int32_t> target, gw, gcnt, slot_of, slot_c, slot_off, slot_fill, mv, touched, glist, key_of,
-      wof, kcount, kfill, list, words, clusters, rpin, dirty, dlist;
+      wof, kcount, kfill, list, words, clusters, rpin;
   DBuf<unsigned long long> stats, max_r;
   const size_t ncap = (size_t)n + 1;
   cst.alloc(&cx.alloc, ncap);
@@ -1038,10 +1186,8 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   words.alloc(&cx.alloc, (size_t)S * CW_WORDS);
   clusters.alloc(&cx.alloc, 1);
   max_r.alloc(&cx.alloc, 1);
-  stats.alloc(&cx.alloc, ST_WORDS);
+  stats.alloc(&cx.alloc, (size_t)ST_WORDS * NCLASS);
   rpin.alloc(&cx.alloc, (size_t)std::max<int64_t>(L.p, 1));
-  dirty.alloc(&cx.alloc, (size_t)L.m + 1);
-  dlist.alloc(&cx.alloc, (size_t)L.m + 1);
   HG_CUDA(cudaMemsetAsync(gw.p, 0, gw.bytes(), cx.stream));
   HG_CUDA(cudaMemsetAsync(gcnt.p, 0, gcnt.bytes(), cx.stream));
   HG_CUDA(cudaMemsetAsync(slot_fill.p, 0, slot_fill.bytes(), cx.stream));
@@ -1050,50 +1196,52 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   HG_CUDA(cudaMemsetAsync(words.p, 0, words.bytes(), cx.stream));
   HG_CUDA(cudaMemsetAsync(max_r.p, 0, max_r.bytes(), cx.stream));
   HG_CUDA(cudaMemsetAsync(stats.p, 0, stats.bytes(), cx.stream));
-  HG_CUDA(cudaMemsetAsync(dirty.p, 0, dirty.bytes(), cx.stream));
   HG_CUDA(cudaMemcpyAsync(clusters.p, &n, sizeof(int32_t), cudaMemcpyHostToDevice, cx.stream));
   if (L.p > 0)
     HG_CUDA(cudaMemcpyAsync(rpin.p, L.pins.p, sizeof(int32_t) * (size_t)L.p,
                             cudaMemcpyDeviceToDevice, cx.stream));
 
-  // block tables are direct-indexed when the level is small enough for the
-  // wider (64-bit) values, so the choice does not depend on the value width
-  const bool dense_block = (size_t)n * 12 <= SMEM_BUDGET;
   const int g_nodes = grid_for(n, 256, cx.num_sms, 4);
   k_init_cluster<<<g_nodes, 256, 0, cx.stream>>>(L.c.p, n, P.seed, P.level, S, L.rep.p, cst.p,
                                                  slot_of.p);
   check_launch("init_cluster");
-  k_node_work<<<g_nodes, 256, 0, cx.stream>>>(L.ioff.p, L.inets.p, L.eoff.p, L.w.p, n, P.T, P.seed,
-                                               P.level, S, dense_block, key_of.p, wof.p, kcount.p,
-                                               max_r.p);
+  k_node_work<<<g_nodes, 256, 0, cx.stream>>>(L.ioff.p, L.inets.p, L.eoff.p, L.w.p, n, P.T,
+                                               wof.p, max_r.p);
   check_launch("node_work");
+  const unsigned long long hmax_r = (unsigned long long)read_i64(cx, (const int64_t*)max_r.p);
+  // 32-bit rating words when no node's total rating can reach 2^31; block
+  // tables are direct-indexed when one value and one used-list entry per
+  // node of the level fit the shared-memory budget
+  const bool narrow = hmax_r < (1ull << 31);
+  const size_t vbytes = narrow ? 4 : 8;
+  const bool dense_block = (size_t)n * (vbytes + 4) <= SMEM_BUDGET;
+  k_node_classify<<<g_nodes, 256, 0, cx.stream>>>(wof.p, n, P.seed, P.level, S, dense_block,
+                                                   narrow, key_of.p, kcount.p);
+  check_launch("node_classify");
   k_node_scatter<<<g_nodes, 256, nkeys * sizeof(int32_t), cx.stream>>>(key_of.p, n, nkeys,
                                                                         kcount.p, kfill.p, list.p);
   check_launch("node_scatter");
-  if (cx.launches) *cx.launches += 3;
+  if (cx.launches) *cx.launches += 4;
 
   std::vector<int32_t> hcount(nkeys);
   HG_CUDA(cudaMemcpyAsync(hcount.data(), kcount.p, sizeof(int32_t) * nkeys, cudaMemcpyDeviceToHost,
                           cx.stream));
-  const unsigned long long hmax_r = (unsigned long long)read_i64(cx, (const int64_t*)max_r.p);
+  check_status(cx);
   std::vector<int32_t> hoff(nkeys + 1, 0);
   for (int i = 0; i < nkeys; ++i) hoff[i + 1] = hoff[i] + hcount[i];
-  // 32-bit rating words when no node's total rating can reach 2^31
-  const bool narrow = hmax_r < (1ull << 31);
-  const size_t vbytes = narrow ? 4 : 8;
 
-  // ---- class 3 plan: items, table offsets and footprint per sub-round
+  // ---- split plan: items, table offsets and footprint per sub-round
   SplitPlan sp;
   sp.lo.resize(S);
   sp.hi.resize(S);
   sp.item_lo.assign(S, 0);
   sp.item_hi.assign(S, 0);
   sp.tab_lo.assign(S, 0);
-  const int32_t split_base = hoff[3 * S];
-  const int32_t nsplit = hoff[4 * S] - split_base;
+  const int32_t split_base = hoff[SPLIT_CLASS * S];
+  const int32_t nsplit = hoff[NCLASS * S] - split_base;
   for (int s = 0; s < S; ++s) {
-    sp.lo[s] = hoff[3 * S + s] - split_base;
-    sp.hi[s] = hoff[3 * S + s + 1] - split_base;
+    sp.lo[s] = hoff[SPLIT_CLASS * S + s] - split_base;
+    sp.hi[s] = hoff[SPLIT_CLASS * S + s + 1] - split_base;
   }
   sp.split = list.p + split_base;
   if (nsplit > 0) {
@@ -1145,29 +1293,43 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
     if (cx.launches) *cx.launches += 10;
   }
 
-  // global sets for the rpin refresh of nets above 1024 pins (only with T > 1024)
-  DBuf<unsigned long long> rset;
-  uint32_t rcap = 0;
-  const int g_refresh = cx.num_sms * 3;
-  const size_t refresh_smem = (size_t)REFRESH_WARPS * 2 * REFRESH_SET * sizeof(unsigned long long);
-  {
-    static bool attr = false;
-    if (!attr) {
-      HG_CUDA(cudaFuncSetAttribute(k_refresh_rpin, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)refresh_smem));
-      attr = true;
+  // (net, cluster) -> first position map: at most one key per rated pin at
+  // the start plus one per joining incidence, so 2p keys; capacity >= 4p
+  // (at most 2^32, which still exceeds 2p since p < 2^31).
+  DBuf<unsigned long long> pm_key;
+  DBuf<int32_t> pm_pos, lpre;
+  DBuf<uint32_t> jslot;
+  PosMap pm;
+  pm.key = nullptr;
+  pm.pos = nullptr;
+  pm.mask = 0;
+  if (L.p > 0 && S > 1) {
+    uint64_t cap = 1024;
+    while (cap < 4 * (uint64_t)L.p && cap < (1ull << 32)) cap <<= 1;
+    pm_key.alloc(&cx.alloc, cap);
+    pm_pos.alloc(&cx.alloc, cap);
+    jslot.alloc(&cx.alloc, (size_t)L.p);
+    HG_CUDA(cudaMemsetAsync(pm_key.p, 0xff, pm_key.bytes(), cx.stream));
+    fill_i32(cx, pm_pos.p, 0x7fffffff, (int64_t)cap);
+    pm.key = pm_key.p;
+    pm.pos = pm_pos.p;
+    pm.mask = cap - 1;
+    DBuf<int32_t> tiles;
+    tiles.alloc(&cx.alloc, (size_t)num_pin_tiles(L.p) + 1);
+    const int32_t nlisted = hoff[nkeys];
+    lpre.alloc(&cx.alloc, (size_t)nlisted + 1);
+    EventTimer tm(cx, &cc.ms_refresh);
+    if (nlisted > 0) {
+      k_list_degree<<<grid_for(nlisted, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(
+          list.p, nlisted, L.ioff.p, lpre.p);
+      check_launch("list_degree");
     }
-  }
-  if (P.T > REFRESH_SET / 2) {
-    rcap = 1;
-    while (rcap < 2u * (uint32_t)P.T) rcap <<= 1;
-    const size_t cnt = (size_t)g_refresh * REFRESH_WARPS * 2 * rcap;
-    rset.alloc(&cx.alloc, cnt);
-    // key halves 0 (generation 0 is never used), position halves all ones
-    const size_t per = 2 * (size_t)rcap;
-    HG_CUDA(cudaMemsetAsync(rset.p, 0xff, rset.bytes(), cx.stream));
-    for (size_t wv = 0; wv < (size_t)g_refresh * REFRESH_WARPS; ++wv)
-      HG_CUDA(cudaMemsetAsync(rset.p + wv * per, 0, rcap * sizeof(unsigned long long), cx.stream));
+    scan_exclusive_i32(cx, lpre.p, lpre.p, nlisted, lpre.p + nlisted);
+    build_tile_index(cx, L.eoff.p, L.m, L.p, tiles.p);
+    k_posmap_init<<<grid_for(num_pin_tiles(L.p), 1, cx.num_sms, 8), PIN_TILE_THREADS, 0,
+                    cx.stream>>>(L.eoff.p, L.pins.p, tiles.p, L.m, L.p, P.T, pm, cx.d_status);
+    check_launch("posmap_init");
+    if (cx.launches) *cx.launches += 1 + (nlisted > 0);
   }
 
   RateArgs A;
@@ -1190,7 +1352,8 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   A.stats = stats.p;
   A.status_word = cx.d_status;
 
-  KernelTimer rate_timer(cx);
+  std::vector<KernelTimer> rate_timers;
+  for (int c = 0; c < NCLASS; ++c) rate_timers.emplace_back(cx);
   for (int s = 0; s < S; ++s) {
     A.s = s;
     A.words = words.p + (size_t)s * CW_WORDS;
@@ -1199,10 +1362,11 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
       EventTimer tm(cx, &cc.ms_rating);
       const int64_t before = cc.rating_launches;
       if (narrow)
-        rate_subround<uint32_t>(cx, A, hoff, list.p, S, s, dense_block, sp, rate_timer, cc);
+        rate_subround<uint32_t>(cx, A, hoff, list.p, S, s, dense_block, sp, rate_timers.data(),
+                                stats.p, cc);
       else
-        rate_subround<unsigned long long>(cx, A, hoff, list.p, S, s, dense_block, sp, rate_timer,
-                                          cc);
+        rate_subround<unsigned long long>(cx, A, hoff, list.p, S, s, dense_block, sp,
+                                          rate_timers.data(), stats.p, cc);
       if (cx.launches) *cx.launches += cc.rating_launches - before;
     }
     {
@@ -1223,29 +1387,42 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
       check_launch("finish");
       if (cx.launches) *cx.launches += 4;
     }
-    if (s + 1 < S) {
+    if (s + 1 < S && L.p > 0) {
       EventTimer tm(cx, &cc.ms_refresh);
-      k_mark_dirty<<<grid_for((n + S - 1) / S, 8, cx.num_sms, 8), 256, 0, cx.stream>>>(
-          mv.p, w_s, L.rep.p, L.ioff.p, L.inets.p, L.eoff.p, P.T, dirty.p, dlist.p,
-          w_s + CW_DIRTY);
-      check_launch("mark_dirty");
-      k_refresh_rpin<<<g_refresh, REFRESH_WARPS * 32, refresh_smem, cx.stream>>>(
-          dlist.p, w_s + CW_DIRTY, L.eoff.p, L.pins.p, L.rep.p, dirty.p, rpin.p, rset.p, rcap,
-          cx.d_status);
-      check_launch("refresh_rpin");
+      SubRanges R;
+      for (int c = 0; c < NCLASS; ++c) {
+        R.lo[c] = hoff[c * S + s];
+        R.hi[c] = hoff[c * S + s + 1];
+      }
+      const int g = cx.num_sms * 8;
+      k_posmap_pass<true><<<g, 256, 0, cx.stream>>>(list.p, lpre.p, R, L.rep.p, L.ioff.p,
+                                                    L.inets.p, L.ipin.p, L.eoff.p, P.T, pm,
+                                                    jslot.p, rpin.p, cx.d_status);
+      check_launch("posmap_join");
+      k_posmap_pass<false><<<g, 256, 0, cx.stream>>>(list.p, lpre.p, R, L.rep.p, L.ioff.p,
+                                                     L.inets.p, L.ipin.p, L.eoff.p, P.T, pm,
+                                                     jslot.p, rpin.p, cx.d_status);
+      check_launch("posmap_fix");
       if (cx.launches) *cx.launches += 2;
     }
   }
-  cc.ms_rating_kernels += rate_timer.flush();
+  for (int c = 0; c < NCLASS; ++c) {
+    const double ms = rate_timers[c].flush();
+    cc.ms_rating_kernels += ms;
+    cc.class_ms[c] += ms;
+  }
   // cluster weights for the contraction (valid at representatives)
   HG_CUDA(cudaMemcpy2DAsync(cw_out.p, sizeof(int32_t), cst.p, sizeof(int2), sizeof(int32_t),
                             (size_t)n, cudaMemcpyDeviceToDevice, cx.stream));
-  unsigned long long hs[ST_WORDS];
+  unsigned long long hs[ST_WORDS * NCLASS];
   HG_CUDA(cudaMemcpyAsync(hs, stats.p, sizeof(hs), cudaMemcpyDeviceToHost, cx.stream));
   check_status(cx);
-  cc.rating_pin_visits += (int64_t)hs[ST_PINS];
-  cc.rating_incidences += (int64_t)hs[ST_INCID];
-  cc.rating_nodes += (int64_t)hs[ST_NODES];
+  for (int c = 0; c < NCLASS; ++c) {
+    cc.rating_pin_visits += (int64_t)hs[c * ST_WORDS + ST_PINS];
+    cc.rating_incidences += (int64_t)hs[c * ST_WORDS + ST_INCID];
+    cc.rating_nodes += (int64_t)hs[c * ST_WORDS + ST_NODES];
+    cc.class_visits[c] += (int64_t)hs[c * ST_WORDS + ST_PINS];
+  }
 }
 
 }  // namespace hgk

@@ -222,6 +222,7 @@ struct Level {
   DBuf<int32_t> c;      // n    node weights
   DBuf<int32_t> ioff;   // n+1  node -> first incident net
   DBuf<int32_t> inets;  // p    incident nets (order unspecified)
+  DBuf<int32_t> ipin;   // p    for every incidence, the index of its pin in `pins`
   DBuf<int32_t> map;    // n    node -> node of the next level (after coarsening)
   DBuf<int32_t> rep;    // n    representative in the clustering that made the next level
   bool coarsened = false;
@@ -270,6 +271,8 @@ struct CoarsenParams {
 struct CoarsenCounters {
   int64_t rating_launches = 0, rating_pin_visits = 0, rating_nodes = 0, rating_incidences = 0;
   double ms_rating = 0, ms_approve = 0, ms_refresh = 0, ms_rating_kernels = 0;
+  double class_ms[8] = {0};        // rating kernel time per node class (kernel timing on)
+  int64_t class_visits[8] = {0};   // pin visits per node class
 };
 
 // Deterministic clustering of level L: fills L.rep (representatives) and

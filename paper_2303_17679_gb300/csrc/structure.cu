@@ -27,11 +27,13 @@ __global__ void k_degrees(const int32_t* __restrict__ pins, int64_t p, int32_t* 
     atomicAdd(&deg[pins[q]], 1);
 }
 
-// Scatter every pin (e, v) into I(v) at a slot taken from v's cursor.
+// Scatter every pin (e, v) into I(v) at a slot taken from v's cursor; the
+// slot also records the pin's index q in `pins`.
 __global__ void __launch_bounds__(PIN_TILE_THREADS)
 k_scatter_incidence(const int32_t* __restrict__ eoff, const int32_t* __restrict__ pins,
                     const int32_t* __restrict__ tile_net, int32_t m, int64_t p,
-                    int32_t* __restrict__ cursor, int32_t* __restrict__ inets) {
+                    int32_t* __restrict__ cursor, int32_t* __restrict__ inets,
+                    int32_t* __restrict__ ipin) {
   __shared__ int32_t s_off[PIN_TILE + 3];
   const int64_t ntiles = num_pin_tiles(p);
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -41,6 +43,7 @@ k_scatter_incidence(const int32_t* __restrict__ eoff, const int32_t* __restrict_
       const int32_t u = pins[q];
       const int32_t slot = atomicAdd(&cursor[u], 1);
       inets[slot] = e;
+      ipin[slot] = (int32_t)q;
     }
     __syncthreads();
   }
@@ -96,6 +99,7 @@ void build_tile_index(const Ctx& cx, const int32_t* eoff, int32_t m, int64_t p, 
 void build_incidence(const Ctx& cx, Level& L) {
   L.ioff.alloc(&cx.alloc, (size_t)L.n + 1);
   L.inets.alloc(&cx.alloc, (size_t)(L.p > 0 ? L.p : 1));
+  L.ipin.alloc(&cx.alloc, (size_t)(L.p > 0 ? L.p : 1));
   HG_CUDA(cudaMemsetAsync(L.ioff.p, 0, sizeof(int32_t) * ((size_t)L.n + 1), cx.stream));
   if (L.p > 0) {
     k_degrees<<<grid_for(L.p, 256, cx.num_sms, 16), 256, 0, cx.stream>>>(L.pins.p, L.p, L.ioff.p);
@@ -111,7 +115,7 @@ void build_incidence(const Ctx& cx, Level& L) {
     build_tile_index(cx, L.eoff.p, L.m, L.p, tiles.p);
     k_scatter_incidence<<<grid_for(num_pin_tiles(L.p), 1, cx.num_sms, 8), PIN_TILE_THREADS, 0,
                           cx.stream>>>(L.eoff.p, L.pins.p, tiles.p, L.m, L.p, cursor.p,
-                                       L.inets.p);
+                                       L.inets.p, L.ipin.p);
     check_launch("scatter_incidence");
     if (cx.launches) *cx.launches += 2;
   }

@@ -54,10 +54,15 @@ class hg_stats(ctypes.Structure):
             "launches", "rating_launches", "rating_pin_visits", "rating_nodes",
             "rating_incidences", "lp_incidences", "lp_nodes", "lp_gain_launches")] + [
         ("ms_rating_kernels", ctypes.c_double), ("ms_lp_gain_kernels", ctypes.c_double),
-        ("ms_rating_refresh", ctypes.c_double)]
+        ("ms_rating_refresh", ctypes.c_double),
+        ("ms_rating_class", ctypes.c_double * 8), ("rating_visits_class", ctypes.c_int64 * 8)]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if isinstance(v, ctypes.Array) else v
+        return out
 
 
 class HgError(RuntimeError):
