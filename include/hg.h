@@ -191,6 +191,44 @@ int hg_objective(hg_t* h, int32_t level, int32_t k, const int32_t* part, int64_t
 int hg_pin_counts(hg_t* h, int32_t level, int32_t k, const int32_t* part, int32_t* phi,
                   uint64_t* lambda, int64_t* block_weights);
 
+/* The objective f_{lambda-1} (Sec. 2) and the block weights c(V_i) of a
+ * partition, for a hypergraph held by the caller in device memory, with no
+ * handle and without allocating device memory.  The paper has no
+ * counterpart: this serves callers that must not allocate, such as a serving
+ * loop where a cudaMalloc/cudaFree would synchronize the device and stall
+ * the other streams, a process whose device memory is reserved in full up
+ * front, or code running inside an hg_options.dev_alloc callback, which must
+ * not re-enter the allocator.
+ *   n, m, p       nodes (>= 1), nets (>= 0), pins (0 <= p < 2^31)
+ *   net_offsets   device, m+1 int32 entries in [0, p], non-decreasing
+ *   pins          device, p int32 entries in [0, n) (NULL when p == 0)
+ *   net_weights   device, m int32 entries, or NULL for all 1
+ *   node_weights  device, n int32 entries, or NULL for all 1
+ *   k             1..64
+ *   part          device, n int32 entries in [0, k)
+ *   cuda_stream   cudaStream_t to run on (NULL = legacy default stream)
+ *   out_objective host, written: sum over nets of (lambda(e) - 1) w(e); an
+ *                 empty net counts 0
+ *   out_block_weights host, k int64 entries written, or NULL
+ * Scratch: a fixed 9,248-byte device array inside the library (1024 block
+ * partials, 64 block-weight counters, a finished-block counter, a status word
+ * and a result record), enough for any n, m and p since the grid is capped
+ * at 1024 blocks.  Returns HG_ERR_UNSUPPORTED for k > 64 (the scratch holds
+ * 64 block-weight counters), HG_ERR_INVALID for other bad sizes or NULL
+ * pointers (checked on the host, nothing launched) and for offsets, pins or
+ * block ids out of range (checked on the device; the call then returns
+ * after the kernel without writing the outputs), HG_ERR_CUDA / HG_ERR_OOM for
+ * a CUDA error.  Synchronizes the stream.
+ * The first call on a device (the current device) looks up the scratch
+ * address and the SM count once; make that first call before any stream
+ * capture begins.  The scratch is shared by all calls on a device: calls
+ * that overlap in time on one device (from two host threads, or on two
+ * streams) race and must be serialized by the caller. */
+int hg_objective_noalloc(int32_t n, int32_t m, int64_t p, const int32_t* net_offsets,
+                         const int32_t* pins, const int32_t* net_weights,
+                         const int32_t* node_weights, int32_t k, const int32_t* part,
+                         void* cuda_stream, int64_t* out_objective, int64_t* out_block_weights);
+
 /* The whole deterministic multilevel path (Algorithm 1 without FM and
  * flows): coarsen until HG_STOP, initial partition of the coarsest level,
  * label propagation on it, then project and refine level by level down to

@@ -99,6 +99,8 @@ def load(path: str | None = None):
             "hg_lp_refine": (ctypes.c_int, [H, i32, i32, i32, i32, vp, P(i64), P(i64)]),
             "hg_objective": (ctypes.c_int, [H, i32, i32, vp, P(i64)]),
             "hg_pin_counts": (ctypes.c_int, [H, i32, i32, vp, vp, vp, vp]),
+            "hg_objective_noalloc": (ctypes.c_int, [i32, i32, i64, vp, vp, vp, vp, i32, vp, vp,
+                                                    P(i64), vp]),
             "hg_partition": (ctypes.c_int, [H, i32, i32, i32, vp, P(i64)]),
             "hg_get_level": (ctypes.c_int, [H, i32, vp, vp, vp, vp, vp, vp]),
             "hg_get_incidence": (ctypes.c_int, [H, i32, vp, vp]),
@@ -122,7 +124,7 @@ def exported_symbols():
     """Names of the C entry points this binding expects the library to export."""
     return ["hg_default_options", "hg_create", "hg_coarsen_level", "hg_num_levels",
             "hg_level_info", "hg_initial_partition", "hg_project", "hg_lp_refine",
-            "hg_objective", "hg_pin_counts", "hg_partition", "hg_get_level", "hg_get_incidence",
+            "hg_objective", "hg_pin_counts", "hg_objective_noalloc", "hg_partition", "hg_get_level", "hg_get_incidence",
             "hg_truncate", "hg_enable_timing", "hg_get_stats", "hg_reset_stats", "hg_destroy",
             "hg_strerror", "hg_version"]
 
@@ -256,6 +258,20 @@ def hg_pin_counts(h, level, k, part):
     _check(load().hg_pin_counts(h, int(level), int(k), _ptr(part), _ptr(phi), _ptr(lam), _ptr(bw)),
            "hg_pin_counts")
     return phi[:m], lam[:m], bw
+
+
+def hg_objective_noalloc(n, m, p, net_offsets, pins, net_weights, node_weights, k, part,
+                         stream=None):
+    """Objective and block weights of a partition of a device CSR, computed
+    without a handle and without any device allocation.  Returns
+    (objective, block weights [k] int64 numpy array)."""
+    obj = ctypes.c_int64()
+    bw = np.zeros(max(int(k), 1), np.int64)
+    _check(load().hg_objective_noalloc(int(n), int(m), int(p), _ptr(net_offsets), _ptr(pins),
+                                       _ptr(net_weights), _ptr(node_weights), int(k), _ptr(part),
+                                       _stream(stream), ctypes.byref(obj), _ptr(bw)),
+           "hg_objective_noalloc")
+    return obj.value, bw[:k]
 
 
 def hg_partition(h, k, eps_ppm, max_passes, part) -> int:
