@@ -63,6 +63,11 @@ constexpr int32_t DENSE_W = 32768;       // largest W of a direct-indexed block 
 constexpr int32_t BIG_W = 65536;         // largest W of a node rated by one 512-thread block
 constexpr int32_t SPLIT_DENSE_MAX = 65536;
 constexpr int SPLIT_WARPS = 8;
+constexpr int PART_THREADS = 1024;
+constexpr int PART_TEAMS = 4;
+constexpr uint32_t PART_SLOTS = 16384;   // shared hash slots of a part block
+constexpr int32_t PART_D = 9830;         // distinct candidates per part (60 % of the slots)
+constexpr int32_t PART_MAX = 8;          // more parts: the node uses a global hash table
 constexpr int ARGMAX_THREADS = 256;
 constexpr int32_t EMPTY_KEY = -1;
 constexpr size_t SMEM_BUDGET = 200 * 1024;
@@ -113,10 +118,10 @@ struct PackedHash {
   static constexpr size_t BYTES_PER_SLOT = 8;
   __device__ __forceinline__ void init(uint32_t i) { slot[i] = EMPTY; }
   // the slot index when C was inserted by this call, else ADD_EXISTING / ADD_FULL
-  __device__ __forceinline__ int32_t add(int32_t C, uint32_t r) {
+  __device__ __forceinline__ int32_t add(int32_t C, uint32_t r, uint32_t max_probe = 0xFFFFFFFFu) {
     const unsigned long long mine = ((unsigned long long)(uint32_t)C << 32) | r;
     uint32_t h = slot_hash(C) & mask;
-    for (uint32_t probe = 0; probe <= mask; ++probe) {
+    for (uint32_t probe = 0; probe <= mask && probe < max_probe; ++probe) {
       unsigned long long w = slot[h];
       while (true) {
         const uint32_t k = (uint32_t)(w >> 32);
@@ -152,9 +157,10 @@ struct WideHash {
     key[i] = EMPTY_KEY;
     val[i] = 0;
   }
-  __device__ __forceinline__ int32_t add(int32_t C, unsigned long long r) {
+  __device__ __forceinline__ int32_t add(int32_t C, unsigned long long r,
+                                         uint32_t max_probe = 0xFFFFFFFFu) {
     uint32_t h = slot_hash(C) & mask;
-    for (uint32_t probe = 0; probe <= mask; ++probe) {
+    for (uint32_t probe = 0; probe <= mask && probe < max_probe; ++probe) {
       int32_t k = key[h];
       bool fresh = false;
       if (k == EMPTY_KEY) {
@@ -217,16 +223,41 @@ __device__ __forceinline__ EachVisit<VT, F> each_visit(F f) {
   return EachVisit<VT, F>{f};
 }
 
+// Filters a batch of pin positions (-1 = no visit) and hands it to `add`:
+// admissible C is not u, not an unclustered node of this sub-round, and fits
+// c_max.
+template <typename VT, typename Add>
+__device__ __forceinline__ void visit_filtered(const RateArgs& A, int32_t u, int32_t cu,
+                                               const int32_t (&q)[RATE_ILP],
+                                               const VT (&rr)[RATE_ILP], Add& add) {
+  int32_t C[RATE_ILP];
+#pragma unroll
+  for (int k = 0; k < RATE_ILP; ++k) C[k] = q[k] >= 0 ? A.rpin[q[k]] : -1;
+  int2 cs[RATE_ILP];
+#pragma unroll
+  for (int k = 0; k < RATE_ILP; ++k)
+    cs[k] = (C[k] >= 0 && C[k] != u) ? A.cst[C[k]] : make_int2(0x7fffffff, 0);
+  bool ok[RATE_ILP];
+#pragma unroll
+  for (int k = 0; k < RATE_ILP; ++k)
+    ok[k] = cs[k].y != A.s && (long long)cs[k].x + cu <= (long long)A.c_max;
+  add(C, rr, ok);
+}
+
 // Adds one group of (up to) 32 consecutive incident nets of u, starting at
 // position g0 of I(u), through `add`.  Nets of at least 32 rated pins are
 // walked one at a time with the lanes over their pins; the smaller nets of
 // the group are walked together over their flattened pins.  A team of TW
-// warps shares the group: warp wt takes the chunks of 32 * RATE_ILP visits
-// numbered wt, wt + TW, ...  Returns the group's pin visits in warp 0 (0 in
-// the other warps, so the team counts each visit once).
-template <typename VT, typename Add>
-__device__ __forceinline__ int32_t rate_group(const RateArgs& A, int32_t u, int32_t cu, int32_t g0,
-                                              int32_t end, int wt, int TW, Add add) {
+// warps shares the group: the chunks of 32 * RATE_ILP visits are numbered on
+// from `run` (the chunks the team has walked before, for this node) and warp
+// wt takes those whose number is wt modulo TW, so the team stays balanced
+// across groups; `run` is advanced past the group's chunks.  Returns the
+// group's pin visits in warp 0 (0 in the other warps, so the team counts each
+// visit once).
+template <typename VT, typename Visit>
+__device__ __forceinline__ int32_t rate_group_raw(const RateArgs& A, int32_t g0, int32_t end,
+                                                  int wt, int TW, int32_t& run, Visit& visit_batch) {
+  constexpr int32_t CH = 32 * RATE_ILP;
   const int lane = lane_id();
   int32_t start = 0, eff = 0;
   VT r = 0;
@@ -239,23 +270,6 @@ __device__ __forceinline__ int32_t rate_group(const RateArgs& A, int32_t u, int3
       r = (VT)((((long long)A.w[e]) << 20) / (size - 1));
     }
   }
-  // filter a batch of pin positions (-1 = no visit) and hand it to `add`:
-  // admissible C is not u, not an unclustered node of this sub-round, and
-  // fits c_max
-  auto visit_batch = [&](const int32_t(&q)[RATE_ILP], const VT(&rr)[RATE_ILP]) {
-    int32_t C[RATE_ILP];
-#pragma unroll
-    for (int k = 0; k < RATE_ILP; ++k) C[k] = q[k] >= 0 ? A.rpin[q[k]] : -1;
-    int2 cs[RATE_ILP];
-#pragma unroll
-    for (int k = 0; k < RATE_ILP; ++k)
-      cs[k] = (C[k] >= 0 && C[k] != u) ? A.cst[C[k]] : make_int2(0x7fffffff, 0);
-    bool ok[RATE_ILP];
-#pragma unroll
-    for (int k = 0; k < RATE_ILP; ++k)
-      ok[k] = cs[k].y != A.s && (long long)cs[k].x + cu <= (long long)A.c_max;
-    add(C, rr, ok);
-  };
   // big nets, one at a time
   unsigned big = __ballot_sync(FULL, eff >= 32);
   int32_t visits = 0;
@@ -265,7 +279,9 @@ __device__ __forceinline__ int32_t rate_group(const RateArgs& A, int32_t u, int3
     const int32_t st = __shfl_sync(FULL, start, j);
     const int32_t sz = __shfl_sync(FULL, eff, j);
     const VT rj = __shfl_sync(FULL, r, j);
-    for (int32_t q0 = 32 * RATE_ILP * wt; q0 < sz; q0 += 32 * RATE_ILP * TW) {
+    const int32_t first = ((wt - run) % TW + TW) % TW;  // this warp's first chunk of the net
+    run += (sz + CH - 1) / CH;
+    for (int32_t q0 = CH * first; q0 < sz; q0 += CH * TW) {
       int32_t q[RATE_ILP];
       VT rr[RATE_ILP];
 #pragma unroll
@@ -282,7 +298,9 @@ __device__ __forceinline__ int32_t rate_group(const RateArgs& A, int32_t u, int3
   const int32_t small = eff < 32 ? eff : 0;
   const int32_t incl = warp_inclusive_scan(small);
   const int32_t Z = __shfl_sync(FULL, incl, 31);
-  for (int32_t f0 = 32 * RATE_ILP * wt; f0 < Z; f0 += 32 * RATE_ILP * TW) {
+  const int32_t first = ((wt - run) % TW + TW) % TW;
+  run += (Z + CH - 1) / CH;
+  for (int32_t f0 = CH * first; f0 < Z; f0 += CH * TW) {
     int32_t q[RATE_ILP];
     VT rr[RATE_ILP];
 #pragma unroll
@@ -304,6 +322,17 @@ __device__ __forceinline__ int32_t rate_group(const RateArgs& A, int32_t u, int3
     visit_batch(q, rr);
   }
   return wt == 0 ? visits + Z : 0;
+}
+
+// rate_group_raw with the admissibility filter of visit_filtered in front of
+// `add`.
+template <typename VT, typename Add>
+__device__ __forceinline__ int32_t rate_group(const RateArgs& A, int32_t u, int32_t cu, int32_t g0,
+                                              int32_t end, int wt, int TW, int32_t& run, Add add) {
+  auto visit = [&](const int32_t(&q)[RATE_ILP], const VT(&rr)[RATE_ILP]) {
+    visit_filtered<VT>(A, u, cu, q, rr, add);
+  };
+  return rate_group_raw<VT>(A, g0, end, wt, TW, run, visit);
 }
 
 template <typename VT>
@@ -379,8 +408,9 @@ __global__ void __launch_bounds__(TW * 32 * TEAMS) k_rate_team(RateArgs A, uint3
     const int32_t u = A.list[i];
     if (A.cst[u].y < 0) continue;  // joined a cluster in an earlier sub-round
     const int32_t cu = A.c[u], beg = A.ioff[u], end = A.ioff[u + 1];
+    int32_t run = 0;
     for (int32_t g0 = beg; g0 < end; g0 += 32)
-      visits += rate_group<VT>(A, u, cu, g0, end, wt, TW, each_visit<VT>([&](int32_t C, VT r) {
+      visits += rate_group<VT>(A, u, cu, g0, end, wt, TW, run, each_visit<VT>([&](int32_t C, VT r) {
         const int32_t sl = tab.add(C, r);
         if (sl >= 0) used[atomicAdd(&s_nused[team], 1)] = sl;
         else if (sl == ADD_FULL) dev_fail(A.status_word, DEV_HASH_FULL);
@@ -441,8 +471,9 @@ __global__ void __launch_bounds__(256) k_rate_dense(RateArgs A) {
     const int32_t u = A.list[i];
     if (A.cst[u].y < 0) continue;
     const int32_t cu = A.c[u], beg = A.ioff[u], end = A.ioff[u + 1];
+    int32_t run = 0;
     for (int32_t g0 = beg; g0 < end; g0 += 32)
-      visits += rate_group<VT>(A, u, cu, g0, end, wv, nw, each_visit<VT>([&](int32_t C, VT r) {
+      visits += rate_group<VT>(A, u, cu, g0, end, wv, nw, run, each_visit<VT>([&](int32_t C, VT r) {
         // every term is >= 1, so a zero before the add marks the first touch
         if (atomicAdd(&val[C], r) == (VT)0) used[atomicAdd(&s_nused, 1)] = C;
       }));
@@ -501,17 +532,18 @@ k_rate_split_acc(RateArgs A, const int32_t* __restrict__ split, const int32_t* _
     VT* val = tval + base;
     int32_t* used = tused + base;
     int32_t* nused = tnused + i;
+    int32_t run = 0;
     if (tab_dense[i]) {
       // direct-indexed: a reduction without a returned value; the argmax
       // scans the whole table, which is no larger than twice the visits
-      visits += rate_group<VT>(A, u, cu, g0, end, 0, 1, each_visit<VT>([&](int32_t C, VT r) {
+      visits += rate_group<VT>(A, u, cu, g0, end, 0, 1, run, each_visit<VT>([&](int32_t C, VT r) {
         atomicAdd(&val[C], r);
       }));
     } else {
       int32_t* key = tkey + base;
       const uint32_t mask = (uint32_t)tab_cap[i] - 1;
       visits += rate_group<VT>(
-          A, u, cu, g0, end, 0, 1,
+          A, u, cu, g0, end, 0, 1, run,
           [&](const int32_t(&C)[RATE_ILP], const VT(&rr)[RATE_ILP], const bool(&ok)[RATE_ILP]) {
             // the first slot of every visit of the batch is loaded at once
             uint32_t h[RATE_ILP];
@@ -556,6 +588,99 @@ k_rate_split_acc(RateArgs A, const int32_t* __restrict__ split, const int32_t* _
   }
 }
 
+// Hashed split nodes whose distinct candidates need more than one shared
+// table: the candidates are partitioned over P blocks by a hash of the
+// cluster id (part_of).  Every block walks all of the node's visits (the pin
+// clusters are read P times, from L2 at the levels where this happens) and
+// accumulates the candidates of its part in a PART_SLOTS-slot shared table;
+// P = ceil(min(W, n) / PART_D) keeps every table at most 60 % full, so no
+// insertion can fail.  A node of one part publishes its argmax directly;
+// otherwise each part leaves its best (rating, cluster) for the per-node
+// combine in k_rate_split_argmax.  Four teams of eight warps take the node's
+// groups of 32 nets in turn.
+__device__ __forceinline__ int32_t part_of(int32_t C, int32_t P) {
+  return (int32_t)(((uint64_t)((uint32_t)C * 0x85EBCA77u) * (uint32_t)P) >> 32);
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(PART_THREADS)
+k_rate_part(RateArgs A, const int32_t* __restrict__ split, const int32_t* __restrict__ part_node,
+            const int32_t* __restrict__ part_off, int32_t part_lo, int32_t part_hi,
+            VT* __restrict__ res_v, int32_t* __restrict__ res_c) {
+  using H = typename HashOf<VT>::type;
+  constexpr int NW = PART_THREADS / 32, TW = NW / PART_TEAMS;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ VT s_rv[NW];
+  __shared__ int32_t s_rc[NW];
+  if (subround_stopped(A)) return;
+  H tab = make_hash<H>(smem, PART_SLOTS);
+  for (uint32_t x = threadIdx.x; x < PART_SLOTS; x += blockDim.x) tab.init(x);
+  __syncthreads();
+  const int wv = warp_in_block(), team = wv / TW, wt = wv % TW;
+  int64_t visits = 0, incid = 0, nodes = 0;
+  for (int32_t t = part_lo + blockIdx.x; t < part_hi; t += gridDim.x) {
+    const int32_t i = part_node[t];
+    const int32_t u = split[i];
+    if (A.cst[u].y < 0) continue;  // joined a cluster in an earlier sub-round
+    const int32_t P = part_off[i + 1] - part_off[i], k = t - part_off[i];
+    const int32_t cu = A.c[u], beg = A.ioff[u], end = A.ioff[u + 1];
+    auto visit = [&](const int32_t(&q)[RATE_ILP], const VT(&rr)[RATE_ILP]) {
+      int32_t C[RATE_ILP];
+#pragma unroll
+      for (int j = 0; j < RATE_ILP; ++j) C[j] = q[j] >= 0 ? A.rpin[q[j]] : -1;
+      bool own[RATE_ILP];
+#pragma unroll
+      for (int j = 0; j < RATE_ILP; ++j)
+        own[j] = C[j] >= 0 && C[j] != u && (P == 1 || part_of(C[j], P) == k);
+      int2 cs[RATE_ILP];
+#pragma unroll
+      for (int j = 0; j < RATE_ILP; ++j) cs[j] = own[j] ? A.cst[C[j]] : make_int2(0x7fffffff, 0);
+#pragma unroll
+      for (int j = 0; j < RATE_ILP; ++j) {
+        if (!own[j] || cs[j].y == A.s || (long long)cs[j].x + cu > (long long)A.c_max) continue;
+        if (tab.add(C[j], rr[j]) == ADD_FULL) dev_fail(A.status_word, DEV_HASH_FULL);
+      }
+    };
+    int32_t run = 0;
+    int64_t v = 0;
+    for (int32_t g0 = beg + 32 * team; g0 < end; g0 += 32 * PART_TEAMS)
+      v += rate_group_raw<VT>(A, g0, end, wt, TW, run, visit);
+    if (k == 0) visits += v;
+    __syncthreads();
+    VT bv = 0;
+    int32_t bc = -1;
+    for (uint32_t x = threadIdx.x; x < PART_SLOTS; x += blockDim.x) {
+      int32_t C;
+      VT val;
+      tab.take(x, C, val);
+      better(bv, bc, val, C);
+    }
+    warp_argmax(bv, bc);
+    if (lane_id() == 0) {
+      s_rv[wv] = bv;
+      s_rc[wv] = bc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int x = 1; x < NW; ++x) better(bv, bc, s_rv[x], s_rc[x]);
+      if (P == 1) {
+        publish(A, u, bc);
+        ++nodes;
+      } else {
+        res_v[t] = bv;
+        res_c[t] = bc;
+      }
+      if (k == 0) incid += end - beg;
+    }
+    __syncthreads();
+  }
+  if (lane_id() == 0 && visits) atomicAdd(&A.stats[ST_PINS], (unsigned long long)visits);
+  if (threadIdx.x == 0 && (incid || nodes)) {
+    atomicAdd(&A.stats[ST_INCID], (unsigned long long)incid);
+    atomicAdd(&A.stats[ST_NODES], (unsigned long long)nodes);
+  }
+}
+
 // class 3, phase 2: one block per class-3 node of the sub-round: argmax over
 // its used slots, which are cleared on the way for the next sub-round
 template <typename VT>
@@ -564,18 +689,26 @@ k_rate_split_argmax(RateArgs A, const int32_t* __restrict__ split, int32_t lo, i
                     const int64_t* __restrict__ tab_off, const int64_t* __restrict__ tab_cap,
                     const int8_t* __restrict__ tab_dense,
                     int64_t tab_base, int32_t* __restrict__ tkey, VT* __restrict__ tval,
-                    const int32_t* __restrict__ tused, int32_t* __restrict__ tnused) {
+                    const int32_t* __restrict__ tused, int32_t* __restrict__ tnused,
+                    const int32_t* __restrict__ part_off, const VT* __restrict__ res_v,
+                    const int32_t* __restrict__ res_c) {
   __shared__ VT s_rv[32];
   __shared__ int32_t s_rc[32];
   if (subround_stopped(A)) return;
   for (int32_t i = lo + blockIdx.x; i < hi; i += gridDim.x) {
     const int32_t u = split[i];
     if (A.cst[u].y < 0) continue;
-    const int64_t base = tab_off[i] - tab_base;
     const bool dense = tab_dense[i] != 0;
+    const int32_t P = part_off[i + 1] - part_off[i];
+    if (P == 1) continue;  // published by its only part
+    const int64_t base = tab_off[i] - tab_base;
     VT bv = 0;
     int32_t bc = -1;
-    if (dense) {
+    if (P > 1) {
+      // the parts hold disjoint candidates: the best of their bests
+      for (int32_t t = part_off[i] + threadIdx.x; t < part_off[i + 1]; t += blockDim.x)
+        better(bv, bc, res_v[t], res_c[t]);
+    } else if (dense) {
       const int32_t cap = (int32_t)tab_cap[i];
       for (int32_t C = threadIdx.x; C < cap; C += blockDim.x) {
         const VT v = tval[base + C];
@@ -693,23 +826,33 @@ __global__ void k_node_scatter(const int32_t* __restrict__ key_of, int32_t n, in
   }
 }
 
-// Item count (groups of 32 incident nets), table mode and capacity of every
-// class-3 node: direct-indexed (n entries) when n <= min(2 W(u), 65536), so
-// the table costs no more than the accumulation; else hashed, a power of two
-// >= 2 min(W, n) + 2.
+// Work items and global table of every split node (D = min(W(u), n)):
+//   direct-indexed global table (n entries) when n <= min(2 W(u), 65536), so
+//   the table costs no more than the accumulation: groups of 32 nets over
+//   the grid (items);
+//   else P = ceil(D / PART_D) shared-memory parts when P <= PART_MAX (no
+//   global table);
+//   else a global hash table of a power of two >= 2 D + 2 slots, with items.
 __global__ void k_split_sizes(const int32_t* __restrict__ split, int32_t nsplit,
                               const int32_t* __restrict__ ioff, const int32_t* __restrict__ wof,
-                              int32_t n, int32_t* __restrict__ items, int32_t* __restrict__ cap,
-                              int8_t* __restrict__ dense) {
+                              int32_t n, int32_t* __restrict__ items, int32_t* __restrict__ parts,
+                              int32_t* __restrict__ cap, int8_t* __restrict__ dense) {
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nsplit; i += gridDim.x * blockDim.x) {
     const int32_t u = split[i];
-    items[i] = (ioff[u + 1] - ioff[u] + 31) / 32;
+    const int32_t deg = ioff[u + 1] - ioff[u];
     const bool d = n <= SPLIT_DENSE_MAX && (int64_t)n <= 2 * (int64_t)wof[u];
+    const int32_t D = min(wof[u], n);
+    const int32_t P = d ? 0 : (D + PART_D - 1) / PART_D;
+    const bool part = !d && P <= PART_MAX;
+    items[i] = part ? 0 : (deg + 31) / 32;
+    parts[i] = part ? P : 0;
     dense[i] = d ? 1 : 0;
     if (d) {
       cap[i] = n;
+    } else if (part) {
+      cap[i] = 0;
     } else {
-      const int64_t want = 2 * (int64_t)min(wof[u], n) + 2;
+      const int64_t want = 2 * (int64_t)D + 2;
       int64_t c = 1;
       while (c < want) c <<= 1;
       cap[i] = (int32_t)c;
@@ -1074,18 +1217,22 @@ void set_rate_attrs() {
   allow_smem(k_rate_team<VT, 8, 1>);
   if (sizeof(VT) == 4) allow_smem(k_rate_team<VT, 16, 1>);
   allow_smem(k_rate_dense<VT>);
+  HG_CUDA(cudaFuncSetAttribute(k_rate_part<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(PART_SLOTS * HashOf<VT>::type::BYTES_PER_SLOT)));
   done = true;
 }
 
 struct SplitPlan {
   std::vector<int32_t> lo, hi;          // class-3 node range of every sub-round (in split order)
   std::vector<int32_t> item_lo, item_hi;
+  std::vector<int32_t> part_lo, part_hi;
   std::vector<int64_t> tab_lo;          // first table entry of every sub-round
   int64_t tab_span = 0;                 // largest table footprint of one sub-round
   const int32_t* split = nullptr;
-  DBuf<int32_t> item_node, item_off, tnused;
+  DBuf<int32_t> item_node, item_off, part_node, part_off, tnused, res_c;
   DBuf<int64_t> tab_off, tab_cap;
   DBuf<int8_t> tab_dense;
+  DBuf<unsigned char> res_v;
   DBuf<int32_t> tkey, tused;
   DBuf<unsigned char> tval;
 };
@@ -1141,15 +1288,26 @@ void rate_subround(const Ctx& cx, RateArgs A, const std::vector<int32_t>& hoff, 
           A, sp.split, sp.item_node.p, sp.item_off.p, sp.tab_off.p, sp.tab_cap.p, sp.tab_dense.p,
           sp.item_lo[s], sp.item_hi[s], sp.tab_lo[s], sp.tkey.p, tval, sp.tused.p, sp.tnused.p);
       check_launch("rate_split_acc");
+      cc.rating_launches += 1;
+    }
+    const int32_t parts = sp.part_hi[s] - sp.part_lo[s];
+    if (parts > 0) {
+      using H = typename HashOf<VT>::type;
+      const size_t bytes = (size_t)PART_SLOTS * H::BYTES_PER_SLOT;
+      k_rate_part<VT><<<grid_for(parts, 1, cx.num_sms, 1), PART_THREADS, bytes, cx.stream>>>(
+          A, sp.split, sp.part_node.p, sp.part_off.p, sp.part_lo[s], sp.part_hi[s],
+          reinterpret_cast<VT*>(sp.res_v.p), sp.res_c.p);
+      check_launch("rate_part");
+      cc.rating_launches += 1;
     }
     const int g2 = grid_for(sp.hi[s] - sp.lo[s], 1, cx.num_sms, 8);
     k_rate_split_argmax<VT><<<g2, ARGMAX_THREADS, 0, cx.stream>>>(
         A, sp.split, sp.lo[s], sp.hi[s], sp.tab_off.p, sp.tab_cap.p, sp.tab_dense.p, sp.tab_lo[s],
-        sp.tkey.p, tval,
-        sp.tused.p, sp.tnused.p);
+        sp.tkey.p, tval, sp.tused.p, sp.tnused.p, sp.part_off.p,
+        reinterpret_cast<const VT*>(sp.res_v.p), sp.res_c.p);
     timer.end();
     check_launch("rate_split_argmax");
-    cc.rating_launches += 2;
+    cc.rating_launches += 1;
   }
 }
 
@@ -1236,6 +1394,8 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   sp.hi.resize(S);
   sp.item_lo.assign(S, 0);
   sp.item_hi.assign(S, 0);
+  sp.part_lo.assign(S, 0);
+  sp.part_hi.assign(S, 0);
   sp.tab_lo.assign(S, 0);
   const int32_t split_base = hoff[SPLIT_CLASS * S];
   const int32_t nsplit = hoff[NCLASS * S] - split_base;
@@ -1245,10 +1405,12 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   }
   sp.split = list.p + split_base;
   if (nsplit > 0) {
-    DBuf<int32_t> items, cap32;
+    DBuf<int32_t> items, parts, cap32;
     items.alloc(&cx.alloc, (size_t)nsplit + 1);
+    parts.alloc(&cx.alloc, (size_t)nsplit + 1);
     cap32.alloc(&cx.alloc, (size_t)nsplit + 1);
     sp.item_off.alloc(&cx.alloc, (size_t)nsplit + 1);
+    sp.part_off.alloc(&cx.alloc, (size_t)nsplit + 1);
     sp.tab_off.alloc(&cx.alloc, (size_t)nsplit + 1);
     sp.tab_cap.alloc(&cx.alloc, (size_t)nsplit + 1);
     sp.tab_dense.alloc(&cx.alloc, (size_t)nsplit + 1);
@@ -1256,15 +1418,18 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
     HG_CUDA(cudaMemsetAsync(sp.tnused.p, 0, sp.tnused.bytes(), cx.stream));
     const int gs = grid_for(nsplit, 256, cx.num_sms, 4);
     k_split_sizes<<<gs, 256, 0, cx.stream>>>(sp.split, nsplit, L.ioff.p, wof.p, n, items.p,
-                                             cap32.p, sp.tab_dense.p);
+                                             parts.p, cap32.p, sp.tab_dense.p);
     check_launch("split_sizes");
     scan_exclusive_i32(cx, items.p, sp.item_off.p, nsplit, sp.item_off.p + nsplit);
+    scan_exclusive_i32(cx, parts.p, sp.part_off.p, nsplit, sp.part_off.p + nsplit);
     scan_exclusive_i32_to_i64(cx, cap32.p, sp.tab_off.p, nsplit, sp.tab_off.p + nsplit);
     k_widen<<<gs, 256, 0, cx.stream>>>(cap32.p, sp.tab_cap.p, nsplit);
     check_launch("widen");
-    std::vector<int32_t> hio((size_t)nsplit + 1);
+    std::vector<int32_t> hio((size_t)nsplit + 1), hso((size_t)nsplit + 1);
     std::vector<int64_t> hto((size_t)nsplit + 1);
     HG_CUDA(cudaMemcpyAsync(hio.data(), sp.item_off.p, sizeof(int32_t) * hio.size(),
+                            cudaMemcpyDeviceToHost, cx.stream));
+    HG_CUDA(cudaMemcpyAsync(hso.data(), sp.part_off.p, sizeof(int32_t) * hso.size(),
                             cudaMemcpyDeviceToHost, cx.stream));
     HG_CUDA(cudaMemcpyAsync(hto.data(), sp.tab_off.p, sizeof(int64_t) * hto.size(),
                             cudaMemcpyDeviceToHost, cx.stream));
@@ -1272,12 +1437,20 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
     for (int s = 0; s < S; ++s) {
       sp.item_lo[s] = hio[sp.lo[s]];
       sp.item_hi[s] = hio[sp.hi[s]];
+      sp.part_lo[s] = hso[sp.lo[s]];
+      sp.part_hi[s] = hso[sp.hi[s]];
       sp.tab_lo[s] = hto[sp.lo[s]];
       sp.tab_span = std::max<int64_t>(sp.tab_span, hto[sp.hi[s]] - hto[sp.lo[s]]);
     }
     sp.item_node.alloc(&cx.alloc, (size_t)std::max<int32_t>(hio[nsplit], 1));
     k_split_items<<<gs, 256, 0, cx.stream>>>(sp.item_off.p, nsplit, sp.item_node.p);
     check_launch("split_items");
+    const size_t nparts = (size_t)std::max<int32_t>(hso[nsplit], 1);
+    sp.part_node.alloc(&cx.alloc, nparts);
+    sp.res_v.alloc(&cx.alloc, nparts * vbytes);
+    sp.res_c.alloc(&cx.alloc, nparts);
+    k_split_items<<<gs, 256, 0, cx.stream>>>(sp.part_off.p, nsplit, sp.part_node.p);
+    check_launch("split_parts");
     const size_t span = (size_t)std::max<int64_t>(sp.tab_span, 1);
     sp.tval.alloc(&cx.alloc, span * vbytes);
     sp.tkey.alloc(&cx.alloc, span);
@@ -1290,7 +1463,7 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
       k_init_table<unsigned long long><<<gi, 256, 0, cx.stream>>>(
           sp.tkey.p, reinterpret_cast<unsigned long long*>(sp.tval.p), span);
     check_launch("init_table");
-    if (cx.launches) *cx.launches += 10;
+    if (cx.launches) *cx.launches += 11;
   }
 
   // (net, cluster) -> first position map: at most one key per rated pin at
