@@ -56,11 +56,10 @@ constexpr int NCLASS = 5;
 constexpr int SPLIT_CLASS = NCLASS - 1;
 constexpr int32_t D_WARP = 256;
 constexpr int32_t D_PAIR = 1024;
+constexpr int32_t D_QUAD = 2048;
 constexpr int32_t D_BLOCK = 4096;
-constexpr int32_t D_WIDE = 8192;
-constexpr int32_t SPLIT_W = 16384;       // largest W of a hashed 256-thread block node
+constexpr int32_t TEAM_W = 65536;        // largest W of a node rated by one eight-warp team
 constexpr int32_t DENSE_W = 32768;       // largest W of a direct-indexed block node
-constexpr int32_t BIG_W = 65536;         // largest W of a node rated by one 512-thread block
 constexpr int32_t SPLIT_DENSE_MAX = 65536;
 constexpr int SPLIT_WARPS = 8;
 constexpr int PART_THREADS = 1024;
@@ -745,22 +744,23 @@ k_rate_split_argmax(RateArgs A, const int32_t* __restrict__ split, int32_t lo, i
 // ------------------------------------------------------- node bucketing
 
 // Team class of a node from W(u) and D = min(W(u), n):
-//   0 warp (512 slots)            D <= 256
-//   1 two warps (2048 slots)      D <= 1024 (unless the level is dense)
-//   2 block, direct-indexed       the level fits a dense shared table, W <= 32768
-//     block, 8192-slot hash       D <= 4096, W <= 16384
-//   3 512-thread block, 16384 slots (32-bit ratings only)  D <= 8192, W <= 65536
-//   4 split over the grid         the rest
+//   0 warp (512 slots)                     D <= 256
+//   1 two warps (2048 slots)               D <= 1024 (unless the level is dense)
+//   2 block, direct-indexed                the level fits a dense shared table,
+//                                          W <= 32768
+//     eight warps, 4096-slot hash          D <= 2048, W <= 65536 (other levels)
+//   3 eight warps, 8192-slot hash          D <= 4096, W <= 65536 (other levels)
+//   4 split over the grid                  the rest
 __device__ __forceinline__ int rate_class(int64_t W, int32_t n, bool dense_block, bool narrow) {
   const int64_t D = W < n ? W : n;  // bound on the distinct candidate clusters
+  (void)narrow;
   if (D <= D_WARP) return 0;
   if (dense_block && W <= DENSE_W) return 2;
   if (D <= D_PAIR) return 1;
-  // measured on GB300: grid-split nodes (class 4) sustain more visits per
-  // second than one node per large shared-memory block, whose table size
-  // limits occupancy; the hashed block (2) and wide block (3) stay available
-  // but are not selected
-  (void)narrow;
+  if (!dense_block && W <= TEAM_W) {
+    if (D <= D_QUAD) return 2;
+    if (D <= D_BLOCK) return 3;
+  }
   return 4;
 }
 
@@ -1215,7 +1215,8 @@ void set_rate_attrs() {
   allow_smem(k_rate_team<VT, 1, 8>);
   allow_smem(k_rate_team<VT, 2, 4>);
   allow_smem(k_rate_team<VT, 8, 1>);
-  if (sizeof(VT) == 4) allow_smem(k_rate_team<VT, 16, 1>);
+  allow_smem(k_rate_team<VT, 8, 2>);
+  allow_smem(k_rate_team<VT, 8, 4>);
   allow_smem(k_rate_dense<VT>);
   HG_CUDA(cudaFuncSetAttribute(k_rate_part<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(PART_SLOTS * HashOf<VT>::type::BYTES_PER_SLOT)));
@@ -1267,9 +1268,11 @@ void rate_subround(const Ctx& cx, RateArgs A, const std::vector<int32_t>& hoff, 
       const int per_sm = std::max<int>(1, (int)(SMEM_BUDGET / bytes));
       k_rate_dense<VT><<<grid_for(A.count, 1, cx.num_sms, per_sm), 256, bytes, cx.stream>>>(A);
     } else if (cls == 2) {
-      launch_team<VT, 8, 1>(cx, A, 2 * D_BLOCK);
-    } else if (sizeof(VT) == 4) {  // class 3 exists for 32-bit ratings only
-      launch_team<VT, 16, 1>(cx, A, 2 * D_WIDE);
+      if (sizeof(VT) == 4) launch_team<VT, 8, 4>(cx, A, 2 * D_QUAD);
+      else launch_team<VT, 8, 2>(cx, A, 2 * D_QUAD);
+    } else {
+      if (sizeof(VT) == 4) launch_team<VT, 8, 2>(cx, A, 2 * D_BLOCK);
+      else launch_team<VT, 8, 1>(cx, A, 2 * D_BLOCK);
     }
     timer.end();
     check_launch("rate_team");
