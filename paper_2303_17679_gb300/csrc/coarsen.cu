@@ -766,16 +766,17 @@ __device__ __forceinline__ int rate_class(int64_t W, int32_t n, bool dense_block
 
 // W(u) (pins of rated nets) of every node, and the largest bound on a node's
 // rating (sum of its net terms), which decides the value width.
+// One warp per node, lanes over its incident nets.
 __global__ void k_node_work(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
                             const int32_t* __restrict__ eoff, const int32_t* __restrict__ w,
                             int32_t n, int T, int32_t* __restrict__ wof,
                             unsigned long long* __restrict__ max_r) {
   unsigned long long lr = 0;
-  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
-       u += (int64_t)gridDim.x * blockDim.x) {
-    int64_t W = 0;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
+    long long W = 0;
     unsigned long long R = 0;
-    for (int32_t j = ioff[u]; j < ioff[u + 1]; ++j) {
+    for (int32_t j = ioff[u] + lane_id(); j < ioff[u + 1]; j += 32) {
       const int32_t e = inets[j];
       const int32_t sz = eoff[e + 1] - eoff[e];
       if (sz >= 2 && sz <= T) {
@@ -783,11 +784,12 @@ __global__ void k_node_work(const int32_t* __restrict__ ioff, const int32_t* __r
         R += (((unsigned long long)w[e]) << 20) / (unsigned long long)(sz - 1);
       }
     }
+    W = warp_sum(W);
+    R = warp_sum(R);
     lr = R > lr ? R : lr;
-    wof[u] = W > 0x7fffffff ? 0x7fffffff : (int32_t)W;
+    if (lane_id() == 0) wof[u] = W > 0x7fffffff ? 0x7fffffff : (int32_t)W;
   }
-  const unsigned long long lr2 = warp_max(lr);
-  if (lane_id() == 0 && lr2) atomicMax(max_r, lr2);
+  if (lane_id() == 0 && lr) atomicMax(max_r, lr);
 }
 
 // key = class * S + sub-round of every node with W(u) > 0, and the counts.
@@ -1366,8 +1368,8 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   k_init_cluster<<<g_nodes, 256, 0, cx.stream>>>(L.c.p, n, P.seed, P.level, S, L.rep.p, cst.p,
                                                  slot_of.p);
   check_launch("init_cluster");
-  k_node_work<<<g_nodes, 256, 0, cx.stream>>>(L.ioff.p, L.inets.p, L.eoff.p, L.w.p, n, P.T,
-                                               wof.p, max_r.p);
+  k_node_work<<<grid_for(n, 8, cx.num_sms, 16), 256, 0, cx.stream>>>(
+      L.ioff.p, L.inets.p, L.eoff.p, L.w.p, n, P.T, wof.p, max_r.p);
   check_launch("node_work");
   const unsigned long long hmax_r = (unsigned long long)read_i64(cx, (const int64_t*)max_r.p);
   // 32-bit rating words when no node's total rating can reach 2^31; block

@@ -150,9 +150,12 @@ enum SubroundWord { SW_MOVES = 0, SW_APPROVED = 1, SW_WORDS = 4 };
 // With b(u) = w(nets where u is the only pin of its block) and W_I = w(I(u)),
 // the gain of Sec. 6 is
 //   g(u, t) = b(u) - W_I + w({e in I(u) : t in Lambda(e)}),
-// evaluated for all t at once: lane L accumulates blocks L and L + 32 while
-// the warp broadcasts each incident net's (weight, Lambda) in turn.  A warp
-// handles the chunks c0 = beg + 32 * (first + i * stride) of I(u).
+// evaluated for all t at once: every lane takes one incident net and adds
+// w(e) to the warp's shared counter of each block of Lambda(e), so the work
+// is the sum of lambda(e).  Counters are int32: the total net weight is
+// below 2^31.  A warp handles the chunks c0 = beg + 32 * (first + i * stride)
+// of I(u); acc0 / acc1 are filled from the counters of blocks lane and
+// lane + 32 by gain_collect.
 struct GainPart {
   long long acc0, acc1, ben, wsum;
 };
@@ -162,29 +165,35 @@ __device__ __forceinline__ GainPart gain_partial(const int32_t* __restrict__ ine
                                                  const int32_t* __restrict__ phi,
                                                  const unsigned long long* __restrict__ lam, int k,
                                                  int from, int32_t beg, int32_t end, int first,
-                                                 int stride) {
+                                                 int stride, int32_t* s_cnt) {
   const int lane = lane_id();
   GainPart g{0, 0, 0, 0};
   for (int32_t c0 = beg + 32 * first; c0 < end; c0 += 32 * stride) {
     const int32_t j = c0 + lane;
-    int32_t we = 0;
-    unsigned long long le = 0;
     if (j < end) {
       const int32_t e = inets[j];
-      we = w[e];
-      le = lam[e];
+      const int32_t we = w[e];
+      unsigned long long le = lam[e];
       if (phi[(int64_t)e * k + from] == 1) g.ben += we;
       g.wsum += we;
-    }
-    const int cnt = min(32, end - c0);
-    for (int jj = 0; jj < cnt; ++jj) {
-      const int32_t wj = __shfl_sync(FULL, we, jj);
-      const unsigned long long lj = __shfl_sync(FULL, le, jj);
-      if ((lj >> lane) & 1ull) g.acc0 += wj;
-      if ((lj >> (lane + 32)) & 1ull) g.acc1 += wj;
+      while (le) {
+        atomicAdd(&s_cnt[__ffsll((long long)le) - 1], we);
+        le &= le - 1;
+      }
     }
   }
   return g;
+}
+
+// Moves the warp's block counters into acc0 / acc1 and clears them.
+__device__ __forceinline__ void gain_collect(GainPart& g, int32_t* s_cnt) {
+  const int lane = lane_id();
+  __syncwarp();
+  g.acc0 = s_cnt[lane];
+  g.acc1 = s_cnt[lane + 32];
+  s_cnt[lane] = 0;
+  s_cnt[lane + 32] = 0;
+  __syncwarp();
 }
 
 // Best target of the warp's complete accumulators: (gain desc, t asc), t != from.
@@ -248,14 +257,20 @@ __device__ __forceinline__ void gain_emit(const GainArgs& A, int32_t u, int from
 
 // class 0 (at most GAIN_BLOCK_DEG incident nets): one warp per node
 __global__ void __launch_bounds__(WARPS * 32) k_lp_gain_warp(GainArgs A) {
+  __shared__ int32_t s_cnt[WARPS][64];
   const int lane = lane_id();
+  int32_t* cnt = s_cnt[warp_in_block()];
+  cnt[lane] = 0;
+  cnt[lane + 32] = 0;
+  __syncwarp();
   const int32_t lo = A.sr_off[2 * A.s], hi = A.sr_off[2 * A.s + 1];
   int64_t incid = 0;
   for (int32_t i = lo + blockIdx.x * WARPS + warp_in_block(); i < hi; i += gridDim.x * WARPS) {
     const int32_t u = A.list[i];
     const int from = A.part[u];
     const int32_t beg = A.ioff[u], end = A.ioff[u + 1];
-    const GainPart g = gain_partial(A.inets, A.w, A.phi, A.lam, A.k, from, beg, end, 0, 1);
+    GainPart g = gain_partial(A.inets, A.w, A.phi, A.lam, A.k, from, beg, end, 0, 1, cnt);
+    gain_collect(g, cnt);
     long long bg;
     int bt;
     gain_best(g, A.k, from, bg, bt);
@@ -270,14 +285,20 @@ __global__ void __launch_bounds__(WARPS * 32) k_lp_gain_warp(GainArgs A) {
 __global__ void __launch_bounds__(WARPS * 32) k_lp_gain_block(GainArgs A) {
   __shared__ long long s_acc[WARPS][64];
   __shared__ long long s_bw[WARPS][2];
+  __shared__ int32_t s_cnt[WARPS][64];
   const int lane = lane_id(), wv = warp_in_block();
+  int32_t* cnt = s_cnt[wv];
+  cnt[lane] = 0;
+  cnt[lane + 32] = 0;
+  __syncwarp();
   const int32_t lo = A.sr_off[2 * A.s + 1], hi = A.sr_off[2 * A.s + 2];
   int64_t incid = 0;
   for (int32_t i = lo + blockIdx.x; i < hi; i += gridDim.x) {
     const int32_t u = A.list[i];
     const int from = A.part[u];
     const int32_t beg = A.ioff[u], end = A.ioff[u + 1];
-    GainPart g = gain_partial(A.inets, A.w, A.phi, A.lam, A.k, from, beg, end, wv, WARPS);
+    GainPart g = gain_partial(A.inets, A.w, A.phi, A.lam, A.k, from, beg, end, wv, WARPS, cnt);
+    gain_collect(g, cnt);
     s_acc[wv][lane] = g.acc0;
     s_acc[wv][lane + 32] = g.acc1;
     const long long b = warp_sum(g.ben), ws = warp_sum(g.wsum);
