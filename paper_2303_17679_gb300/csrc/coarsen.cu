@@ -81,7 +81,7 @@ struct RateArgs {
   const int32_t* inets;
   const int32_t* eoff;
   const int32_t* rpin;
-  const int32_t* w;
+  const unsigned long long* rterm;  // Q20 net term of every rated net, 0 otherwise
   const int32_t* c;
   const int2* cst;  // {cw, status}
   int s, T;
@@ -253,22 +253,35 @@ __device__ __forceinline__ void visit_filtered(const RateArgs& A, int32_t u, int
 // across groups; `run` is advanced past the group's chunks.  Returns the
 // group's pin visits in warp 0 (0 in the other warps, so the team counts each
 // visit once).
-template <typename VT, typename Visit>
-__device__ __forceinline__ int32_t rate_group_raw(const RateArgs& A, int32_t g0, int32_t end,
-                                                  int wt, int TW, int32_t& run, Visit& visit_batch) {
-  constexpr int32_t CH = 32 * RATE_ILP;
-  const int lane = lane_id();
-  int32_t start = 0, eff = 0;
-  VT r = 0;
-  if (g0 + lane < end) {
-    const int32_t e = A.inets[g0 + lane];
-    start = A.eoff[e];
-    const int32_t size = A.eoff[e + 1] - start;
-    if (size >= 2 && size <= A.T) {
-      eff = size;
-      r = (VT)((((long long)A.w[e]) << 20) / (size - 1));
+// Per lane: first pin, rated size (0 if the net is not rated) and Q20 term of
+// one incident net.
+template <typename VT>
+struct NetMeta {
+  int32_t start, eff;
+  VT r;
+};
+
+template <typename VT>
+__device__ __forceinline__ NetMeta<VT> net_meta(const RateArgs& A, int32_t e) {
+  NetMeta<VT> m{0, 0, (VT)0};
+  if (e >= 0) {
+    const unsigned long long r = A.rterm[e];
+    m.start = A.eoff[e];
+    if (r != 0) {
+      m.eff = A.eoff[e + 1] - m.start;
+      m.r = (VT)r;
     }
   }
+  return m;
+}
+
+template <typename VT, typename Visit>
+__device__ __forceinline__ int32_t walk_group(const NetMeta<VT>& m, int wt, int TW, int32_t& run,
+                                              Visit& visit_batch) {
+  constexpr int32_t CH = 32 * RATE_ILP;
+  const int lane = lane_id();
+  const int32_t start = m.start, eff = m.eff;
+  const VT r = m.r;
   // big nets, one at a time
   unsigned big = __ballot_sync(FULL, eff >= 32);
   int32_t visits = 0;
@@ -323,15 +336,56 @@ __device__ __forceinline__ int32_t rate_group_raw(const RateArgs& A, int32_t g0,
   return wt == 0 ? visits + Z : 0;
 }
 
-// rate_group_raw with the admissibility filter of visit_filtered in front of
-// `add`.
+template <typename VT, typename Visit>
+__device__ __forceinline__ int32_t rate_group_raw(const RateArgs& A, int32_t g0, int32_t end,
+                                                  int wt, int TW, int32_t& run, Visit& visit_batch) {
+  const int32_t e = g0 + lane_id() < end ? A.inets[g0 + lane_id()] : -1;
+  return walk_group<VT>(net_meta<VT>(A, e), wt, TW, run, visit_batch);
+}
+
+// The groups g0 = first, first + step, ... (< end) of I(u), walked as by
+// rate_group_raw with the loads of the next group's net metadata and of the
+// net ids of the group after it issued before the current group is walked.
+template <typename VT, typename Visit>
+__device__ __forceinline__ int64_t rate_groups_raw(const RateArgs& A, int32_t first, int32_t end,
+                                                   int32_t step, int wt, int TW, int32_t& run,
+                                                   Visit& visit_batch) {
+  const int lane = lane_id();
+  int64_t visits = 0;
+  if (first >= end) return 0;
+  int32_t g = first;
+  NetMeta<VT> m = net_meta<VT>(A, g + lane < end ? A.inets[g + lane] : -1);
+  int32_t e_next = g + step + lane < end ? A.inets[g + step + lane] : -1;
+  while (g < end) {
+    const int32_t gn = g + step;
+    const NetMeta<VT> mn = net_meta<VT>(A, e_next);
+    e_next = gn + step + lane < end ? A.inets[gn + step + lane] : -1;
+    visits += walk_group<VT>(m, wt, TW, run, visit_batch);
+    m = mn;
+    g = gn;
+  }
+  return visits;
+}
+
+// rate_group_raw / rate_groups_raw with the admissibility filter of
+// visit_filtered in front of `add`.
 template <typename VT, typename Add>
 __device__ __forceinline__ int32_t rate_group(const RateArgs& A, int32_t u, int32_t cu, int32_t g0,
                                               int32_t end, int wt, int TW, int32_t& run, Add add) {
-  auto visit = [&](const int32_t(&q)[RATE_ILP], const VT(&rr)[RATE_ILP]) {
+  auto visit = [&](const int32_t(&q)[RATE_ILP], const VT(&rr)[RATE_ILP]) HG_INLINE {
     visit_filtered<VT>(A, u, cu, q, rr, add);
   };
   return rate_group_raw<VT>(A, g0, end, wt, TW, run, visit);
+}
+
+template <typename VT, typename Add>
+__device__ __forceinline__ int64_t rate_groups(const RateArgs& A, int32_t u, int32_t cu,
+                                               int32_t first, int32_t end, int32_t step, int wt,
+                                               int TW, int32_t& run, Add add) {
+  auto visit = [&](const int32_t(&q)[RATE_ILP], const VT(&rr)[RATE_ILP]) HG_INLINE {
+    visit_filtered<VT>(A, u, cu, q, rr, add);
+  };
+  return rate_groups_raw<VT>(A, first, end, step, wt, TW, run, visit);
 }
 
 template <typename VT>
@@ -387,7 +441,7 @@ constexpr size_t team_bytes(uint32_t slots) {
 }
 
 template <typename VT, int TW, int TEAMS>
-__global__ void __launch_bounds__(TW * 32 * TEAMS) k_rate_team(RateArgs A, uint32_t slots) {
+__global__ void __launch_bounds__(TW * 32 * TEAMS, 1024 / (TW * 32 * TEAMS)) k_rate_team(RateArgs A, uint32_t slots) {
   using H = typename HashOf<VT>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ VT s_rv[TEAMS][TW];
@@ -408,12 +462,12 @@ __global__ void __launch_bounds__(TW * 32 * TEAMS) k_rate_team(RateArgs A, uint3
     if (A.cst[u].y < 0) continue;  // joined a cluster in an earlier sub-round
     const int32_t cu = A.c[u], beg = A.ioff[u], end = A.ioff[u + 1];
     int32_t run = 0;
-    for (int32_t g0 = beg; g0 < end; g0 += 32)
-      visits += rate_group<VT>(A, u, cu, g0, end, wt, TW, run, each_visit<VT>([&](int32_t C, VT r) {
-        const int32_t sl = tab.add(C, r);
-        if (sl >= 0) used[atomicAdd(&s_nused[team], 1)] = sl;
-        else if (sl == ADD_FULL) dev_fail(A.status_word, DEV_HASH_FULL);
-      }));
+    visits += rate_groups<VT>(A, u, cu, beg, end, 32, wt, TW, run,
+                              each_visit<VT>([&](int32_t C, VT r) HG_INLINE {
+                                const int32_t sl = tab.add(C, r);
+                                if (sl >= 0) used[atomicAdd(&s_nused[team], 1)] = sl;
+                                else if (sl == ADD_FULL) dev_fail(A.status_word, DEV_HASH_FULL);
+                              }));
     team_sync<TW>(team);
     VT bv = 0;
     int32_t bc = -1;
@@ -452,7 +506,7 @@ __global__ void __launch_bounds__(TW * 32 * TEAMS) k_rate_team(RateArgs A, uint3
 // class 2 on small levels: one block per node with a table direct-indexed by
 // cluster id (n values, then the list of touched ids)
 template <typename VT>
-__global__ void __launch_bounds__(256) k_rate_dense(RateArgs A) {
+__global__ void __launch_bounds__(256, 4) k_rate_dense(RateArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int32_t s_nused;
   __shared__ VT s_rv[8];
@@ -471,11 +525,13 @@ __global__ void __launch_bounds__(256) k_rate_dense(RateArgs A) {
     if (A.cst[u].y < 0) continue;
     const int32_t cu = A.c[u], beg = A.ioff[u], end = A.ioff[u + 1];
     int32_t run = 0;
-    for (int32_t g0 = beg; g0 < end; g0 += 32)
-      visits += rate_group<VT>(A, u, cu, g0, end, wv, nw, run, each_visit<VT>([&](int32_t C, VT r) {
-        // every term is >= 1, so a zero before the add marks the first touch
-        if (atomicAdd(&val[C], r) == (VT)0) used[atomicAdd(&s_nused, 1)] = C;
-      }));
+    visits += rate_groups<VT>(A, u, cu, beg, end, 32, wv, nw, run,
+                              each_visit<VT>([&](int32_t C, VT r) HG_INLINE {
+                                // every term is >= 1, so a zero before the add
+                                // marks the first touch
+                                if (atomicAdd(&val[C], r) == (VT)0)
+                                  used[atomicAdd(&s_nused, 1)] = C;
+                              }));
     __syncthreads();
     VT bv = 0;
     int32_t bc = -1;
@@ -512,7 +568,7 @@ __global__ void __launch_bounds__(256) k_rate_dense(RateArgs A) {
 // table at tab_off[i] - tab_base (values; keys in hash mode; the list of
 // used slots with its counter tnused[i])
 template <typename VT>
-__global__ void __launch_bounds__(SPLIT_WARPS * 32)
+__global__ void __launch_bounds__(SPLIT_WARPS * 32, 1024 / (SPLIT_WARPS * 32))
 k_rate_split_acc(RateArgs A, const int32_t* __restrict__ split, const int32_t* __restrict__ item_node,
                  const int32_t* __restrict__ item_off, const int64_t* __restrict__ tab_off,
                  const int64_t* __restrict__ tab_cap, const int8_t* __restrict__ tab_dense,
@@ -535,7 +591,7 @@ k_rate_split_acc(RateArgs A, const int32_t* __restrict__ split, const int32_t* _
     if (tab_dense[i]) {
       // direct-indexed: a reduction without a returned value; the argmax
       // scans the whole table, which is no larger than twice the visits
-      visits += rate_group<VT>(A, u, cu, g0, end, 0, 1, run, each_visit<VT>([&](int32_t C, VT r) {
+      visits += rate_group<VT>(A, u, cu, g0, end, 0, 1, run, each_visit<VT>([&](int32_t C, VT r) HG_INLINE {
         atomicAdd(&val[C], r);
       }));
     } else {
@@ -543,7 +599,7 @@ k_rate_split_acc(RateArgs A, const int32_t* __restrict__ split, const int32_t* _
       const uint32_t mask = (uint32_t)tab_cap[i] - 1;
       visits += rate_group<VT>(
           A, u, cu, g0, end, 0, 1, run,
-          [&](const int32_t(&C)[RATE_ILP], const VT(&rr)[RATE_ILP], const bool(&ok)[RATE_ILP]) {
+          [&](const int32_t(&C)[RATE_ILP], const VT(&rr)[RATE_ILP], const bool(&ok)[RATE_ILP]) HG_INLINE {
             // the first slot of every visit of the batch is loaded at once
             uint32_t h[RATE_ILP];
             int32_t k0[RATE_ILP];
@@ -623,7 +679,7 @@ k_rate_part(RateArgs A, const int32_t* __restrict__ split, const int32_t* __rest
     if (A.cst[u].y < 0) continue;  // joined a cluster in an earlier sub-round
     const int32_t P = part_off[i + 1] - part_off[i], k = t - part_off[i];
     const int32_t cu = A.c[u], beg = A.ioff[u], end = A.ioff[u + 1];
-    auto visit = [&](const int32_t(&q)[RATE_ILP], const VT(&rr)[RATE_ILP]) {
+    auto visit = [&](const int32_t(&q)[RATE_ILP], const VT(&rr)[RATE_ILP]) HG_INLINE {
       int32_t C[RATE_ILP];
 #pragma unroll
       for (int j = 0; j < RATE_ILP; ++j) C[j] = q[j] >= 0 ? A.rpin[q[j]] : -1;
@@ -641,9 +697,8 @@ k_rate_part(RateArgs A, const int32_t* __restrict__ split, const int32_t* __rest
       }
     };
     int32_t run = 0;
-    int64_t v = 0;
-    for (int32_t g0 = beg + 32 * team; g0 < end; g0 += 32 * PART_TEAMS)
-      v += rate_group_raw<VT>(A, g0, end, wt, TW, run, visit);
+    const int64_t v = rate_groups_raw<VT>(A, beg + 32 * team, end, 32 * PART_TEAMS, wt, TW, run,
+                                          visit);
     if (k == 0) visits += v;
     __syncthreads();
     VT bv = 0;
@@ -766,11 +821,24 @@ __device__ __forceinline__ int rate_class(int64_t W, int32_t n, bool dense_block
 
 // W(u) (pins of rated nets) of every node, and the largest bound on a node's
 // rating (sum of its net terms), which decides the value width.
+// floor(w(e) * 2^20 / (|e| - 1)) for the rated nets (2 <= |e| <= T), else 0;
+// at least 1 for a rated net since |e| - 1 < 2^20.
+__global__ void k_net_terms(const int32_t* __restrict__ eoff, const int32_t* __restrict__ w,
+                            int32_t m, int T, unsigned long long* __restrict__ rterm) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t sz = eoff[e + 1] - eoff[e];
+    rterm[e] = (sz >= 2 && sz <= T)
+                   ? (((unsigned long long)w[e]) << 20) / (unsigned long long)(sz - 1)
+                   : 0ull;
+  }
+}
+
 // One warp per node, lanes over its incident nets.
 __global__ void k_node_work(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
-                            const int32_t* __restrict__ eoff, const int32_t* __restrict__ w,
-                            int32_t n, int T, int32_t* __restrict__ wof,
-                            unsigned long long* __restrict__ max_r) {
+                            const int32_t* __restrict__ eoff,
+                            const unsigned long long* __restrict__ rterm, int32_t n,
+                            int32_t* __restrict__ wof, unsigned long long* __restrict__ max_r) {
   unsigned long long lr = 0;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
@@ -778,10 +846,10 @@ __global__ void k_node_work(const int32_t* __restrict__ ioff, const int32_t* __r
     unsigned long long R = 0;
     for (int32_t j = ioff[u] + lane_id(); j < ioff[u + 1]; j += 32) {
       const int32_t e = inets[j];
-      const int32_t sz = eoff[e + 1] - eoff[e];
-      if (sz >= 2 && sz <= T) {
-        W += sz;
-        R += (((unsigned long long)w[e]) << 20) / (unsigned long long)(sz - 1);
+      const unsigned long long r = rterm[e];
+      if (r != 0) {
+        W += eoff[e + 1] - eoff[e];
+        R += r;
       }
     }
     W = warp_sum(W);
@@ -945,7 +1013,7 @@ __device__ void group_bitonic(unsigned long long* buf, int P) {
 
 // One block per contested target C: order the movers by (c(u), u), accept
 // the longest prefix with cw[C] + weight <= c_max.
-__global__ void __launch_bounds__(GROUP_THREADS)
+__global__ void __launch_bounds__(GROUP_THREADS, 1024 / GROUP_THREADS)
 k_contest_group(const int32_t* __restrict__ words, const int32_t* __restrict__ slot_c,
                 const int32_t* __restrict__ slot_off, int32_t* __restrict__ slot_fill,
                 int32_t* __restrict__ slot_of, const int32_t* __restrict__ glist,
@@ -1368,8 +1436,15 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   k_init_cluster<<<g_nodes, 256, 0, cx.stream>>>(L.c.p, n, P.seed, P.level, S, L.rep.p, cst.p,
                                                  slot_of.p);
   check_launch("init_cluster");
+  DBuf<unsigned long long> rterm;
+  rterm.alloc(&cx.alloc, (size_t)std::max<int32_t>(L.m, 1));
+  if (L.m > 0) {
+    k_net_terms<<<grid_for(L.m, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(L.eoff.p, L.w.p, L.m,
+                                                                          P.T, rterm.p);
+    check_launch("net_terms");
+  }
   k_node_work<<<grid_for(n, 8, cx.num_sms, 16), 256, 0, cx.stream>>>(
-      L.ioff.p, L.inets.p, L.eoff.p, L.w.p, n, P.T, wof.p, max_r.p);
+      L.ioff.p, L.inets.p, L.eoff.p, rterm.p, n, wof.p, max_r.p);
   check_launch("node_work");
   const unsigned long long hmax_r = (unsigned long long)read_i64(cx, (const int64_t*)max_r.p);
   // 32-bit rating words when no node's total rating can reach 2^31; block
@@ -1384,7 +1459,7 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   k_node_scatter<<<g_nodes, 256, nkeys * sizeof(int32_t), cx.stream>>>(key_of.p, n, nkeys,
                                                                         kcount.p, kfill.p, list.p);
   check_launch("node_scatter");
-  if (cx.launches) *cx.launches += 4;
+  if (cx.launches) *cx.launches += 5;
 
   std::vector<int32_t> hcount(nkeys);
   HG_CUDA(cudaMemcpyAsync(hcount.data(), kcount.p, sizeof(int32_t) * nkeys, cudaMemcpyDeviceToHost,
@@ -1515,7 +1590,7 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   A.inets = L.inets.p;
   A.eoff = L.eoff.p;
   A.rpin = rpin.p;
-  A.w = L.w.p;
+  A.rterm = rterm.p;
   A.c = L.c.p;
   A.cst = cst.p;
   A.T = P.T;

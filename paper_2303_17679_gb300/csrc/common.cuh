@@ -41,6 +41,10 @@ enum DevStatus : int32_t {
   DEV_CAPACITY = 4,       // a work list exceeded its capacity
 };
 
+// Forces a device lambda to be inlined at its call sites (hot loops pass
+// lambdas through several template layers).
+#define HG_INLINE __attribute__((always_inline))
+
 __device__ __forceinline__ void dev_fail(int32_t* status, int32_t code) {
   atomicCAS(status, 0, code);
 }

@@ -97,7 +97,7 @@ __global__ void k_remap_small(const int32_t* __restrict__ list, int32_t count,
 }
 
 // Nets of 33..4096 pins: one block per net, bitonic sort in shared memory.
-__global__ void __launch_bounds__(MID_THREADS)
+__global__ void __launch_bounds__(MID_THREADS, 1024 / MID_THREADS)
 k_remap_mid(const int32_t* __restrict__ list, int32_t count, const int32_t* __restrict__ eoff,
             const int32_t* __restrict__ pins, const int32_t* __restrict__ map, int fp_bits,
             int32_t* __restrict__ tpins, int32_t* __restrict__ tsize,
