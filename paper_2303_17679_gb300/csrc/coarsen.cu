@@ -63,7 +63,7 @@ constexpr int32_t DENSE_W = 32768;       // largest W of a direct-indexed block 
 constexpr int32_t SPLIT_DENSE_MAX = 65536;
 constexpr int SPLIT_WARPS = 8;
 constexpr int PART_THREADS = 1024;
-constexpr int PART_TEAMS = 4;
+constexpr int PART_TEAMS = 1;
 constexpr uint32_t PART_SLOTS = 16384;   // shared hash slots of a part block
 constexpr int32_t PART_D = 9830;         // distinct candidates per part (60 % of the slots)
 constexpr int32_t PART_MAX = 8;          // more parts: the node uses a global hash table
@@ -651,8 +651,8 @@ k_rate_split_acc(RateArgs A, const int32_t* __restrict__ split, const int32_t* _
 // P = ceil(min(W, n) / PART_D) keeps every table at most 60 % full, so no
 // insertion can fail.  A node of one part publishes its argmax directly;
 // otherwise each part leaves its best (rating, cluster) for the per-node
-// combine in k_rate_split_argmax.  Four teams of eight warps take the node's
-// groups of 32 nets in turn.
+// combine in k_rate_split_argmax.  All warps of the block walk the node's
+// groups of 32 nets, sharing the chunks in turn.
 __device__ __forceinline__ int32_t part_of(int32_t C, int32_t P) {
   return (int32_t)(((uint64_t)((uint32_t)C * 0x85EBCA77u) * (uint32_t)P) >> 32);
 }
@@ -800,11 +800,11 @@ k_rate_split_argmax(RateArgs A, const int32_t* __restrict__ split, int32_t lo, i
 
 // Team class of a node from W(u) and D = min(W(u), n):
 //   0 warp (512 slots)                     D <= 256
-//   1 two warps (2048 slots)               D <= 1024 (unless the level is dense)
+//   1 four warps (2048 slots)              D <= 1024 (unless the level is dense)
 //   2 block, direct-indexed                the level fits a dense shared table,
 //                                          W <= 32768
 //     eight warps, 4096-slot hash          D <= 2048, W <= 65536 (other levels)
-//   3 eight warps, 8192-slot hash          D <= 4096, W <= 65536 (other levels)
+//   3 sixteen warps, 8192-slot hash        D <= 4096, W <= 65536 (other levels)
 //   4 split over the grid                  the rest
 __device__ __forceinline__ int rate_class(int64_t W, int32_t n, bool dense_block, bool narrow) {
   const int64_t D = W < n ? W : n;  // bound on the distinct candidate clusters
@@ -1283,7 +1283,8 @@ void set_rate_attrs() {
   static bool done = false;  // attributes belong to the function, once per process
   if (done) return;
   allow_smem(k_rate_team<VT, 1, 8>);
-  allow_smem(k_rate_team<VT, 2, 4>);
+  allow_smem(k_rate_team<VT, 4, 2>);
+  allow_smem(k_rate_team<VT, 16, 1>);
   allow_smem(k_rate_team<VT, 8, 1>);
   allow_smem(k_rate_team<VT, 8, 2>);
   allow_smem(k_rate_team<VT, 8, 4>);
@@ -1332,7 +1333,7 @@ void rate_subround(const Ctx& cx, RateArgs A, const std::vector<int32_t>& hoff, 
     if (cls == 0) {
       launch_team<VT, 1, 8>(cx, A, 2 * D_WARP);
     } else if (cls == 1) {
-      launch_team<VT, 2, 4>(cx, A, 2 * D_PAIR);
+      launch_team<VT, 4, 2>(cx, A, 2 * D_PAIR);
     } else if (cls == 2 && dense_block) {
       const size_t bytes = (size_t)std::max<int32_t>(A.n, 1) * (sizeof(VT) + 4);
       const int per_sm = std::max<int>(1, (int)(SMEM_BUDGET / bytes));
@@ -1341,7 +1342,7 @@ void rate_subround(const Ctx& cx, RateArgs A, const std::vector<int32_t>& hoff, 
       if (sizeof(VT) == 4) launch_team<VT, 8, 4>(cx, A, 2 * D_QUAD);
       else launch_team<VT, 8, 2>(cx, A, 2 * D_QUAD);
     } else {
-      if (sizeof(VT) == 4) launch_team<VT, 8, 2>(cx, A, 2 * D_BLOCK);
+      if (sizeof(VT) == 4) launch_team<VT, 16, 1>(cx, A, 2 * D_BLOCK);
       else launch_team<VT, 8, 1>(cx, A, 2 * D_BLOCK);
     }
     timer.end();
