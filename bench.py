@@ -31,6 +31,22 @@ WORKLOAD = ("config 2: n=m=1,000,000, Zipf(2.2) net sizes in [2,1024], preferent
             "5 LP passes per level, full V-cycle")
 L2_FLUSH_BYTES = 512 << 20
 
+# DRAM traffic of the rating kernels (k_rate_*), from one ncu capture of
+# every rating launch of the config-2 hierarchy (dram__bytes_read.sum +
+# dram__bytes_write.sum, averaged per launch); see
+# profiles/rating_kernels_config2.md.  Reported only while the source the
+# counters were taken from is unchanged.
+RATING_TRAFFIC = {
+    "source_sha256": "4b47ffcb78d1c2669be7e07d185e8c6a07bf9f378a3ebe284a3efff9ada2be1a",
+    "bytes_per_launch": 18801329,
+}
+
+
+def _source_sha256(rel: str) -> str:
+    import hashlib
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
 
 def peaks():
     try:
@@ -127,22 +143,24 @@ def sum_over_ranks(world, x: float) -> float:
 
 # ------------------------------------------------------------ CPU oracle
 
-def oracle_sample(target_seconds: float = 15.0):
-    """Times the CPU oracle (as it stands, one core) on a bounded sample of
-    the same workload shape: config 2 scaled to n = m = 40,000."""
-    import numpy as np
+ORACLE_SAMPLE_N = 200_000
 
+
+def oracle_sample():
+    """Times the CPU oracle (as it stands, one core) on a bounded sample of
+    the same workload shape: config 2 scaled to n = m = 200,000 (about ten
+    seconds of single-threaded work)."""
     import oracle
     import synth
-    hgr = synth.config2(SEED, n=40_000)
+    hgr = synth.config2(SEED, n=ORACLE_SAMPLE_N)
     t0 = time.perf_counter()
     vc = oracle.multilevel(hgr, K_BLOCKS, EPS_PPM, S=16, T=1000, factor=160, seed=SEED,
                            max_passes=PASSES)
     dt = time.perf_counter() - t0
     pins = sum(int(l.p) for l in vc.levels)
     return dict(value=pins / dt, seconds=dt, pins=pins, levels=len(vc.levels),
-                sample=f"config 2 scaled to n=m=40,000 ({hgr.p} pins, {len(vc.levels)} levels), "
-                       "full V-cycle, one process, single-threaded oracle")
+                sample=f"config 2 scaled to n=m={ORACLE_SAMPLE_N:,} ({hgr.p} pins, "
+                       f"{len(vc.levels)} levels), full V-cycle, one process, single-threaded oracle")
 
 
 def run_reference(args, world, rank):
@@ -271,18 +289,28 @@ def run_ours(args, world, rank, local):
     h2d = 4 * (hgr.m + 1 + hgr.p + hgr.m + hgr.n)
     d2h = 4 * hgr.n
 
-    # ---- roofline of the dominant kernel class (per-launch events inside the timed region)
+    # ---- roofline of the dominant kernel family (per-launch events inside the timed region)
     peak, peak_kind = peaks()
     rating_ms = agg["ms_rating_kernels"]
     gain_ms = agg["ms_lp_gain_kernels"]
-    # algorithmic bytes (see the design notes): gain = 16 B per node + 20 B per incidence;
-    # rating = 17 B per node + 16 B per incidence + 13 B per pin visit
-    gain_bytes = 16 * agg["lp_nodes"] + 20 * agg["lp_incidences"]
-    rating_bytes = 17 * agg["rating_nodes"] + 16 * agg["rating_incidences"] + 13 * agg["rating_pin_visits"]
+    # algorithmic bytes per unit: rating = 24 B per rated node (c, cluster weight
+    # and status, target, rep) + 16 B per incidence (net id, two offsets, weight)
+    # + 8 B per pin visit (pin, cluster); LP gain = 30 B per node + 20 B per
+    # incidence (net id, weight, Lambda, Phi(e, from))
+    gain_bytes = 30 * agg["lp_nodes"] + 20 * agg["lp_incidences"]
+    rating_bytes = (24 * agg["rating_nodes"] + 16 * agg["rating_incidences"]
+                    + 8 * agg["rating_pin_visits"])
+    traffic = None
     if rating_ms >= gain_ms:
-        kname, kms, kbytes, klaunch = "k_rate_* (heavy-edge rating)", rating_ms, rating_bytes, agg["rating_launches"]
+        kname, kms, kbytes, klaunch = ("k_rate_* (heavy-edge rating)", rating_ms, rating_bytes,
+                                       agg["rating_launches"])
+        if (RATING_TRAFFIC["source_sha256"]
+                and RATING_TRAFFIC["source_sha256"]
+                == _source_sha256("paper_2303_17679_gb300/csrc/coarsen.cu")):
+            traffic = RATING_TRAFFIC["bytes_per_launch"]
     else:
-        kname, kms, kbytes, klaunch = "k_lp_gain (LP best moves)", gain_ms, gain_bytes, agg["lp_gain_launches"]
+        kname, kms, kbytes, klaunch = ("k_lp_gain (LP best moves)", gain_ms, gain_bytes,
+                                       agg["lp_gain_launches"])
     achieved = (kbytes / (kms / 1e3)) / 1e9 if kms > 0 else 0.0
 
     line = {
@@ -298,9 +326,11 @@ def run_ours(args, world, rank, local):
                 "ms_per_step": statistics.mean(e2e_ms) if e2e_ms else None},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                     "peak_kind": peak_kind, "launches": int(klaunch),
-                     "ms_total": kms, "share_of_step": kms / sum(step_ms)},
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": peak_kind, "launches_per_step": int(klaunch // args.steps),
+                     "algorithmic_bytes_per_launch": kbytes / max(klaunch, 1),
+                     "ms_per_launch": kms / max(klaunch, 1),
+                     "share_of_step": kms / sum(step_ms)},
         "clocks": clocks,
         "wall_s": wall,
         "phase_ms": {"rating_kernels": rating_ms / args.steps, "lp_gain_kernels": gain_ms / args.steps},
