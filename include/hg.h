@@ -237,6 +237,65 @@ int hg_objective_noalloc(int32_t n, int32_t m, int64_t p, const int32_t* net_off
 int hg_partition(hg_t* h, int32_t k, int32_t eps_ppm, int32_t max_passes, int32_t* part,
                  int64_t* out_objective);
 
+/* ------------------------------------------------------------------
+ * Executor: many partition jobs on one GPU (batching and serving).
+ * The paper has no counterpart; it runs whole jobs of Algorithm 1 (as
+ * hg_partition) concurrently.  Each of `slots` host threads owns a
+ * non-blocking CUDA stream on the device current at hg_exec_create and runs
+ * one job at a time: hg_create from the job's host CSR, hg_partition, the
+ * partition copied to job.part_out, hg_destroy.  A job's results are those of
+ * the same plain calls: every step is deterministic and a handle touches no
+ * state outside itself.  Jobs start in submission order when a slot is free
+ * and the estimated device bytes of the running jobs plus the next one fit
+ * mem_budget_bytes (0: 80 % of the device memory free at creation); a job
+ * whose estimate exceeds the whole budget starts once nothing else runs.
+ * The kernels of jobs on different slots overlap on the device.
+ * ------------------------------------------------------------------ */
+typedef struct hg_exec_t hg_exec_t;
+
+typedef struct {
+  int32_t n, m;                 /* as hg_create */
+  const int32_t* net_offsets;   /* host, m+1; read at submission and while the job runs */
+  const int32_t* pins;          /* host, net_offsets[m] */
+  const int32_t* net_weights;   /* host, m, or NULL for all 1 */
+  const int32_t* node_weights;  /* host, n, or NULL for all 1 */
+  int32_t k, eps_ppm, max_passes; /* as hg_partition; k in 2..64 */
+  int32_t* part_out;            /* host, n int32, written when the job finishes */
+  int64_t tag;                  /* returned with the result */
+} hg_job;
+
+typedef struct {
+  int64_t ticket, tag;
+  int32_t status;               /* HG_OK or the first error of the job's calls */
+  int32_t levels;               /* levels of the job's hierarchy */
+  int64_t objective;            /* f_{lambda-1} of part_out (as hg_partition) */
+  int64_t level_pins;           /* sum of the pins of all levels */
+  int64_t est_bytes;            /* device-memory estimate used for admission */
+  int64_t t_submit_ns, t_start_ns, t_end_ns; /* hg_exec_now_ns clock */
+} hg_job_result;
+
+/* slots in 1..256; mem_budget_bytes >= 0; opt as hg_create (NULL: defaults). */
+int hg_exec_create(int32_t slots, int64_t mem_budget_bytes, const hg_options* opt,
+                   hg_exec_t** out);
+/* Queues a job; the caller keeps the job's host arrays valid and part_out
+ * untouched until its result has been returned by hg_exec_wait.  Rejects bad
+ * sizes and NULL pointers with HG_ERR_INVALID (the CSR itself is checked by
+ * hg_create when the job runs; its status is then in the result). */
+int hg_exec_submit(hg_exec_t* ex, const hg_job* job, int64_t* out_ticket);
+/* Returns up to max_results finished jobs (in completion order) in out and
+ * their number in *out_count.  Waits until at least one is available, at
+ * most timeout_ms (negative: no limit); returns at once with *out_count = 0
+ * when no job is queued, running or unreturned. */
+int hg_exec_wait(hg_exec_t* ex, int32_t max_results, int32_t timeout_ms, hg_job_result* out,
+                 int32_t* out_count);
+/* Jobs queued and running now (either pointer may be NULL). */
+int hg_exec_pending(hg_exec_t* ex, int32_t* out_queued, int32_t* out_running);
+/* Monotonic clock of the result timestamps, in nanoseconds. */
+int64_t hg_exec_now_ns(void);
+/* Runs every queued job to completion, then frees the executor.  Safe on
+ * NULL.  Results not yet returned are dropped. */
+int hg_exec_destroy(hg_exec_t* ex);
+
 /* Copies a level to the host in canonical form.  Any pointer may be NULL.
  *   offsets (m+1), pins (p), net_weights (m), node_weights (n);
  *   map (n): coarse node of every node in level+1 (only for levels that have

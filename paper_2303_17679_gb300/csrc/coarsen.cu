@@ -44,6 +44,7 @@
 // fits (then a hash slot packs cluster id and rating into one 64-bit word),
 // else in 64-bit words.
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "pintile.cuh"
@@ -1279,9 +1280,7 @@ void allow_smem(F* kernel) {
 }
 
 template <typename VT>
-void set_rate_attrs() {
-  static bool done = false;  // attributes belong to the function, once per process
-  if (done) return;
+void set_rate_attrs_once() {
   allow_smem(k_rate_team<VT, 1, 8>);
   allow_smem(k_rate_team<VT, 4, 2>);
   allow_smem(k_rate_team<VT, 16, 1>);
@@ -1291,7 +1290,14 @@ void set_rate_attrs() {
   allow_smem(k_rate_dense<VT>);
   HG_CUDA(cudaFuncSetAttribute(k_rate_part<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(PART_SLOTS * HashOf<VT>::type::BYTES_PER_SLOT)));
-  done = true;
+}
+
+// Attributes belong to the functions: set once per process, also when
+// several handles rate concurrently from different host threads.
+template <typename VT>
+void set_rate_attrs() {
+  static std::once_flag once;
+  std::call_once(once, set_rate_attrs_once<VT>);
 }
 
 struct SplitPlan {

@@ -46,6 +46,29 @@ class hg_options(ctypes.Structure):
     ]
 
 
+class hg_job(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32), ("m", ctypes.c_int32),
+        ("net_offsets", ctypes.c_void_p), ("pins", ctypes.c_void_p),
+        ("net_weights", ctypes.c_void_p), ("node_weights", ctypes.c_void_p),
+        ("k", ctypes.c_int32), ("eps_ppm", ctypes.c_int32), ("max_passes", ctypes.c_int32),
+        ("part_out", ctypes.c_void_p), ("tag", ctypes.c_int64),
+    ]
+
+
+class hg_job_result(ctypes.Structure):
+    _fields_ = [
+        ("ticket", ctypes.c_int64), ("tag", ctypes.c_int64),
+        ("status", ctypes.c_int32), ("levels", ctypes.c_int32),
+        ("objective", ctypes.c_int64), ("level_pins", ctypes.c_int64),
+        ("est_bytes", ctypes.c_int64),
+        ("t_submit_ns", ctypes.c_int64), ("t_start_ns", ctypes.c_int64), ("t_end_ns", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class hg_stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_double) for name in (
         "ms_transpose", "ms_rating", "ms_approve", "ms_contract", "ms_project", "ms_phi",
@@ -109,6 +132,12 @@ def load(path: str | None = None):
             "hg_get_stats": (ctypes.c_int, [H, P(hg_stats)]),
             "hg_reset_stats": (ctypes.c_int, [H]),
             "hg_destroy": (ctypes.c_int, [H]),
+            "hg_exec_create": (ctypes.c_int, [i32, i64, P(hg_options), P(H)]),
+            "hg_exec_submit": (ctypes.c_int, [H, P(hg_job), P(i64)]),
+            "hg_exec_wait": (ctypes.c_int, [H, i32, i32, P(hg_job_result), P(i32)]),
+            "hg_exec_pending": (ctypes.c_int, [H, P(i32), P(i32)]),
+            "hg_exec_now_ns": (ctypes.c_int64, []),
+            "hg_exec_destroy": (ctypes.c_int, [H]),
             "hg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "hg_version": (ctypes.c_char_p, []),
         }
@@ -126,7 +155,8 @@ def exported_symbols():
             "hg_level_info", "hg_initial_partition", "hg_project", "hg_lp_refine",
             "hg_objective", "hg_pin_counts", "hg_objective_noalloc", "hg_partition", "hg_get_level", "hg_get_incidence",
             "hg_truncate", "hg_enable_timing", "hg_get_stats", "hg_reset_stats", "hg_destroy",
-            "hg_strerror", "hg_version"]
+            "hg_exec_create", "hg_exec_submit", "hg_exec_wait", "hg_exec_pending",
+            "hg_exec_now_ns", "hg_exec_destroy", "hg_strerror", "hg_version"]
 
 
 # ------------------------------------------------------------------ helpers
@@ -328,3 +358,75 @@ def hg_reset_stats(h):
 def hg_destroy(h):
     if h:
         load().hg_destroy(h)
+
+
+# ------------------------------------------------------------------ executor
+
+def hg_exec_create(slots, mem_budget_bytes=0, opt: hg_options | None = None):
+    ex = ctypes.c_void_p()
+    _check(load().hg_exec_create(int(slots), int(mem_budget_bytes),
+                                 ctypes.byref(opt) if opt else None, ctypes.byref(ex)),
+           "hg_exec_create")
+    return ex
+
+
+def hg_exec_submit(ex, job: hg_job) -> int:
+    t = ctypes.c_int64()
+    _check(load().hg_exec_submit(ex, ctypes.byref(job), ctypes.byref(t)), "hg_exec_submit")
+    return t.value
+
+
+def hg_exec_wait(ex, max_results=64, timeout_ms=-1):
+    buf = (hg_job_result * int(max_results))()
+    cnt = ctypes.c_int32()
+    _check(load().hg_exec_wait(ex, int(max_results), int(timeout_ms), buf, ctypes.byref(cnt)),
+           "hg_exec_wait")
+    return [buf[i].as_dict() for i in range(cnt.value)]
+
+
+def hg_exec_pending(ex):
+    q, r = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().hg_exec_pending(ex, ctypes.byref(q), ctypes.byref(r)), "hg_exec_pending")
+    return q.value, r.value
+
+
+def hg_exec_now_ns() -> int:
+    return int(load().hg_exec_now_ns())
+
+
+def hg_exec_destroy(ex):
+    if ex:
+        load().hg_exec_destroy(ex)
+
+
+class Executor:
+    """Keeps each job's host arrays alive until its result has been returned."""
+
+    def __init__(self, slots, mem_budget_bytes=0, opt: hg_options | None = None):
+        self.ex = hg_exec_create(slots, mem_budget_bytes, opt)
+        self.live = {}
+
+    def submit(self, hgr, k, eps_ppm=30000, max_passes=5, tag=0):
+        arrs = [np.ascontiguousarray(a, np.int32) for a in
+                (hgr.offsets, hgr.pins, hgr.net_w, hgr.node_w)]
+        part = np.zeros(max(hgr.n, 1), np.int32)
+        job = hg_job(n=int(hgr.n), m=int(hgr.m), net_offsets=arrs[0].ctypes.data,
+                     pins=arrs[1].ctypes.data if len(arrs[1]) else None,
+                     net_weights=arrs[2].ctypes.data, node_weights=arrs[3].ctypes.data,
+                     k=int(k), eps_ppm=int(eps_ppm), max_passes=int(max_passes),
+                     part_out=part.ctypes.data, tag=int(tag))
+        t = hg_exec_submit(self.ex, job)
+        self.live[t] = (arrs, part[:hgr.n])
+        return t
+
+    def wait(self, max_results=64, timeout_ms=-1):
+        out = []
+        for r in hg_exec_wait(self.ex, max_results, timeout_ms):
+            r["part"] = self.live.pop(r["ticket"])[1]
+            out.append(r)
+        return out
+
+    def close(self):
+        hg_exec_destroy(self.ex)
+        self.ex = None
+        self.live.clear()
