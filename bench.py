@@ -186,6 +186,137 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ batching and serving
+
+def level_pins_of(h, hg):
+    return sum(hg.hg_level_info(h, lv)[2] for lv in range(hg.hg_num_levels(h)))
+
+
+def run_plain_job(hg, torch, stream, hgr, k):
+    h = hg.hg_create(hgr.n, hgr.m, hgr.offsets, hgr.pins, hgr.net_w, hgr.node_w, hg.HG_MEM_HOST,
+                     None, stream)
+    try:
+        part = torch.empty(hgr.n, dtype=torch.int32, device="cuda")
+        obj = hg.hg_partition(h, k, EPS_PPM, PASSES, part)
+        part.cpu()
+        return obj, level_pins_of(h, hg)
+    finally:
+        hg.hg_destroy(h)
+
+
+def run_batch(hg, torch, slots):
+    """Config 4: 512 seeded instances (n log-uniform in [1e3, 2e5]); the plain
+    form runs them one call after another (host CSR in, partition out), the
+    batched form through the executor's slots, largest first."""
+    import synth
+    jobs = synth.config4(SEED)
+    stream = torch.cuda.current_stream()
+    for hgr, k in jobs[:8]:
+        run_plain_job(hg, torch, stream, hgr, k)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = [run_plain_job(hg, torch, stream, hgr, k) for hgr, k in jobs]
+    t_plain = time.perf_counter() - t0
+    pins = sum(p for _, p in plain)
+    ex = hg.Executor(slots)
+    try:
+        for i, (hgr, k) in enumerate(jobs[:slots]):
+            ex.submit(hgr, k, EPS_PPM, PASSES, tag=i)
+        seen = 0
+        while seen < min(slots, len(jobs)):
+            seen += len(ex.wait())
+        t0 = time.perf_counter()
+        for i in sorted(range(len(jobs)), key=lambda i: -jobs[i][0].p):
+            ex.submit(jobs[i][0], jobs[i][1], EPS_PPM, PASSES, tag=i)
+        got = {}
+        while len(got) < len(jobs):
+            for r in ex.wait():
+                got[r["tag"]] = r
+        t_batch = time.perf_counter() - t0
+    finally:
+        ex.close()
+    same = all(got[i]["status"] == 0 and got[i]["objective"] == plain[i][0] for i in range(len(jobs)))
+    return {"workload": "config 4: 512 instances, n log-uniform in [1e3, 2e5], m/n in [0.5, 3], "
+                        "config-1 net sizes, weights in [1, 10], k in {2,4,8,16,32}, host CSR in, "
+                        "partition out",
+            "instances": len(jobs), "level_pins": pins, "slots": slots,
+            "plain_s": t_plain, "batched_s": t_batch,
+            "plain_pins_per_s": pins / t_plain, "batched_pins_per_s": pins / t_batch,
+            "speedup": t_plain / t_batch, "identical_objectives": same}
+
+
+def serve_stream(hg, arrivals, slots, gen_workers=8):
+    """Submits each request at its arrival time (generated just ahead of it by
+    a thread pool) and collects results; latency = completion - arrival."""
+    import concurrent.futures as cf
+
+    import synth
+    ex = hg.Executor(slots)
+    pool = cf.ThreadPoolExecutor(gen_workers)
+    futs = {}
+    lookahead = 64
+    lat, pins, objs = [], 0, {}
+    t_first = t_last = None
+    try:
+        for i in range(min(lookahead, len(arrivals))):
+            _, s, p, _ = arrivals[i]
+            futs[i] = pool.submit(synth.config5_request, s, p)
+        t0_ns = hg.hg_exec_now_ns()
+        done = 0
+
+        def collect(timeout_ms):
+            nonlocal done, pins, t_last
+            for r in ex.wait(timeout_ms=timeout_ms):
+                arr_ns = t0_ns + int(arrivals[r["tag"]][0] * 1e9)
+                lat.append((r["t_end_ns"] - arr_ns) / 1e6)
+                pins += r["level_pins"]
+                objs[r["tag"]] = r["objective"]
+                t_last = r["t_end_ns"]
+                done += 1
+
+        for i, (t_arr, _, _, k) in enumerate(arrivals):
+            while True:
+                wait_ns = t0_ns + int(t_arr * 1e9) - hg.hg_exec_now_ns()
+                if wait_ns <= 0:
+                    break
+                collect(min(50, max(0, wait_ns // 1_000_000)))
+            hgr = futs.pop(i).result()
+            j = i + lookahead
+            if j < len(arrivals):
+                futs[j] = pool.submit(synth.config5_request, arrivals[j][1], arrivals[j][2])
+            ex.submit(hgr, k, EPS_PPM, PASSES, tag=i)
+            if t_first is None:
+                t_first = t0_ns + int(t_arr * 1e9)
+            collect(0)
+        while done < len(arrivals):
+            collect(-1)
+    finally:
+        ex.close()
+        pool.shutdown()
+    lat.sort()
+    q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))]
+    wall = (t_last - t_first) / 1e9
+    return {"slots": slots, "requests": len(arrivals), "p50_ms": q(0.50), "p99_ms": q(0.99),
+            "max_ms": lat[-1], "level_pins": pins, "pins_per_s": pins / wall, "wall_s": wall}, objs
+
+
+def run_serve(hg, seconds, slots):
+    """Config 5: Poisson(200/s) requests of 1e4..2e6 pins (log-uniform), Zipf
+    net sizes, k in {2, 8, 32}; continuous batching over the executor's slots
+    against the plain form (one request at a time, same arrivals)."""
+    import synth
+    arrivals = synth.config5_arrivals(SEED, rate=200.0, duration=seconds)
+    served, objs_s = serve_stream(hg, arrivals, slots)
+    # the plain form cannot keep up with the offered load, so it runs the first
+    # second of arrivals only (its queue, and latency, grow without bound)
+    head = [a for a in arrivals if a[0] < 1.0]
+    plain, objs_p = serve_stream(hg, head, 1)
+    return {"workload": f"config 5: Poisson 200 req/s for {seconds:g} s, 1e4..2e6 pins "
+                        "log-uniform, Zipf(2.2) net sizes, k in {2, 8, 32}",
+            "served": served, "plain_first_second": plain,
+            "identical_objectives": all(objs_s[i] == objs_p[i] for i in objs_p)}
+
+
 # ------------------------------------------------------------ GPU path
 
 def run_ours(args, world, rank, local):
@@ -349,6 +480,10 @@ def run_ours(args, world, rank, local):
         _, _, pst = step(phases=True)
         line["phase_breakdown_ms"] = {k: round(v, 3) for k, v in pst.items()
                                       if k.startswith("ms_") and not isinstance(v, list)}
+    if world == 1 and not args.no_batch:
+        line["batch"] = run_batch(hg, torch, args.slots)
+    if world == 1 and args.serve_seconds > 0:
+        line["serve"] = run_serve(hg, args.serve_seconds, args.slots)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_sample()
         line["cpu_baseline"] = {"value": cb["value"], "unit": "pins/s", "cores": 1, "kind": "oracle",
@@ -365,6 +500,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end steps")
+    ap.add_argument("--no-batch", action="store_true", help="skip the config-4 batch comparison")
+    ap.add_argument("--serve-seconds", type=float, default=20.0,
+                    help="length of the config-5 serving run (0: skip; the config states 60)")
+    ap.add_argument("--slots", type=int, default=16, help="executor slots for batch and serve")
     ap.add_argument("--phases", action="store_true",
                     help="add a per-phase breakdown from one extra, untimed step")
     args = ap.parse_args()
