@@ -104,8 +104,9 @@ __device__ __forceinline__ int lp_key(const int32_t* ioff, uint64_t seed, int le
 }
 
 __global__ void k_lp_count(const int32_t* __restrict__ ioff, int32_t n, uint64_t seed, int level,
-                           int pass, int S, int32_t* __restrict__ cnt) {
+                           const int32_t* __restrict__ d_pass, int S, int32_t* __restrict__ cnt) {
   extern __shared__ int32_t s_cnt[];
+  const int pass = *d_pass;
   for (int i = threadIdx.x; i < 2 * S; i += blockDim.x) s_cnt[i] = 0;
   __syncthreads();
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
@@ -120,10 +121,11 @@ __global__ void k_lp_count(const int32_t* __restrict__ ioff, int32_t n, uint64_t
 
 // Every block recomputes the (tiny) exclusive scan of the 2S counts.
 __global__ void k_lp_scatter(const int32_t* __restrict__ ioff, int32_t n, uint64_t seed, int level,
-                             int pass, int S, const int32_t* __restrict__ cnt,
-                             int32_t* __restrict__ fill, int32_t* __restrict__ off,
-                             int32_t* __restrict__ list) {
+                             const int32_t* __restrict__ d_pass, int S,
+                             const int32_t* __restrict__ cnt, int32_t* __restrict__ fill,
+                             int32_t* __restrict__ off, int32_t* __restrict__ list) {
   extern __shared__ int32_t s_off[];
+  const int pass = *d_pass;
   if (threadIdx.x == 0) {
     int32_t run = 0;
     for (int i = 0; i < 2 * S; ++i) {
@@ -141,6 +143,10 @@ __global__ void k_lp_scatter(const int32_t* __restrict__ ioff, int32_t n, uint64
     if (key >= 0) list[s_off[key] + atomicAdd(&fill[key], 1)] = (int32_t)u;
   }
 }
+
+// Advances the pass index read by k_lp_count / k_lp_scatter (the last launch
+// of a pass, so one captured pass can be replayed).
+__global__ void k_lp_next_pass(int32_t* d_pass) { *d_pass += 1; }
 
 // Per sub-round bookkeeping words.
 enum SubroundWord { SW_MOVES = 0, SW_APPROVED = 1, SW_WORDS = 4 };
@@ -712,26 +718,32 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   G.mv_g = mv_g.p;
   G.work = counters.p + 1;
 
-  for (int pass = 0; pass < max_passes; ++pass) {
-    HG_CUDA(cudaMemsetAsync(sr_cnt.p, 0, sr_cnt.bytes(), cx.stream));
-    HG_CUDA(cudaMemsetAsync(sr_fill.p, 0, sr_fill.bytes(), cx.stream));
-    HG_CUDA(cudaMemsetAsync(dcnt.p, 0, dcnt.bytes(), cx.stream));
-    HG_CUDA(cudaMemsetAsync(dfill.p, 0, dfill.bytes(), cx.stream));
-    HG_CUDA(cudaMemsetAsync(words.p, 0, words.bytes(), cx.stream));
-    HG_CUDA(cudaMemsetAsync(counters.p, 0, sizeof(unsigned long long), cx.stream));
-    std::vector<int32_t> hcnt(2 * S);
+  // One pass = the sub-round lists, then per sub-round best moves, pair
+  // bucketing and selection, application.  Every launch has a fixed geometry
+  // and reads its sizes on the device, so a pass is captured once per level
+  // as a CUDA graph and replayed; with phase timing on (which synchronizes
+  // around phases) the launches are issued directly.
+  DBuf<int32_t> d_pass;
+  d_pass.alloc(&cx.alloc, 1);
+  HG_CUDA(cudaMemsetAsync(d_pass.p, 0, sizeof(int32_t), cx.stream));
+  const bool use_graph = !cx.timing;
+  const int per_pass_launches = 3 + 5 * S;
+  auto enqueue_pass = [&](bool timed, cudaStream_t sm) {
+    HG_CUDA(cudaMemsetAsync(sr_cnt.p, 0, sr_cnt.bytes(), sm));
+    HG_CUDA(cudaMemsetAsync(sr_fill.p, 0, sr_fill.bytes(), sm));
+    HG_CUDA(cudaMemsetAsync(dcnt.p, 0, dcnt.bytes(), sm));
+    HG_CUDA(cudaMemsetAsync(dfill.p, 0, dfill.bytes(), sm));
+    HG_CUDA(cudaMemsetAsync(words.p, 0, words.bytes(), sm));
+    HG_CUDA(cudaMemsetAsync(counters.p, 0, counters.bytes(), sm));
     {
-      EventTimer tm(cx, &rc.ms_gain);
-      k_lp_count<<<g_nodes, 256, 2 * S * sizeof(int32_t), cx.stream>>>(L.ioff.p, n, seed,
-                                                                      level_index, pass, S,
+      EventTimer tm(cx, timed ? &rc.ms_gain : nullptr);
+      k_lp_count<<<g_nodes, 256, 2 * S * sizeof(int32_t), sm>>>(L.ioff.p, n, seed,
+                                                                      level_index, d_pass.p, S,
                                                                       sr_cnt.p);
       check_launch("lp_count");
-      k_lp_scatter<<<g_nodes, 256, (2 * S + 1) * sizeof(int32_t), cx.stream>>>(
-          L.ioff.p, n, seed, level_index, pass, S, sr_cnt.p, sr_fill.p, sr_off.p, list.p);
+      k_lp_scatter<<<g_nodes, 256, (2 * S + 1) * sizeof(int32_t), sm>>>(
+          L.ioff.p, n, seed, level_index, d_pass.p, S, sr_cnt.p, sr_fill.p, sr_off.p, list.p);
       check_launch("lp_scatter");
-      HG_CUDA(cudaMemcpyAsync(hcnt.data(), sr_cnt.p, sizeof(int32_t) * 2 * S,
-                              cudaMemcpyDeviceToHost, cx.stream));
-      HG_CUDA(cudaStreamSynchronize(cx.stream));
     }
     for (int s = 0; s < S; ++s) {
       int32_t* w_s = words.p + (size_t)s * SW_WORDS;
@@ -741,57 +753,72 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
       G.dcount = dc_s;
       G.words = w_s;
       {
-        EventTimer tm(cx, &rc.ms_gain);
-        if (hcnt[2 * s] > 0) {
-          gain_timer.begin();
-          k_lp_gain_warp<<<grid_for(hcnt[2 * s], WARPS, cx.num_sms, 16), WARPS * 32, 0,
-                           cx.stream>>>(G);
-          gain_timer.end();
-          check_launch("lp_gain_warp");
-          rc.lp_gain_launches += 1;
-          if (cx.launches) *cx.launches += 1;
-        }
-        if (hcnt[2 * s + 1] > 0) {
-          gain_timer.begin();
-          k_lp_gain_block<<<grid_for(hcnt[2 * s + 1], 1, cx.num_sms, 8), WARPS * 32, 0,
-                            cx.stream>>>(G);
-          gain_timer.end();
-          check_launch("lp_gain_block");
-          rc.lp_gain_launches += 1;
-          if (cx.launches) *cx.launches += 1;
-        }
+        EventTimer tm(cx, timed ? &rc.ms_gain : nullptr);
+        if (timed) gain_timer.begin();
+        k_lp_gain_warp<<<g_gain, WARPS * 32, 0, sm>>>(G);
+        if (timed) gain_timer.end();
+        check_launch("lp_gain_warp");
+        if (timed) gain_timer.begin();
+        k_lp_gain_block<<<g_gain_block, WARPS * 32, 0, sm>>>(G);
+        if (timed) gain_timer.end();
+        check_launch("lp_gain_block");
+        rc.lp_gain_launches += 2;
       }
       {
-        EventTimer tm(cx, &rc.ms_select);
-        k_lp_bucket<<<g_bucket, 256, (kk + 1) * sizeof(int32_t), cx.stream>>>(
+        EventTimer tm(cx, timed ? &rc.ms_select : nullptr);
+        k_lp_bucket<<<g_bucket, 256, (kk + 1) * sizeof(int32_t), sm>>>(
             mv_u.p, mv_to.p, part, k, dc_s, df_s, doff.p, w_s, bucket.p);
         check_launch("lp_bucket");
-        k_lp_select<<<g_sel, SEL_THREADS, 0, cx.stream>>>(
+        k_lp_select<<<g_sel, SEL_THREADS, 0, sm>>>(
             L.ioff.p, bucket.p, doff.p, dc_s, mv_u.p, mv_to.p, mv_g.p, L.c.p, st.bw.p, lmax, k,
             gkeys.p, gpre.p, ap_u.p, ap_from.p, ap_to.p, w_s);
         check_launch("lp_select");
       }
       {
-        EventTimer tm(cx, &rc.ms_apply);
-        k_lp_apply<<<g_apply, WARPS * 32, 0, cx.stream>>>(L.ioff.p, L.inets.p, L.c.p, k, ap_u.p,
+        EventTimer tm(cx, timed ? &rc.ms_apply : nullptr);
+        k_lp_apply<<<g_apply, WARPS * 32, 0, sm>>>(L.ioff.p, L.inets.p, L.c.p, k, ap_u.p,
                                                           ap_from.p, ap_to.p, w_s, part, st.phi.p,
                                                           st.lam.p, st.bw.p, counters.p);
         check_launch("lp_apply");
       }
-      if (cx.launches) *cx.launches += 3;
     }
-    (void)g_gain;
-    (void)g_gain_block;
-    if (cx.launches) *cx.launches += 2;
-    unsigned long long hc[2];
-    HG_CUDA(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, cx.stream));
-    check_status(cx);
-    res.passes = pass + 1;
-    res.moves += (int64_t)hc[0];
-    rc.lp_incidences += (int64_t)hc[1];
-    HG_CUDA(cudaMemsetAsync(counters.p + 1, 0, sizeof(unsigned long long), cx.stream));
-    if (hc[0] == 0) break;
+    k_lp_next_pass<<<1, 1, 0, sm>>>(d_pass.p);
+    check_launch("lp_next_pass");
+  };
+  cudaGraphExec_t exec = nullptr;
+  if (use_graph && max_passes > 0) {
+    cudaGraph_t graph = nullptr;
+    HG_CUDA(cudaStreamBeginCapture(cx.capture_stream, cudaStreamCaptureModeThreadLocal));
+    try {
+      enqueue_pass(false, cx.capture_stream);
+    } catch (...) {
+      cudaStreamEndCapture(cx.capture_stream, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    HG_CUDA(cudaStreamEndCapture(cx.capture_stream, &graph));
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    HG_CUDA(ie);
   }
+  try {
+    for (int pass = 0; pass < max_passes; ++pass) {
+      if (exec) HG_CUDA(cudaGraphLaunch(exec, cx.stream));
+      else enqueue_pass(true, cx.stream);
+      if (cx.launches) *cx.launches += per_pass_launches;
+      unsigned long long hc[2];
+      HG_CUDA(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, cx.stream));
+      check_status(cx);
+      res.passes = pass + 1;
+      res.moves += (int64_t)hc[0];
+      rc.lp_incidences += (int64_t)hc[1];
+      if (hc[0] == 0) break;
+    }
+  } catch (...) {
+    if (exec) cudaGraphExecDestroy(exec);
+    throw;
+  }
+  if (exec) HG_CUDA(cudaGraphExecDestroy(exec));
   rc.ms_gain_kernels += gain_timer.flush();
   rc.lp_nodes += (int64_t)res.passes * n;
   {
