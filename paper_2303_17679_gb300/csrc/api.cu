@@ -160,7 +160,6 @@ int hg_create(int32_t n, int32_t m, const int32_t* net_offsets, const int32_t* p
     HG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
     h->cx.num_sms = sms;
     h->cx.stream = static_cast<cudaStream_t>(cuda_stream);
-    HG_CUDA(cudaStreamCreateWithFlags(&h->cx.capture_stream, cudaStreamNonBlocking));
     h->cx.alloc.fn_alloc = o.dev_alloc;
     h->cx.alloc.fn_free = o.dev_free;
     h->cx.alloc.ctx = o.alloc_ctx;
@@ -489,7 +488,6 @@ int hg_destroy(hg_t* h) {
   if (h->cx.d_status) h->cx.alloc.put(h->cx.d_status);
   h->cx.d_status = nullptr;
   cudaStreamSynchronize(h->cx.stream);
-  if (h->cx.capture_stream) cudaStreamDestroy(h->cx.capture_stream);
   delete h;
   return HG_OK;
 }

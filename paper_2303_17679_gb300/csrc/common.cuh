@@ -196,8 +196,6 @@ struct Ctx {
   int64_t* launches = nullptr;   // host counter
   bool timing = false;           // per-phase event timing (synchronizes at phase ends)
   bool kernel_timing = false;    // event pair around every rating / gain launch (no sync)
-  cudaStream_t capture_stream = nullptr;  // private stream for graph capture (the caller's
-                                          // stream may be the legacy one, which cannot capture)
 };
 
 // Grid size helper: enough blocks for `work` items of `per_block` each,

@@ -653,6 +653,66 @@ void pin_counts_of(const Ctx& cx, const Level& L, int k, const int32_t* part, in
   check_status(cx);
 }
 
+namespace {
+
+// The instantiated graph of one LP pass is kept per host thread and updated
+// in place (cudaGraphExecUpdate) for every new level and handle: its
+// topology depends on S only, and instantiating anew for every level is
+// costly, the more so when several host threads (executor slots) do it at
+// once.  Captures run on a private stream of the thread, since the caller's
+// stream may be the legacy default stream, which cannot be captured.  Every
+// use of the graph ends with a host wait before the next update.
+struct PassGraphCache {
+  int device = -1;
+  int S = -1;
+  cudaStream_t capture = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (capture) cudaStreamDestroy(capture);
+    exec = nullptr;
+    capture = nullptr;
+    device = S = -1;
+  }
+  // Makes exec run `graph` (which it consumes) and returns it.
+  cudaGraphExec_t bind(cudaGraph_t graph, int subrounds) {
+    if (exec && S == subrounds) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(exec, graph, &info) == cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return exec;
+      }
+      cudaGetLastError();  // topology changed: instantiate anew
+      cudaGraphExecDestroy(exec);
+      exec = nullptr;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      exec = nullptr;
+      HG_CUDA(ie);
+    }
+    S = subrounds;
+    return exec;
+  }
+  ~PassGraphCache() { reset(); }
+};
+
+PassGraphCache& pass_graph_cache(const Ctx& cx) {
+  thread_local PassGraphCache cache;
+  int dev = 0;
+  HG_CUDA(cudaGetDevice(&dev));
+  if (cache.device != dev) {
+    cache.reset();
+    HG_CUDA(cudaStreamCreateWithFlags(&cache.capture, cudaStreamNonBlocking));
+    cache.device = dev;
+  }
+  (void)cx;
+  return cache;
+}
+
+}  // namespace
+
 LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, int eps_ppm,
                          int max_passes, int S, uint64_t seed, int64_t total_node_weight,
                          int32_t* part, RefineCounters& rc) {
@@ -787,38 +847,31 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   };
   cudaGraphExec_t exec = nullptr;
   if (use_graph && max_passes > 0) {
+    PassGraphCache& gc = pass_graph_cache(cx);
     cudaGraph_t graph = nullptr;
-    HG_CUDA(cudaStreamBeginCapture(cx.capture_stream, cudaStreamCaptureModeThreadLocal));
+    HG_CUDA(cudaStreamBeginCapture(gc.capture, cudaStreamCaptureModeThreadLocal));
     try {
-      enqueue_pass(false, cx.capture_stream);
+      enqueue_pass(false, gc.capture);
     } catch (...) {
-      cudaStreamEndCapture(cx.capture_stream, &graph);
+      cudaStreamEndCapture(gc.capture, &graph);
       if (graph) cudaGraphDestroy(graph);
       throw;
     }
-    HG_CUDA(cudaStreamEndCapture(cx.capture_stream, &graph));
-    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    HG_CUDA(ie);
+    HG_CUDA(cudaStreamEndCapture(gc.capture, &graph));
+    exec = gc.bind(graph, S);
   }
-  try {
-    for (int pass = 0; pass < max_passes; ++pass) {
-      if (exec) HG_CUDA(cudaGraphLaunch(exec, cx.stream));
-      else enqueue_pass(true, cx.stream);
-      if (cx.launches) *cx.launches += per_pass_launches;
-      unsigned long long hc[2];
-      HG_CUDA(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, cx.stream));
-      check_status(cx);
-      res.passes = pass + 1;
-      res.moves += (int64_t)hc[0];
-      rc.lp_incidences += (int64_t)hc[1];
-      if (hc[0] == 0) break;
-    }
-  } catch (...) {
-    if (exec) cudaGraphExecDestroy(exec);
-    throw;
+  for (int pass = 0; pass < max_passes; ++pass) {
+    if (exec) HG_CUDA(cudaGraphLaunch(exec, cx.stream));
+    else enqueue_pass(true, cx.stream);
+    if (cx.launches) *cx.launches += per_pass_launches;
+    unsigned long long hc[2];
+    HG_CUDA(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, cx.stream));
+    check_status(cx);  // also waits for the pass, so the graph is idle before its next update
+    res.passes = pass + 1;
+    res.moves += (int64_t)hc[0];
+    rc.lp_incidences += (int64_t)hc[1];
+    if (hc[0] == 0) break;
   }
-  if (exec) HG_CUDA(cudaGraphExecDestroy(exec));
   rc.ms_gain_kernels += gain_timer.flush();
   rc.lp_nodes += (int64_t)res.passes * n;
   {
