@@ -334,6 +334,15 @@ def run_ours(args, world, rank, local):
     hgr = synth.config2(SEED)
     opt = hg.hg_default_options()
     opt.seed = SEED
+    # launch mapping chosen by paper_2303_17679_gb300.autotune for this workload
+    # (results are identical under every mapping; only the speed differs)
+    tuned_path = os.path.join(ROOT, "paper_2303_17679_gb300", "tuned_config2_k8.json")
+    mapping = "built-in defaults"
+    if os.path.exists(tuned_path):
+        from paper_2303_17679_gb300 import autotune
+        with open(tuned_path) as f:
+            autotune.apply(opt, json.load(f))
+        mapping = "autotuned (paper_2303_17679_gb300/tuned_config2_k8.json)"
     t_in = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).cuda()
     d_off, d_pins, d_w, d_c = t_in(hgr.offsets), t_in(hgr.pins), t_in(hgr.net_w), t_in(hgr.node_w)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory()
@@ -451,6 +460,7 @@ def run_ours(args, world, rank, local):
         "data": "synthetic (seeded generator, config 2 shape)",
         "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "flushed between steps (512 MiB write outside the timed events)",
+                   "launch_mapping": mapping,
                    "levels": len(levels), "pins_per_step": pins_per_step, "objective": obj},
         "e2e": {"value": e2e_value, "unit": "pins/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,

@@ -81,6 +81,21 @@ typedef struct {
   void* (*dev_alloc)(size_t bytes, void* ctx);
   void (*dev_free)(void* ptr, void* ctx);
   void* alloc_ctx;
+  /* Launch mapping, the autotuner's knobs (0 = built-in default).  Results
+   * never depend on them: every mapping computes the same integer sums and
+   * the same picks.  A rated node with D = min(W(u), n) distinct-candidate
+   * bound (W(u) = pins of its rated nets) goes to the first team whose bound
+   * holds: one warp (rate_warp_max_d, <= 256, default 256), four warps
+   * (rate_pair_max_d, <= 1024, default 1024), eight warps (rate_quad_max_d,
+   * <= 2048, default 2048), sixteen warps (rate_block_max_d, <= 4096,
+   * default 4096), else the grid-split path.  In label propagation, nodes
+   * with more than lp_block_min_deg incident nets (default 64, <= 2^20) are
+   * evaluated by a block of eight warps, the others by one warp. */
+  int32_t rate_warp_max_d;
+  int32_t rate_pair_max_d;
+  int32_t rate_quad_max_d;
+  int32_t rate_block_max_d;
+  int32_t lp_block_min_deg;
 } hg_options;
 
 /* Per-phase device time (milliseconds, from CUDA events) and work counters,

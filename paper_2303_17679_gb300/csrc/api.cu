@@ -143,6 +143,11 @@ int hg_create(int32_t n, int32_t m, const int32_t* net_offsets, const int32_t* p
       o.rating_max_net_size > (1 << 20) || o.contraction_limit_factor < 1 ||
       o.fingerprint_bits < 0 || o.fingerprint_bits > 64 || (!o.dev_alloc != !o.dev_free))
     return HG_ERR_INVALID;
+  if (o.rate_warp_max_d < 0 || o.rate_warp_max_d > 256 || o.rate_pair_max_d < 0 ||
+      o.rate_pair_max_d > 1024 || o.rate_quad_max_d < 0 || o.rate_quad_max_d > 2048 ||
+      o.rate_block_max_d < 0 || o.rate_block_max_d > 4096 || o.lp_block_min_deg < 0 ||
+      o.lp_block_min_deg > (1 << 20))
+    return HG_ERR_INVALID;
   int64_t W = 0;
   int64_t p = 0;
   if (mem == HG_MEM_HOST) {
@@ -250,6 +255,10 @@ int hg_coarsen_level(hg_t* h, int32_t k, int32_t* out_level, int32_t* out_n, int
     P.S = h->opt.subrounds;
     P.T = h->opt.rating_max_net_size;
     P.c_max = (int32_t)((h->W0 + limit - 1) / limit);
+    P.cuts.warp = h->opt.rate_warp_max_d ? h->opt.rate_warp_max_d : 256;
+    P.cuts.pair = h->opt.rate_pair_max_d ? h->opt.rate_pair_max_d : 1024;
+    P.cuts.quad = h->opt.rate_quad_max_d ? h->opt.rate_quad_max_d : 2048;
+    P.cuts.block = h->opt.rate_block_max_d ? h->opt.rate_block_max_d : 4096;
     hgk::CoarsenCounters cc;
     DBuf<int32_t> cw;
     hgk::cluster_level(h->cx, L, P, cc, cw);
@@ -334,7 +343,9 @@ int hg_lp_refine(hg_t* h, int32_t level, int32_t k, int32_t eps_ppm, int32_t max
     hgk::RefineCounters rc;
     const Level& L = *h->levels[level];
     hgk::LPResult r = hgk::lp_refine_level(h->cx, L, level, k, eps_ppm, max_passes,
-                                           h->opt.subrounds, h->opt.seed, h->W0, part, rc);
+                                           h->opt.subrounds, h->opt.seed, h->W0,
+                                           h->opt.lp_block_min_deg ? h->opt.lp_block_min_deg : 64,
+                                           part, rc);
     h->stats.ms_phi += rc.ms_phi;
     h->stats.ms_lp_gain += rc.ms_gain;
     h->stats.ms_lp_select += rc.ms_select;

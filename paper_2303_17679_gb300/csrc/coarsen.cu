@@ -807,15 +807,14 @@ k_rate_split_argmax(RateArgs A, const int32_t* __restrict__ split, int32_t lo, i
 //     eight warps, 4096-slot hash          D <= 2048, W <= 65536 (other levels)
 //   3 sixteen warps, 8192-slot hash        D <= 4096, W <= 65536 (other levels)
 //   4 split over the grid                  the rest
-__device__ __forceinline__ int rate_class(int64_t W, int32_t n, bool dense_block, bool narrow) {
+__device__ __forceinline__ int rate_class(int64_t W, int32_t n, bool dense_block, RateCuts cut) {
   const int64_t D = W < n ? W : n;  // bound on the distinct candidate clusters
-  (void)narrow;
-  if (D <= D_WARP) return 0;
+  if (D <= cut.warp) return 0;
   if (dense_block && W <= DENSE_W) return 2;
-  if (D <= D_PAIR) return 1;
+  if (D <= cut.pair) return 1;
   if (!dense_block && W <= TEAM_W) {
-    if (D <= D_QUAD) return 2;
-    if (D <= D_BLOCK) return 3;
+    if (D <= cut.quad) return 2;
+    if (D <= cut.block) return 3;
   }
   return 4;
 }
@@ -863,14 +862,14 @@ __global__ void k_node_work(const int32_t* __restrict__ ioff, const int32_t* __r
 
 // key = class * S + sub-round of every node with W(u) > 0, and the counts.
 __global__ void k_node_classify(const int32_t* __restrict__ wof, int32_t n, uint64_t seed,
-                                int level, int S, bool dense_block, bool narrow,
+                                int level, int S, bool dense_block, RateCuts cut,
                                 int32_t* __restrict__ key_of, int32_t* __restrict__ kcount) {
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
        u += (int64_t)gridDim.x * blockDim.x) {
     const int32_t W = wof[u];
     int32_t key = -1;
     if (W > 0) {
-      key = rate_class(W, n, dense_block, narrow) * S +
+      key = rate_class(W, n, dense_block, cut) * S +
             subround_of_node_cluster(seed, level, (int)u, S);
       atomicAdd(&kcount[key], 1);
     }
@@ -1461,7 +1460,7 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   const size_t vbytes = narrow ? 4 : 8;
   const bool dense_block = (size_t)n * (vbytes + 4) <= SMEM_BUDGET;
   k_node_classify<<<g_nodes, 256, 0, cx.stream>>>(wof.p, n, P.seed, P.level, S, dense_block,
-                                                   narrow, key_of.p, kcount.p);
+                                                   P.cuts, key_of.p, kcount.p);
   check_launch("node_classify");
   k_node_scatter<<<g_nodes, 256, nkeys * sizeof(int32_t), cx.stream>>>(key_of.p, n, nkeys,
                                                                         kcount.p, kfill.p, list.p);

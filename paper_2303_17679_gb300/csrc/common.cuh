@@ -264,12 +264,19 @@ bool validate_level_device(const Ctx& cx, const Level& L, int64_t* total_node_w,
 
 // ------------------------------------------------------ coarsening (coarsen.cu)
 
+// Upper bounds on D = min(W(u), n) of the rating team classes (launch
+// mapping only; the tables hold 2 D slots).
+struct RateCuts {
+  int32_t warp, pair, quad, block;
+};
+
 struct CoarsenParams {
   uint64_t seed;
   int level;      // index of the level being clustered
   int S;          // sub-rounds
   int T;          // rating net-size threshold
   int32_t c_max;  // cluster weight cap
+  RateCuts cuts;
 };
 
 struct CoarsenCounters {
@@ -317,7 +324,7 @@ struct LPResult {
 
 LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, int eps_ppm,
                          int max_passes, int S, uint64_t seed, int64_t total_node_weight,
-                         int32_t* part, RefineCounters& rc);
+                         int lp_block_deg, int32_t* part, RefineCounters& rc);
 
 // ---------------------------------------------------------------- timing
 

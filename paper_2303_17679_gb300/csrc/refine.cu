@@ -93,25 +93,24 @@ __global__ void k_objective(const unsigned long long* __restrict__ lam,
 // -------------------------------------------- sub-round node lists (a11)
 
 // Nodes of a pass are listed by key = sub-round * 2 + class, class 1 for
-// nodes with more than GAIN_BLOCK_DEG incident nets (a block per node).
-constexpr int GAIN_BLOCK_DEG = 64;
-
+// nodes with more than block_deg incident nets (a block per node).
 __device__ __forceinline__ int lp_key(const int32_t* ioff, uint64_t seed, int level, int pass,
-                                      int64_t u, int S) {
+                                      int64_t u, int S, int block_deg) {
   const int32_t deg = ioff[u + 1] - ioff[u];
   if (deg == 0) return -1;  // isolated nodes never move
-  return subround_of_node_lp(seed, level, pass, (int)u, S) * 2 + (deg > GAIN_BLOCK_DEG ? 1 : 0);
+  return subround_of_node_lp(seed, level, pass, (int)u, S) * 2 + (deg > block_deg ? 1 : 0);
 }
 
 __global__ void k_lp_count(const int32_t* __restrict__ ioff, int32_t n, uint64_t seed, int level,
-                           const int32_t* __restrict__ d_pass, int S, int32_t* __restrict__ cnt) {
+                           const int32_t* __restrict__ d_pass, int S, int block_deg,
+                           int32_t* __restrict__ cnt) {
   extern __shared__ int32_t s_cnt[];
   const int pass = *d_pass;
   for (int i = threadIdx.x; i < 2 * S; i += blockDim.x) s_cnt[i] = 0;
   __syncthreads();
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
        u += (int64_t)gridDim.x * blockDim.x) {
-    const int key = lp_key(ioff, seed, level, pass, u, S);
+    const int key = lp_key(ioff, seed, level, pass, u, S, block_deg);
     if (key >= 0) atomicAdd(&s_cnt[key], 1);
   }
   __syncthreads();
@@ -121,7 +120,7 @@ __global__ void k_lp_count(const int32_t* __restrict__ ioff, int32_t n, uint64_t
 
 // Every block recomputes the (tiny) exclusive scan of the 2S counts.
 __global__ void k_lp_scatter(const int32_t* __restrict__ ioff, int32_t n, uint64_t seed, int level,
-                             const int32_t* __restrict__ d_pass, int S,
+                             const int32_t* __restrict__ d_pass, int S, int block_deg,
                              const int32_t* __restrict__ cnt, int32_t* __restrict__ fill,
                              int32_t* __restrict__ off, int32_t* __restrict__ list) {
   extern __shared__ int32_t s_off[];
@@ -139,7 +138,7 @@ __global__ void k_lp_scatter(const int32_t* __restrict__ ioff, int32_t n, uint64
   __syncthreads();
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
        u += (int64_t)gridDim.x * blockDim.x) {
-    const int key = lp_key(ioff, seed, level, pass, u, S);
+    const int key = lp_key(ioff, seed, level, pass, u, S, block_deg);
     if (key >= 0) list[s_off[key] + atomicAdd(&fill[key], 1)] = (int32_t)u;
   }
 }
@@ -261,7 +260,7 @@ __device__ __forceinline__ void gain_emit(const GainArgs& A, int32_t u, int from
   }
 }
 
-// class 0 (at most GAIN_BLOCK_DEG incident nets): one warp per node
+// class 0 (at most block_deg incident nets): one warp per node
 __global__ void __launch_bounds__(WARPS * 32) k_lp_gain_warp(GainArgs A) {
   __shared__ int32_t s_cnt[WARPS][64];
   const int lane = lane_id();
@@ -715,7 +714,7 @@ PassGraphCache& pass_graph_cache(const Ctx& cx) {
 
 LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, int eps_ppm,
                          int max_passes, int S, uint64_t seed, int64_t total_node_weight,
-                         int32_t* part, RefineCounters& rc) {
+                         int lp_block_deg, int32_t* part, RefineCounters& rc) {
   LPResult res;
   PinState st;
   {
@@ -799,10 +798,11 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
       EventTimer tm(cx, timed ? &rc.ms_gain : nullptr);
       k_lp_count<<<g_nodes, 256, 2 * S * sizeof(int32_t), sm>>>(L.ioff.p, n, seed,
                                                                       level_index, d_pass.p, S,
-                                                                      sr_cnt.p);
+                                                                      lp_block_deg, sr_cnt.p);
       check_launch("lp_count");
       k_lp_scatter<<<g_nodes, 256, (2 * S + 1) * sizeof(int32_t), sm>>>(
-          L.ioff.p, n, seed, level_index, d_pass.p, S, sr_cnt.p, sr_fill.p, sr_off.p, list.p);
+          L.ioff.p, n, seed, level_index, d_pass.p, S, lp_block_deg, sr_cnt.p, sr_fill.p,
+          sr_off.p, list.p);
       check_launch("lp_scatter");
     }
     for (int s = 0; s < S; ++s) {

@@ -43,7 +43,15 @@ class hg_options(ctypes.Structure):
         ("dev_alloc", ALLOC_FN),
         ("dev_free", FREE_FN),
         ("alloc_ctx", ctypes.c_void_p),
+        ("rate_warp_max_d", ctypes.c_int32),
+        ("rate_pair_max_d", ctypes.c_int32),
+        ("rate_quad_max_d", ctypes.c_int32),
+        ("rate_block_max_d", ctypes.c_int32),
+        ("lp_block_min_deg", ctypes.c_int32),
     ]
+
+    TUNABLE = ("rate_warp_max_d", "rate_pair_max_d", "rate_quad_max_d", "rate_block_max_d",
+               "lp_block_min_deg")
 
 
 class hg_job(ctypes.Structure):

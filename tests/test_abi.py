@@ -90,6 +90,25 @@ def test_bad_options_rejected(lib):
         assert rc == hg.HG_ERR_INVALID
 
 
+def test_launch_mapping_options_bounded(lib):
+    """The tunable cutoffs default to 0 (built-in mapping) and are rejected
+    above the capacity of the kernels' tables."""
+    from paper_2303_17679_gb300 import hg
+    o = hg.hg_default_options()
+    assert all(getattr(o, f) == 0 for f in hg.hg_options.TUNABLE)
+    for field, value in (("rate_warp_max_d", 257), ("rate_pair_max_d", 1025),
+                         ("rate_quad_max_d", 2049), ("rate_block_max_d", 4097),
+                         ("lp_block_min_deg", -1), ("rate_warp_max_d", -1)):
+        bad = hg.hg_default_options()
+        setattr(bad, field, value)
+        h = ctypes.c_void_p()
+        off = np.array([0, 2], np.int32)
+        pins = np.array([0, 1], np.int32)
+        rc = lib.hg_create(2, 1, ctypes.c_void_p(off.ctypes.data), ctypes.c_void_p(pins.ctypes.data),
+                           None, None, hg.HG_MEM_HOST, ctypes.byref(bad), None, ctypes.byref(h))
+        assert rc == hg.HG_ERR_INVALID, (field, value)
+
+
 def test_null_handle_calls_are_rejected(lib):
     from paper_2303_17679_gb300 import hg
     assert lib.hg_destroy(None) == hg.HG_OK
