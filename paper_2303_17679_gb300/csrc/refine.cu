@@ -285,9 +285,12 @@ __global__ void __launch_bounds__(WARPS * 32) k_lp_gain_warp(GainArgs A) {
   if (lane == 0 && incid) atomicAdd(A.work, (unsigned long long)incid);
 }
 
-// class 1: one block (WARPS warps) per node; the warps split I(u) and their
-// partial accumulators are summed in shared memory before the argmax
-__global__ void __launch_bounds__(WARPS * 32) k_lp_gain_block(GainArgs A) {
+// class 1: one block (GAIN_BLOCK_WARPS warps) per node; the warps split I(u)
+// and their partial accumulators are summed in shared memory before the argmax
+constexpr int GAIN_BLOCK_WARPS = 32;
+
+__global__ void __launch_bounds__(GAIN_BLOCK_WARPS * 32) k_lp_gain_block(GainArgs A) {
+  constexpr int WARPS = GAIN_BLOCK_WARPS;
   __shared__ long long s_acc[WARPS][64];
   __shared__ long long s_bw[WARPS][2];
   __shared__ int32_t s_cnt[WARPS][64];
@@ -337,17 +340,32 @@ __global__ void __launch_bounds__(WARPS * 32) k_lp_gain_block(GainArgs A) {
 
 // ------------------------------------- pair bucketing + selection (a12)
 
-// Exclusive scan of the k*k direction counts into s_doff (by thread 0; k*k
-// <= 4096 small integers).
+// Exclusive scan of the k*k direction counts into s_doff[0..kk] by the whole
+// block (kk <= 4096: each thread scans a contiguous run, then the run totals
+// are scanned by warps).
 __device__ void direction_offsets(const int32_t* dcount, int kk, int32_t* s_doff) {
-  if (threadIdx.x == 0) {
-    int32_t run = 0;
-    for (int d = 0; d < kk; ++d) {
-      s_doff[d] = run;
-      run += dcount[d];
-    }
-    s_doff[kk] = run;
+  __shared__ int32_t s_tot[32];
+  const int nt = blockDim.x;
+  const int per = (kk + nt - 1) / nt;
+  const int d0 = threadIdx.x * per;
+  int32_t run = 0;
+  for (int d = d0; d < d0 + per && d < kk; ++d) run += dcount[d];
+  const int32_t incl = warp_inclusive_scan(run);
+  if (lane_id() == 31) s_tot[warp_in_block()] = incl;
+  __syncthreads();
+  if (warp_in_block() == 0) {
+    const int nw = nt >> 5;
+    int32_t x = lane_id() < nw ? s_tot[lane_id()] : 0;
+    x = warp_inclusive_scan(x);
+    if (lane_id() < nw) s_tot[lane_id()] = x;
   }
+  __syncthreads();
+  int32_t base = (warp_in_block() ? s_tot[warp_in_block() - 1] : 0) + incl - run;
+  for (int d = d0; d < d0 + per && d < kk; ++d) {
+    s_doff[d] = base;
+    base += dcount[d];
+  }
+  if (threadIdx.x == nt - 1) s_doff[kk] = s_tot[(nt >> 5) - 1];
   __syncthreads();
 }
 
@@ -819,7 +837,7 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
         if (timed) gain_timer.end();
         check_launch("lp_gain_warp");
         if (timed) gain_timer.begin();
-        k_lp_gain_block<<<g_gain_block, WARPS * 32, 0, sm>>>(G);
+        k_lp_gain_block<<<g_gain_block, GAIN_BLOCK_WARPS * 32, 0, sm>>>(G);
         if (timed) gain_timer.end();
         check_launch("lp_gain_block");
         rc.lp_gain_launches += 2;
