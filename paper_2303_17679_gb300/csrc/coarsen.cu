@@ -889,10 +889,13 @@ __global__ void k_node_scatter(const int32_t* __restrict__ key_of, int32_t n, in
     }
   }
   __syncthreads();
-  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
-       u += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t key = key_of[u];
-    if (key >= 0) list[s_off[key] + atomicAdd(&kfill[key], 1)] = (int32_t)u;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < n; b += stride) {
+    const int64_t u = b + lane_id();
+    const bool valid = u < n;
+    const int32_t key = valid ? key_of[u] : -1;
+    const int32_t slot = warp_claim_slot(kfill, key, __ballot_sync(FULL, valid));
+    if (slot >= 0) list[s_off[key] + slot] = (int32_t)u;
   }
 }
 

@@ -88,6 +88,27 @@ constexpr unsigned FULL = 0xffffffffu;
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 __device__ __forceinline__ int warp_in_block() { return threadIdx.x >> 5; }
 
+// Claims one slot from counter[key] for every lane of `active` (a ballot
+// taken in converged code) with key >= 0: lanes with equal keys share one
+// atomicAdd and take consecutive slots in lane order.  Returns the lane's
+// slot, or -1 for a lane outside `active` or with key < 0.
+__device__ __forceinline__ int32_t warp_claim_slot(int32_t* counter, int key, unsigned active) {
+  const int lane = threadIdx.x & 31;
+  const bool mine = ((active >> lane) & 1u) && key >= 0;
+  const unsigned want = __ballot_sync(0xffffffffu, mine);
+  const unsigned peers = __match_any_sync(0xffffffffu, mine ? key : -1 - lane) & want;
+  int32_t slot = -1;
+  if (mine) {
+    const int leader = __ffs(peers) - 1;
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    int32_t base = 0;
+    if (lane == leader) base = atomicAdd(&counter[key], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    slot = base + rank;
+  }
+  return slot;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_inclusive_scan(T x) {
 #pragma unroll

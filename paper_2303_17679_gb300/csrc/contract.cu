@@ -46,11 +46,17 @@ __global__ void k_map(const int32_t* __restrict__ rep, const int32_t* __restrict
 
 __global__ void k_classify_nets(const int32_t* __restrict__ eoff, int32_t m,
                                 int32_t* __restrict__ lists, int32_t* __restrict__ counts) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t sz = eoff[e + 1] - eoff[e];
-    const int cls = sz <= SMALL_NET ? 0 : (sz <= MID_NET ? 1 : 2);
-    lists[(int64_t)cls * m + atomicAdd(&counts[cls], 1)] = (int32_t)e;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < m; b += stride) {
+    const int64_t e = b + lane_id();
+    const bool valid = e < m;
+    int cls = -1;
+    if (valid) {
+      const int32_t sz = eoff[e + 1] - eoff[e];
+      cls = sz <= SMALL_NET ? 0 : (sz <= MID_NET ? 1 : 2);
+    }
+    const int32_t slot = warp_claim_slot(counts, cls, __ballot_sync(FULL, valid));
+    if (valid) lists[(int64_t)cls * m + slot] = (int32_t)e;
   }
 }
 

@@ -136,10 +136,13 @@ __global__ void k_lp_scatter(const int32_t* __restrict__ ioff, int32_t n, uint64
       for (int i = 0; i <= 2 * S; ++i) off[i] = s_off[i];
   }
   __syncthreads();
-  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
-       u += (int64_t)gridDim.x * blockDim.x) {
-    const int key = lp_key(ioff, seed, level, pass, u, S, block_deg);
-    if (key >= 0) list[s_off[key] + atomicAdd(&fill[key], 1)] = (int32_t)u;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < n; b += stride) {
+    const int64_t u = b + lane_id();
+    const bool valid = u < n;
+    const int key = valid ? lp_key(ioff, seed, level, pass, u, S, block_deg) : -1;
+    const int32_t slot = warp_claim_slot(fill, key, __ballot_sync(FULL, valid));
+    if (slot >= 0) list[s_off[key] + slot] = (int32_t)u;
   }
 }
 
@@ -380,9 +383,13 @@ __global__ void k_lp_bucket(const int32_t* __restrict__ mv_u, const int32_t* __r
   if (blockIdx.x == 0)
     for (int d = threadIdx.x; d <= kk; d += blockDim.x) doff[d] = s_doff[d];
   const int32_t nm = words[SW_MOVES];
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nm; i += gridDim.x * blockDim.x) {
-    const int d = part[mv_u[i]] * k + mv_to[i];
-    bucket[s_doff[d] + atomicAdd(&dfill[d], 1)] = i;
+  const int32_t stride = gridDim.x * blockDim.x;
+  for (int32_t b = blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < nm; b += stride) {
+    const int32_t i = b + lane_id();
+    const bool valid = i < nm;
+    const int d = valid ? part[mv_u[i]] * k + mv_to[i] : -1;
+    const int32_t slot = warp_claim_slot(dfill, d, __ballot_sync(FULL, valid));
+    if (slot >= 0) bucket[s_doff[d] + slot] = i;
   }
 }
 
