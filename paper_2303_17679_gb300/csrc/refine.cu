@@ -8,6 +8,7 @@
 // sub-round is four launches: best moves (a11), bucketing by block pair and
 // per-pair prefix selection (a12), application (a13).
 #include <climits>
+#include <mutex>
 
 #include "common.cuh"
 #include "pintile.cuh"
@@ -394,7 +395,11 @@ __global__ void k_lp_bucket(const int32_t* __restrict__ mv_u, const int32_t* __r
 }
 
 constexpr int SEL_THREADS = 256;
-constexpr int SEL_SMEM_CAP = 1024;  // moves per direction sorted in shared memory
+// Moves per direction sorted in shared memory (more go through global
+// memory): 4096 for k <= 8, 2048 for k <= 16, else 1024 (pairs hold fewer
+// moves as k grows, and a smaller buffer lets more pair blocks share an SM).
+__host__ __device__ inline int sel_cap_for(int k) { return k <= 8 ? 4096 : (k <= 16 ? 2048 : 1024); }
+inline size_t sel_smem_bytes(int cap) { return (size_t)(4 * cap + 2) * sizeof(unsigned long long); }
 
 // Sort key: gain descending, node id ascending (gains are < 2^31).
 __device__ __forceinline__ unsigned long long sel_key(long long g, int32_t u) {
@@ -465,8 +470,12 @@ k_lp_select(const int32_t* __restrict__ ioff, const int32_t* __restrict__ bucket
             unsigned long long* __restrict__ gkeys, long long* __restrict__ gpre,
             int32_t* __restrict__ ap_u, int32_t* __restrict__ ap_from,
             int32_t* __restrict__ ap_to, int32_t* __restrict__ words) {
-  __shared__ unsigned long long s_keys[2][SEL_SMEM_CAP];
-  __shared__ long long s_pre[2][SEL_SMEM_CAP + 1];
+  extern __shared__ __align__(16) unsigned long long sel_smem[];
+  const int cap = sel_cap_for(k);
+  unsigned long long* s_keys0 = sel_smem;
+  unsigned long long* s_keys1 = sel_smem + cap;
+  long long* s_pre0 = reinterpret_cast<long long*>(sel_smem + 2 * cap);
+  long long* s_pre1 = s_pre0 + cap + 1;
   __shared__ long long s_red[33];
   __shared__ int s_best;
   // decode the pair index into (a, b), a < b
@@ -489,10 +498,10 @@ k_lp_select(const int32_t* __restrict__ ioff, const int32_t* __restrict__ bucket
   const int Pa = pow2(na), Pb = pow2(nb);
   // buffers: shared memory when the padded sequence fits, else a global
   // region of 2 * count slots at twice the direction's bucket offset
-  unsigned long long* ka = Pa <= SEL_SMEM_CAP ? s_keys[0] : gkeys + 2 * (int64_t)oa;
-  unsigned long long* kb = Pb <= SEL_SMEM_CAP ? s_keys[1] : gkeys + 2 * (int64_t)ob;
-  long long* A = na <= SEL_SMEM_CAP ? s_pre[0] : gpre + (int64_t)oa + dab;
-  long long* B = nb <= SEL_SMEM_CAP ? s_pre[1] : gpre + (int64_t)ob + dba;
+  unsigned long long* ka = Pa <= cap ? s_keys0 : gkeys + 2 * (int64_t)oa;
+  unsigned long long* kb = Pb <= cap ? s_keys1 : gkeys + 2 * (int64_t)ob;
+  long long* A = na <= cap ? s_pre0 : gpre + (int64_t)oa + dab;
+  long long* B = nb <= cap ? s_pre1 : gpre + (int64_t)ob + dba;
 
   for (int i = threadIdx.x; i < Pa; i += blockDim.x) {
     if (i < na) {
@@ -811,6 +820,14 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   d_pass.alloc(&cx.alloc, 1);
   HG_CUDA(cudaMemsetAsync(d_pass.p, 0, sizeof(int32_t), cx.stream));
   const bool use_graph = !cx.timing;
+  const size_t sel_bytes = sel_smem_bytes(sel_cap_for(k));
+  {
+    static std::once_flag once;
+    std::call_once(once, [] {
+      HG_CUDA(cudaFuncSetAttribute(k_lp_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sel_smem_bytes(sel_cap_for(2))));
+    });
+  }
   const int per_pass_launches = 3 + 5 * S;
   auto enqueue_pass = [&](bool timed, cudaStream_t sm) {
     HG_CUDA(cudaMemsetAsync(sr_cnt.p, 0, sr_cnt.bytes(), sm));
@@ -854,7 +871,7 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
         k_lp_bucket<<<g_bucket, 256, (kk + 1) * sizeof(int32_t), sm>>>(
             mv_u.p, mv_to.p, part, k, dc_s, df_s, doff.p, w_s, bucket.p);
         check_launch("lp_bucket");
-        k_lp_select<<<g_sel, SEL_THREADS, 0, sm>>>(
+        k_lp_select<<<g_sel, SEL_THREADS, sel_bytes, sm>>>(
             L.ioff.p, bucket.p, doff.p, dc_s, mv_u.p, mv_to.p, mv_g.p, L.c.p, st.bw.p, lmax, k,
             gkeys.p, gpre.p, ap_u.p, ap_from.p, ap_to.p, w_s);
         check_launch("lp_select");
