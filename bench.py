@@ -143,7 +143,7 @@ def sum_over_ranks(world, x: float) -> float:
 
 # ------------------------------------------------------------ CPU oracle
 
-ORACLE_SAMPLE_N = 200_000
+ORACLE_SAMPLE_N = int(os.environ.get("BENCH_ORACLE_N", "200000"))
 
 
 def oracle_sample():
