@@ -108,31 +108,32 @@ __device__ __forceinline__ uint32_t slot_hash(int32_t C) { return (uint32_t)C * 
 constexpr int32_t ADD_EXISTING = -1;
 constexpr int32_t ADD_FULL = -2;
 
-// 32-bit ratings: one 64-bit word per slot, cluster id above the rating, an
-// empty slot = id -1 with rating 0.  An add to the low half never carries
-// into the id because every rating stays below 2^31.
+// 32-bit ratings: a key array and a value array (32-bit each).  An insertion
+// claims the key with a 32-bit CAS and every visit adds its term with a
+// 32-bit atomic add; both commute, so the sums do not depend on the order.
 struct PackedHash {
-  unsigned long long* slot;
+  uint32_t* val;
+  int32_t* key;
   uint32_t mask;
-  static constexpr unsigned long long EMPTY = 0xFFFFFFFF00000000ull;
   static constexpr size_t BYTES_PER_SLOT = 8;
-  __device__ __forceinline__ void init(uint32_t i) { slot[i] = EMPTY; }
+  __device__ __forceinline__ void init(uint32_t i) {
+    key[i] = EMPTY_KEY;
+    val[i] = 0;
+  }
   // the slot index when C was inserted by this call, else ADD_EXISTING / ADD_FULL
   __device__ __forceinline__ int32_t add(int32_t C, uint32_t r, uint32_t max_probe = 0xFFFFFFFFu) {
-    const unsigned long long mine = ((unsigned long long)(uint32_t)C << 32) | r;
     uint32_t h = slot_hash(C) & mask;
     for (uint32_t probe = 0; probe <= mask && probe < max_probe; ++probe) {
-      unsigned long long w = slot[h];
-      while (true) {
-        const uint32_t k = (uint32_t)(w >> 32);
-        if (k == (uint32_t)C) {
-          atomicAdd(&slot[h], (unsigned long long)r);
-          return ADD_EXISTING;
-        }
-        if (k != 0xFFFFFFFFu) break;
-        const unsigned long long old = atomicCAS(&slot[h], w, mine);
-        if (old == w) return (int32_t)h;
-        w = old;
+      int32_t k = key[h];
+      bool fresh = false;
+      if (k == EMPTY_KEY) {
+        const int32_t old = atomicCAS(&key[h], EMPTY_KEY, C);
+        fresh = old == EMPTY_KEY;
+        k = fresh ? C : old;
+      }
+      if (k == C) {
+        atomicAdd(&val[h], r);
+        return fresh ? (int32_t)h : ADD_EXISTING;
       }
       h = (h + 1) & mask;
     }
@@ -140,10 +141,10 @@ struct PackedHash {
   }
   // cluster and rating of slot i (C = -1 when empty); the slot is cleared
   __device__ __forceinline__ void take(uint32_t i, int32_t& C, uint32_t& v) {
-    const unsigned long long w = slot[i];
-    C = (int32_t)(uint32_t)(w >> 32);
-    v = (uint32_t)w;
-    slot[i] = EMPTY;
+    C = key[i];
+    v = val[i];
+    key[i] = EMPTY_KEY;
+    val[i] = 0;
   }
 };
 
@@ -192,7 +193,8 @@ template <typename H>
 __device__ __forceinline__ H make_hash(unsigned char* base, uint32_t slots);
 template <>
 __device__ __forceinline__ PackedHash make_hash<PackedHash>(unsigned char* base, uint32_t slots) {
-  return PackedHash{reinterpret_cast<unsigned long long*>(base), slots - 1};
+  uint32_t* val = reinterpret_cast<uint32_t*>(base);
+  return PackedHash{val, reinterpret_cast<int32_t*>(val + slots), slots - 1};
 }
 template <>
 __device__ __forceinline__ WideHash make_hash<WideHash>(unsigned char* base, uint32_t slots) {
