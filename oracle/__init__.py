@@ -53,6 +53,8 @@ def _L():
             lib.o_objective.argtypes = [i32, i32, vp, vp, vp, i32, vp]
             lib.o_gains.argtypes = [i32, i32, vp, vp, vp, i32, vp, vp]
             lib.o_block_weights.argtypes = [i32, vp, i32, vp, vp]
+            lib.o_recalculate_gains.restype = i32
+            lib.o_recalculate_gains.argtypes = [i32, i32, vp, vp, vp, i32, vp, i32, vp, vp, vp]
             lib.o_balance_limit.restype = i64
             lib.o_balance_limit.argtypes = [i64, i32, i32]
             lib.o_lp_refine.restype = i32
@@ -139,6 +141,19 @@ def gains(hg, k: int, part) -> np.ndarray:
     out = np.zeros((hg.n, k), dtype=np.int64)
     _L().o_gains(hg.n, hg.m, _p(off), _p(pins), _p(w), k, _p(part), _p(out))
     return out
+
+
+def recalculate_gains(hg, k: int, part, nodes, targets) -> np.ndarray:
+    """Exact gains of the move sequence (nodes[i] -> targets[i], in this
+    order) from partition `part` (Sec. 6.3)."""
+    off, pins, w, _ = _arrs(hg)
+    part, nodes, targets = _i32(part), _i32(nodes), _i32(targets)
+    out = np.zeros(max(len(nodes), 1), np.int64)
+    rc = _L().o_recalculate_gains(hg.n, hg.m, _p(off), _p(pins), _p(w), k, _p(part), len(nodes),
+                                  _p(nodes), _p(targets), _p(out))
+    if rc != 0:
+        raise ValueError("invalid move sequence")
+    return out[:len(nodes)]
 
 
 def block_weights(hg, k: int, part) -> np.ndarray:

@@ -467,6 +467,37 @@ void o_gains(int32_t n, int32_t m, const int32_t* off, const int32_t* pins, cons
       out[(int64_t)u * k + t] = (t == part[u]) ? 0 : gain(h, phi, part, u, t);
 }
 
+// Exact gains of a move sequence M = <m_1, ..., m_l>, m_i = (u_i, Pi[u_i],
+// t_i), each node moved at most once (Sec. 6.3, "The Parallel Gain
+// Recalculation Algorithm"): g_i is the gain of Sec. 6 of moving u_i to t_i
+// in the partition reached after m_1 .. m_{i-1}, i.e. the objective decrease
+// that m_i causes when the moves are performed in this order.  Evaluated here
+// by performing the moves one by one on the pin counts.  Returns 0, or 1 for
+// a node moved twice, a target outside [0, k) or equal to the node's block.
+int32_t o_recalculate_gains(int32_t n, int32_t m, const int32_t* off, const int32_t* pins,
+                            const int32_t* w, int32_t k, const int32_t* part, int32_t l,
+                            const int32_t* nodes, const int32_t* targets, int64_t* gains) {
+  Hypergraph h = load(n, m, off, pins, w, nullptr);
+  vector<int32_t> cur(part, part + n);
+  vector<char> moved(n, 0);
+  for (int i = 0; i < l; ++i) {
+    const int u = nodes[i], t = targets[i];
+    if (u < 0 || u >= n || moved[u] || t < 0 || t >= k || t == part[u]) return 1;
+    moved[u] = 1;
+  }
+  auto phi = pin_counts(h, k, cur.data());
+  for (int i = 0; i < l; ++i) {
+    const int u = nodes[i], t = targets[i], s = cur[u];
+    gains[i] = gain(h, phi, cur.data(), u, t);
+    for (int e : h.inc[u]) {
+      phi[e][s] -= 1;
+      phi[e][t] += 1;
+    }
+    cur[u] = t;
+  }
+  return 0;
+}
+
 void o_block_weights(int32_t n, const int32_t* c, int32_t k, const int32_t* part, int64_t* bw) {
   for (int i = 0; i < k; ++i) bw[i] = 0;
   for (int u = 0; u < n; ++u) bw[part[u]] += c ? c[u] : 1;
