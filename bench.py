@@ -317,6 +317,54 @@ def run_serve(hg, seconds, slots):
             "identical_objectives": all(objs_s[i] == objs_p[i] for i in objs_p)}
 
 
+def run_gain_recalc(hg, torch, hgr, d_off, d_pins, d_w, d_c, opt, stream, part, peak):
+    """Exact gains of a move sequence (Sec. 6.3) on config 2, level 0: a seeded
+    sequence moving 10 % of the nodes (from the V-cycle's partition) to
+    random other blocks.  Algorithmic bytes: 16 per move (node, target, index
+    write and read), 8 per incidence of a moved node (net id, mark), 20 per
+    pin of a touched net (pin, index, block; the second loop re-reads pin and
+    index), 8 per touched net (offsets, weight)."""
+    import numpy as np
+    rng = np.random.default_rng(SEED + 7)
+    p0 = part.cpu().numpy()
+    nodes = rng.permutation(hgr.n)[: hgr.n // 10].astype(np.int32)
+    targets = ((p0[nodes] + 1 + rng.integers(0, K_BLOCKS - 1, size=len(nodes))) % K_BLOCKS)
+    dn = torch.from_numpy(nodes).cuda()
+    dt = torch.from_numpy(targets.astype(np.int32)).cuda()
+    gains = torch.zeros(len(nodes), dtype=torch.int64, device="cuda")
+    h = hg.hg_create(hgr.n, hgr.m, d_off, d_pins, d_w, d_c, hg.HG_MEM_DEVICE, opt, stream)
+    try:
+        for _ in range(3):
+            hg.hg_recalculate_gains(h, 0, K_BLOCKS, part, dn, dt, gains)
+        ms = []
+        for _ in range(10):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hg.hg_recalculate_gains(h, 0, K_BLOCKS, part, dn, dt, gains)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    finally:
+        hg.hg_destroy(h)
+    off = np.asarray(hgr.offsets, np.int64)
+    sizes = np.diff(off)
+    pins = np.asarray(hgr.pins)
+    moved = np.zeros(hgr.n, bool)
+    moved[nodes] = True
+    net_of = np.repeat(np.arange(hgr.m), sizes)
+    touched = np.zeros(hgr.m, bool)
+    touched[net_of[moved[pins]]] = True
+    incid = int(moved[pins].sum())
+    tpins = int(sizes[touched].sum())
+    nbytes = 16 * len(nodes) + 8 * incid + 20 * tpins + 8 * int(touched.sum())
+    t = statistics.median(ms) / 1e3
+    return {"workload": "config 2 level 0, 100,000 seeded moves to random other blocks",
+            "moves": len(nodes), "touched_nets": int(touched.sum()), "touched_pins": tpins,
+            "ms": t * 1e3, "moves_per_s": len(nodes) / t,
+            "achieved_gbs": nbytes / t / 1e9, "frac_of_hbm": nbytes / t / 1e9 / peak}
+
+
 # ------------------------------------------------------------ GPU path
 
 def run_ours(args, world, rank, local):
@@ -490,6 +538,9 @@ def run_ours(args, world, rank, local):
         _, _, pst = step(phases=True)
         line["phase_breakdown_ms"] = {k: round(v, 3) for k, v in pst.items()
                                       if k.startswith("ms_") and not isinstance(v, list)}
+    if world == 1:
+        line["gain_recalc"] = run_gain_recalc(hg, torch, hgr, d_off, d_pins, d_w, d_c, opt, stream,
+                                              part, peak)
     if world == 1 and not args.no_batch:
         line["batch"] = run_batch(hg, torch, args.slots)
     if world == 1 and args.serve_seconds > 0:

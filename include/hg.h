@@ -206,6 +206,25 @@ int hg_objective(hg_t* h, int32_t level, int32_t k, const int32_t* part, int64_t
 int hg_pin_counts(hg_t* h, int32_t level, int32_t k, const int32_t* part, int32_t* phi,
                   uint64_t* lambda, int64_t* block_weights);
 
+/* Exact gains of a move sequence (Sec. 6.3, "The Parallel Gain Recalculation
+ * Algorithm", Algorithm 4).  Move i moves node move_nodes[i] from its block
+ * in `part` to move_targets[i]; the moves are taken in index order and every
+ * node moves at most once.  gains[i] = the objective decrease (Sec. 2) that
+ * move i causes after moves 0 .. i-1, so the gains sum to
+ * f(part) - f(part after all moves).  Computed per net over the nets of the
+ * moved nodes; `part` is not changed.
+ *   level         a level held by the handle
+ *   k             2..64; part has n_level device int32 entries in [0, k)
+ *   num_moves     0..n_level
+ *   move_nodes, move_targets  device, num_moves int32 each
+ *   gains         device, num_moves int64, written
+ * HG_ERR_INVALID for a node moved twice, a node or target out of range, a
+ * target equal to the node's block, or a block id in `part` out of range
+ * (checked on the device; the handle stays usable).  Synchronizes the stream. */
+int hg_recalculate_gains(hg_t* h, int32_t level, int32_t k, const int32_t* part,
+                         int32_t num_moves, const int32_t* move_nodes,
+                         const int32_t* move_targets, int64_t* gains);
+
 /* The objective f_{lambda-1} (Sec. 2) and the block weights c(V_i) of a
  * partition, for a hypergraph held by the caller in device memory, with no
  * handle and without allocating device memory.  The paper has no

@@ -374,6 +374,22 @@ int hg_objective(hg_t* h, int32_t level, int32_t k, const int32_t* part, int64_t
   });
 }
 
+int hg_recalculate_gains(hg_t* h, int32_t level, int32_t k, const int32_t* part,
+                         int32_t num_moves, const int32_t* move_nodes,
+                         const int32_t* move_targets, int64_t* gains) {
+  if (!h || !part || num_moves < 0) return HG_ERR_INVALID;
+  if (k < 2 || k > HG_MAX_K) return HG_ERR_INVALID;
+  if (num_moves > 0 && (!move_nodes || !move_targets || !gains)) return HG_ERR_INVALID;
+  if (!valid_level(h, level)) return HG_ERR_STATE;
+  if (num_moves > h->levels[level]->n) return HG_ERR_INVALID;  // a node would move twice
+  return guarded(h, [&]() -> int {
+    hgk::recalculate_gains(h->cx, *h->levels[level], k, part, num_moves, move_nodes, move_targets,
+                           gains);
+    sync_stats(h);
+    return HG_OK;
+  });
+}
+
 int hg_pin_counts(hg_t* h, int32_t level, int32_t k, const int32_t* part, int32_t* phi,
                   uint64_t* lambda, int64_t* block_weights) {
   if (!h || !part) return HG_ERR_INVALID;

@@ -343,6 +343,9 @@ struct LPResult {
   int passes = 0;
 };
 
+void recalculate_gains(const Ctx& cx, const Level& L, int k, const int32_t* part, int32_t l,
+                       const int32_t* nodes, const int32_t* targets, int64_t* gains);
+
 LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, int eps_ppm,
                          int max_passes, int S, uint64_t seed, int64_t total_node_weight,
                          int lp_block_deg, int32_t* part, RefineCounters& rc);

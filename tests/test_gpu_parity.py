@@ -270,3 +270,57 @@ def test_repeated_runs_identical():
     assert results[0][0] == results[1][0]
     assert np.array_equal(results[0][1], results[1][1])
     assert np.array_equal(results[0][2], results[1][2])
+
+
+# ------------------------------------------------- gain recalculation (Sec. 6.3)
+
+def random_moves(rng, part, k, count):
+    nodes = rng.permutation(len(part))[:count].astype(np.int32)
+    targets = np.array([(int(part[u]) + 1 + int(rng.integers(0, k - 1))) % k for u in nodes],
+                       np.int32)
+    return nodes, targets
+
+
+@pytest.mark.parametrize("name,k,frac,level", [("zipf20k", 8, 0.1, 0), ("zipf20k", 8, 1.0, 0),
+                                               ("zipf20k", 4, 0.3, 1), ("stress", 64, 0.2, 0),
+                                               ("weighted", 2, 0.5, 0)])
+def test_gain_recalculation_parity(oracle_mod, name, k, frac, level):
+    hgr = medium_cases()[name]
+    h = create(hgr, make_opt(factor=10))
+    try:
+        if level > 0:
+            hg.hg_coarsen_level(h, k)
+            got = hg.hg_get_level(h, level)
+            lvl = oracle_mod.Level(len(got["node_w"]), len(got["net_w"]), got["offsets"],
+                                   got["pins"], got["net_w"], got["node_w"])
+        else:
+            lvl = hgr
+        rng = np.random.default_rng(k * 100 + level)
+        part = rng.integers(0, k, size=lvl.n).astype(np.int32)
+        nodes, targets = random_moves(rng, part, k, max(1, int(frac * lvl.n)))
+        gains = torch.zeros(len(nodes), dtype=torch.int64, device="cuda")
+        hg.hg_recalculate_gains(h, level, k, dev(part), dev(nodes), dev(targets), gains)
+        want = oracle_mod.recalculate_gains(lvl, k, part, nodes, targets)
+        assert np.array_equal(gains.cpu().numpy(), want)
+        moved = part.copy()
+        moved[nodes] = targets
+        assert int(want.sum()) == (oracle_mod.objective(lvl, k, part)
+                                   - oracle_mod.objective(lvl, k, moved))
+    finally:
+        hg.hg_destroy(h)
+
+
+def test_gain_recalculation_rejects_bad_sequences():
+    hgr = medium_cases()["cfg1"]
+    h = create(hgr, make_opt())
+    try:
+        part = dev(np.zeros(hgr.n, np.int32))
+        gains = torch.zeros(2, dtype=torch.int64, device="cuda")
+        for nodes, targets in (([0, 0], [1, 1]), ([1, 2], [0, 1]), ([1, 2], [1, 5])):
+            with pytest.raises(hg.HgError) as ei:
+                hg.hg_recalculate_gains(h, 0, 4, part, dev(nodes), dev(targets), gains)
+            assert ei.value.status == hg.HG_ERR_INVALID
+        # the handle stays usable
+        hg.hg_recalculate_gains(h, 0, 4, part, dev([1, 2]), dev([1, 3]), gains)
+    finally:
+        hg.hg_destroy(h)
