@@ -53,6 +53,7 @@ def _L():
             lib.o_objective.argtypes = [i32, i32, vp, vp, vp, i32, vp]
             lib.o_gains.argtypes = [i32, i32, vp, vp, vp, i32, vp, vp]
             lib.o_block_weights.argtypes = [i32, vp, i32, vp, vp]
+            lib.o_gain_table.argtypes = [i32, i32, vp, vp, vp, i32, vp, vp, vp]
             lib.o_recalculate_gains.restype = i32
             lib.o_recalculate_gains.argtypes = [i32, i32, vp, vp, vp, i32, vp, i32, vp, vp, vp]
             lib.o_balance_limit.restype = i64
@@ -141,6 +142,16 @@ def gains(hg, k: int, part) -> np.ndarray:
     out = np.zeros((hg.n, k), dtype=np.int64)
     _L().o_gains(hg.n, hg.m, _p(off), _p(pins), _p(w), k, _p(part), _p(out))
     return out
+
+
+def gain_table(hg, k: int, part):
+    """(b [n] int64, p [n, k] int64) of Sec. 6.2 for partition `part`."""
+    off, pins, w, _ = _arrs(hg)
+    part = _i32(part)
+    b = np.zeros(max(hg.n, 1), np.int64)
+    p = np.zeros((max(hg.n, 1), k), np.int64)
+    _L().o_gain_table(hg.n, hg.m, _p(off), _p(pins), _p(w), k, _p(part), _p(b), _p(p))
+    return b[:hg.n], p[:hg.n]
 
 
 def recalculate_gains(hg, k: int, part, nodes, targets) -> np.ndarray:

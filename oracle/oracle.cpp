@@ -498,6 +498,27 @@ int32_t o_recalculate_gains(int32_t n, int32_t m, const int32_t* off, const int3
   return 0;
 }
 
+// Gain table (Sec. 6.2): benefit b(u) = w({e in I(u) : Phi(e, Pi[u]) = 1})
+// and penalty p(u, V_i) = w({e in I(u) : Phi(e, V_i) = 0}) for every block,
+// from their definitions; b is n int64, p is n x k int64.
+void o_gain_table(int32_t n, int32_t m, const int32_t* off, const int32_t* pins, const int32_t* w,
+                  int32_t k, const int32_t* part, int64_t* b, int64_t* p) {
+  Hypergraph h = load(n, m, off, pins, w, nullptr);
+  auto phi = pin_counts(h, k, part);
+  for (int u = 0; u < n; ++u) {
+    int64_t bu = 0;
+    for (int e : h.inc[u])
+      if (phi[e][part[u]] == 1) bu += h.w[e];
+    b[u] = bu;
+    for (int i = 0; i < k; ++i) {
+      int64_t pu = 0;
+      for (int e : h.inc[u])
+        if (phi[e][i] == 0) pu += h.w[e];
+      p[(int64_t)u * k + i] = pu;
+    }
+  }
+}
+
 void o_block_weights(int32_t n, const int32_t* c, int32_t k, const int32_t* part, int64_t* bw) {
   for (int i = 0; i < k; ++i) bw[i] = 0;
   for (int u = 0; u < n; ++u) bw[part[u]] += c ? c[u] : 1;
