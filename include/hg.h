@@ -225,6 +225,29 @@ int hg_recalculate_gains(hg_t* h, int32_t level, int32_t k, const int32_t* part,
                          int32_t num_moves, const int32_t* move_nodes,
                          const int32_t* move_targets, int64_t* gains);
 
+/* Gain table (Sec. 6.2, "The Gain Table"): benefit b(u) = w of the nets of
+ * u in which u is the only pin of its block, penalty p(u, V_i) = w of the
+ * nets of u without a pin in V_i; the gain of Sec. 6 is b(u) - p(u, V_t).
+ *   part      device, n_level int32 in [0, k) (k in 2..64)
+ *   benefit   device, n_level int64, written
+ *   penalty   device, n_level x k int64 (row per node), written
+ * HG_ERR_INVALID for a block id out of range.  Synchronizes the stream. */
+int hg_gain_table(hg_t* h, int32_t level, int32_t k, const int32_t* part, int64_t* benefit,
+                  int64_t* penalty);
+
+/* Moves move_nodes[i] to move_targets[i] for all i at once (every node at
+ * most once, each target in [0, k) and not the node's block), updating
+ * `part` in place and the gain table (benefit, penalty: the table of `part`
+ * on entry, as hg_gain_table writes it) with the update rules of Sec. 6.2
+ * applied concurrently; afterwards the benefits of the moved nodes are
+ * recomputed (Sec. 6.2, "Benefit Peculiarities"), so the table equals
+ * hg_gain_table of the new partition.  Same arguments and errors as
+ * hg_gain_table plus those of hg_recalculate_gains for the moves (nothing
+ * is changed when the moves are bad).  Synchronizes the stream. */
+int hg_gain_table_move(hg_t* h, int32_t level, int32_t k, int32_t* part, int32_t num_moves,
+                       const int32_t* move_nodes, const int32_t* move_targets, int64_t* benefit,
+                       int64_t* penalty);
+
 /* The objective f_{lambda-1} (Sec. 2) and the block weights c(V_i) of a
  * partition, for a hypergraph held by the caller in device memory, with no
  * handle and without allocating device memory.  The paper has no

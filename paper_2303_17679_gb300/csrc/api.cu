@@ -342,6 +342,7 @@ int hg_lp_refine(hg_t* h, int32_t level, int32_t k, int32_t eps_ppm, int32_t max
   return guarded(h, [&]() -> int {
     hgk::RefineCounters rc;
     const Level& L = *h->levels[level];
+    hgk::validate_partition(h->cx, part, L.n, k);
     hgk::LPResult r = hgk::lp_refine_level(h->cx, L, level, k, eps_ppm, max_passes,
                                            h->opt.subrounds, h->opt.seed, h->W0,
                                            h->opt.lp_block_min_deg ? h->opt.lp_block_min_deg : 64,
@@ -367,6 +368,7 @@ int hg_objective(hg_t* h, int32_t level, int32_t k, const int32_t* part, int64_t
   if (k < 1 || k > HG_MAX_K) return HG_ERR_INVALID;
   if (!valid_level(h, level)) return HG_ERR_STATE;
   return guarded(h, [&]() -> int {
+    hgk::validate_partition(h->cx, part, h->levels[level]->n, k);
     hgk::EventTimer tm(h->cx, &h->stats.ms_objective);
     *out = hgk::objective_of(h->cx, *h->levels[level], k, part);
     sync_stats(h);
@@ -390,12 +392,41 @@ int hg_recalculate_gains(hg_t* h, int32_t level, int32_t k, const int32_t* part,
   });
 }
 
+int hg_gain_table(hg_t* h, int32_t level, int32_t k, const int32_t* part, int64_t* benefit,
+                  int64_t* penalty) {
+  if (!h || !part || !benefit || !penalty) return HG_ERR_INVALID;
+  if (k < 2 || k > HG_MAX_K) return HG_ERR_INVALID;
+  if (!valid_level(h, level)) return HG_ERR_STATE;
+  return guarded(h, [&]() -> int {
+    hgk::gain_table_build(h->cx, *h->levels[level], k, part, benefit, penalty);
+    sync_stats(h);
+    return HG_OK;
+  });
+}
+
+int hg_gain_table_move(hg_t* h, int32_t level, int32_t k, int32_t* part, int32_t num_moves,
+                       const int32_t* move_nodes, const int32_t* move_targets, int64_t* benefit,
+                       int64_t* penalty) {
+  if (!h || !part || !benefit || !penalty || num_moves < 0) return HG_ERR_INVALID;
+  if (k < 2 || k > HG_MAX_K) return HG_ERR_INVALID;
+  if (num_moves > 0 && (!move_nodes || !move_targets)) return HG_ERR_INVALID;
+  if (!valid_level(h, level)) return HG_ERR_STATE;
+  if (num_moves > h->levels[level]->n) return HG_ERR_INVALID;
+  return guarded(h, [&]() -> int {
+    hgk::gain_table_move(h->cx, *h->levels[level], k, part, num_moves, move_nodes, move_targets,
+                         benefit, penalty);
+    sync_stats(h);
+    return HG_OK;
+  });
+}
+
 int hg_pin_counts(hg_t* h, int32_t level, int32_t k, const int32_t* part, int32_t* phi,
                   uint64_t* lambda, int64_t* block_weights) {
   if (!h || !part) return HG_ERR_INVALID;
   if (k < 1 || k > HG_MAX_K) return HG_ERR_INVALID;
   if (!valid_level(h, level)) return HG_ERR_STATE;
   return guarded(h, [&]() -> int {
+    hgk::validate_partition(h->cx, part, h->levels[level]->n, k);
     hgk::pin_counts_of(h->cx, *h->levels[level], k, part, phi, lambda, block_weights);
     return HG_OK;
   });

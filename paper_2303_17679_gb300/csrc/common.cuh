@@ -336,6 +336,16 @@ int64_t objective_of(const Ctx& cx, const Level& L, int k, const int32_t* part);
 
 void pin_counts_of(const Ctx& cx, const Level& L, int k, const int32_t* part, int32_t* phi,
                    uint64_t* lambda, int64_t* bw);
+// Throws HG_ERR_INVALID unless every block id of a caller's partition is in
+// [0, k) (a block id indexes Phi).
+void validate_partition(const Ctx& cx, const int32_t* part, int32_t n, int k);
+// Phi (m x k) and Lambda of a partition, left on the device.
+void device_pin_counts(const Ctx& cx, const Level& L, int k, const int32_t* part,
+                       DBuf<int32_t>& phi, DBuf<unsigned long long>& lam);
+void gain_table_build(const Ctx& cx, const Level& L, int k, const int32_t* part, int64_t* b,
+                      int64_t* p);
+void gain_table_move(const Ctx& cx, const Level& L, int k, int32_t* part, int32_t l,
+                     const int32_t* nodes, const int32_t* targets, int64_t* b, int64_t* p);
 
 struct LPResult {
   int64_t objective = 0;

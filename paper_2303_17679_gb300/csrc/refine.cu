@@ -670,6 +670,32 @@ int64_t objective_of(const Ctx& cx, const Level& L, int k, const int32_t* part) 
   return objective_from_lambda(cx, L, st.lam.p);
 }
 
+namespace {
+
+__global__ void k_check_part(const int32_t* __restrict__ part, int32_t n, int k, int32_t* status) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x)
+    if (part[u] < 0 || part[u] >= k) dev_fail(status, DEV_BAD_INPUT);
+}
+
+}  // namespace
+
+void validate_partition(const Ctx& cx, const int32_t* part, int32_t n, int k) {
+  if (n <= 0) return;
+  k_check_part<<<grid_for(n, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(part, n, k, cx.d_status);
+  check_launch("check_part");
+  if (cx.launches) *cx.launches += 1;
+  check_status(cx);
+}
+
+void device_pin_counts(const Ctx& cx, const Level& L, int k, const int32_t* part,
+                       DBuf<int32_t>& phi, DBuf<unsigned long long>& lam) {
+  PinState st;
+  build_pin_state(cx, L, k, part, st);
+  phi = std::move(st.phi);
+  lam = std::move(st.lam);
+}
+
 void pin_counts_of(const Ctx& cx, const Level& L, int k, const int32_t* part, int32_t* phi,
                    uint64_t* lambda, int64_t* bw) {
   PinState st;

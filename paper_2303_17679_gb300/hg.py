@@ -131,6 +131,8 @@ def load(path: str | None = None):
             "hg_objective": (ctypes.c_int, [H, i32, i32, vp, P(i64)]),
             "hg_pin_counts": (ctypes.c_int, [H, i32, i32, vp, vp, vp, vp]),
             "hg_recalculate_gains": (ctypes.c_int, [H, i32, i32, vp, i32, vp, vp, vp]),
+            "hg_gain_table": (ctypes.c_int, [H, i32, i32, vp, vp, vp]),
+            "hg_gain_table_move": (ctypes.c_int, [H, i32, i32, vp, i32, vp, vp, vp, vp]),
             "hg_objective_noalloc": (ctypes.c_int, [i32, i32, i64, vp, vp, vp, vp, i32, vp, vp,
                                                     P(i64), vp]),
             "hg_partition": (ctypes.c_int, [H, i32, i32, i32, vp, P(i64)]),
@@ -162,7 +164,8 @@ def exported_symbols():
     """Names of the C entry points this binding expects the library to export."""
     return ["hg_default_options", "hg_create", "hg_coarsen_level", "hg_num_levels",
             "hg_level_info", "hg_initial_partition", "hg_project", "hg_lp_refine",
-            "hg_objective", "hg_pin_counts", "hg_recalculate_gains", "hg_objective_noalloc", "hg_partition", "hg_get_level", "hg_get_incidence",
+            "hg_objective", "hg_pin_counts", "hg_recalculate_gains", "hg_gain_table", "hg_gain_table_move",
+            "hg_objective_noalloc", "hg_partition", "hg_get_level", "hg_get_incidence",
             "hg_truncate", "hg_enable_timing", "hg_get_stats", "hg_reset_stats", "hg_destroy",
             "hg_exec_create", "hg_exec_submit", "hg_exec_wait", "hg_exec_pending",
             "hg_exec_now_ns", "hg_exec_destroy", "hg_strerror", "hg_version"]
@@ -304,6 +307,19 @@ def hg_recalculate_gains(h, level, k, part, move_nodes, move_targets, gains):
     _check(load().hg_recalculate_gains(h, int(level), int(k), _ptr(part), int(len(move_nodes)),
                                        _ptr(move_nodes), _ptr(move_targets), _ptr(gains)),
            "hg_recalculate_gains")
+
+
+def hg_gain_table(h, level, k, part, benefit, penalty):
+    """Device tensors: benefit int64 [n], penalty int64 [n, k] are written."""
+    _check(load().hg_gain_table(h, int(level), int(k), _ptr(part), _ptr(benefit), _ptr(penalty)),
+           "hg_gain_table")
+
+
+def hg_gain_table_move(h, level, k, part, move_nodes, move_targets, benefit, penalty):
+    """Device tensors; part, benefit and penalty are updated in place."""
+    _check(load().hg_gain_table_move(h, int(level), int(k), _ptr(part), int(len(move_nodes)),
+                                     _ptr(move_nodes), _ptr(move_targets), _ptr(benefit),
+                                     _ptr(penalty)), "hg_gain_table_move")
 
 
 def hg_objective_noalloc(n, m, p, net_offsets, pins, net_weights, node_weights, k, part,

@@ -324,3 +324,58 @@ def test_gain_recalculation_rejects_bad_sequences():
         hg.hg_recalculate_gains(h, 0, 4, part, dev([1, 2]), dev([1, 3]), gains)
     finally:
         hg.hg_destroy(h)
+
+
+# ------------------------------------------------------ gain table (Sec. 6.2)
+
+@pytest.mark.parametrize("name,k,frac", [("zipf20k", 8, 0.2), ("stress", 64, 0.1),
+                                         ("weighted", 3, 1.0), ("cfg1", 2, 0.5)])
+def test_gain_table_build_and_moves(oracle_mod, name, k, frac):
+    hgr = medium_cases()[name]
+    h = create(hgr, make_opt())
+    try:
+        rng = np.random.default_rng(k + 5)
+        part = rng.integers(0, k, size=hgr.n).astype(np.int32)
+        dpart = dev(part)
+        b = torch.zeros(hgr.n, dtype=torch.int64, device="cuda")
+        p = torch.zeros((hgr.n, k), dtype=torch.int64, device="cuda")
+        hg.hg_gain_table(h, 0, k, dpart, b, p)
+        wb, wp = oracle_mod.gain_table(hgr, k, part)
+        assert np.array_equal(b.cpu().numpy(), wb) and np.array_equal(p.cpu().numpy(), wp)
+        # a set of moves applied at once with the update rules, then the moved
+        # nodes' benefits recomputed: the table of the new partition
+        nodes, targets = random_moves(rng, part, k, max(1, int(frac * hgr.n)))
+        hg.hg_gain_table_move(h, 0, k, dpart, dev(nodes), dev(targets), b, p)
+        moved = part.copy()
+        moved[nodes] = targets
+        assert np.array_equal(dpart.cpu().numpy(), moved)
+        wb2, wp2 = oracle_mod.gain_table(hgr, k, moved)
+        assert np.array_equal(b.cpu().numpy(), wb2)
+        assert np.array_equal(p.cpu().numpy(), wp2)
+    finally:
+        hg.hg_destroy(h)
+
+
+def test_gain_table_and_objective_reject_bad_block_ids():
+    hgr = medium_cases()["cfg1"]
+    h = create(hgr, make_opt())
+    try:
+        part = np.zeros(hgr.n, np.int32)
+        part[7] = 4  # k = 4: out of range
+        dpart = dev(part)
+        b = torch.zeros(hgr.n, dtype=torch.int64, device="cuda")
+        p = torch.zeros((hgr.n, 4), dtype=torch.int64, device="cuda")
+        for call in (lambda: hg.hg_gain_table(h, 0, 4, dpart, b, p),
+                     lambda: hg.hg_objective(h, 0, 4, dpart),
+                     lambda: hg.hg_pin_counts(h, 0, 4, dpart)):
+            with pytest.raises(hg.HgError) as ei:
+                call()
+            assert ei.value.status == hg.HG_ERR_INVALID
+        good = dev(np.zeros(hgr.n, np.int32))
+        before = good.clone()
+        with pytest.raises(hg.HgError):  # node 3 twice: nothing changes
+            hg.hg_gain_table_move(h, 0, 4, good, dev([3, 3]), dev([1, 2]), b, p)
+        assert torch.equal(good, before)
+        assert hg.hg_objective(h, 0, 4, good) == 0
+    finally:
+        hg.hg_destroy(h)
