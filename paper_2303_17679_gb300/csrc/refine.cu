@@ -169,6 +169,8 @@ struct GainPart {
   long long acc0, acc1, ben, wsum;
 };
 
+constexpr int GAIN_REDUCE_K = 16;
+
 __device__ __forceinline__ GainPart gain_partial(const int32_t* __restrict__ inets,
                                                  const int32_t* __restrict__ w,
                                                  const int32_t* __restrict__ phi,
@@ -179,12 +181,23 @@ __device__ __forceinline__ GainPart gain_partial(const int32_t* __restrict__ ine
   GainPart g{0, 0, 0, 0};
   for (int32_t c0 = beg + 32 * first; c0 < end; c0 += 32 * stride) {
     const int32_t j = c0 + lane;
+    int32_t we = 0;
+    unsigned long long le = 0;
     if (j < end) {
       const int32_t e = inets[j];
-      const int32_t we = w[e];
-      unsigned long long le = lam[e];
+      we = w[e];
+      le = lam[e];
       if (phi[(int64_t)e * k + from] == 1) g.ben += we;
       g.wsum += we;
+    }
+    if (k <= GAIN_REDUCE_K) {
+      // small k: one warp reduction per block instead of atomics, which on
+      // coarse levels (many blocks per net) would all hit the same k counters
+      for (int t = 0; t < k; ++t) {
+        const unsigned x = __reduce_add_sync(FULL, ((le >> t) & 1ull) ? (unsigned)we : 0u);
+        if (lane == t) g.acc0 += x;
+      }
+    } else {
       while (le) {
         atomicAdd(&s_cnt[__ffsll((long long)le) - 1], we);
         le &= le - 1;
@@ -194,8 +207,10 @@ __device__ __forceinline__ GainPart gain_partial(const int32_t* __restrict__ ine
   return g;
 }
 
-// Moves the warp's block counters into acc0 / acc1 and clears them.
-__device__ __forceinline__ void gain_collect(GainPart& g, int32_t* s_cnt) {
+// Moves the warp's block counters into acc0 / acc1 and clears them (k above
+// GAIN_REDUCE_K; for smaller k the counts are in acc0 already).
+__device__ __forceinline__ void gain_collect(GainPart& g, int32_t* s_cnt, int k) {
+  if (k <= GAIN_REDUCE_K) return;
   const int lane = lane_id();
   __syncwarp();
   g.acc0 = s_cnt[lane];
@@ -279,7 +294,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_lp_gain_warp(GainArgs A) {
     const int from = A.part[u];
     const int32_t beg = A.ioff[u], end = A.ioff[u + 1];
     GainPart g = gain_partial(A.inets, A.w, A.phi, A.lam, A.k, from, beg, end, 0, 1, cnt);
-    gain_collect(g, cnt);
+    gain_collect(g, cnt, A.k);
     long long bg;
     int bt;
     gain_best(g, A.k, from, bg, bt);
@@ -310,7 +325,7 @@ __global__ void __launch_bounds__(GAIN_BLOCK_WARPS * 32) k_lp_gain_block(GainArg
     const int from = A.part[u];
     const int32_t beg = A.ioff[u], end = A.ioff[u + 1];
     GainPart g = gain_partial(A.inets, A.w, A.phi, A.lam, A.k, from, beg, end, wv, WARPS, cnt);
-    gain_collect(g, cnt);
+    gain_collect(g, cnt, A.k);
     s_acc[wv][lane] = g.acc0;
     s_acc[wv][lane + 32] = g.acc1;
     const long long b = warp_sum(g.ben), ws = warp_sum(g.wsum);
