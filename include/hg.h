@@ -96,6 +96,11 @@ typedef struct {
   int32_t rate_quad_max_d;
   int32_t rate_block_max_d;
   int32_t lp_block_min_deg;
+  /* 1: wait for the device by sleeping on a blocking-sync event instead of
+   * spinning (frees the host core while waiting, at a few microseconds of
+   * wake-up latency per wait; the executor sets it for its jobs).  0 (default):
+   * spin. */
+  int32_t blocking_sync;
 } hg_options;
 
 /* Per-phase device time (milliseconds, from CUDA events) and work counters,

@@ -146,7 +146,7 @@ int hg_create(int32_t n, int32_t m, const int32_t* net_offsets, const int32_t* p
   if (o.rate_warp_max_d < 0 || o.rate_warp_max_d > 256 || o.rate_pair_max_d < 0 ||
       o.rate_pair_max_d > 1024 || o.rate_quad_max_d < 0 || o.rate_quad_max_d > 2048 ||
       o.rate_block_max_d < 0 || o.rate_block_max_d > 4096 || o.lp_block_min_deg < 0 ||
-      o.lp_block_min_deg > (1 << 20))
+      o.lp_block_min_deg > (1 << 20) || o.blocking_sync < 0 || o.blocking_sync > 1)
     return HG_ERR_INVALID;
   int64_t W = 0;
   int64_t p = 0;
@@ -165,6 +165,9 @@ int hg_create(int32_t n, int32_t m, const int32_t* net_offsets, const int32_t* p
     HG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
     h->cx.num_sms = sms;
     h->cx.stream = static_cast<cudaStream_t>(cuda_stream);
+    if (o.blocking_sync)
+      HG_CUDA(cudaEventCreateWithFlags(&h->cx.sync_event,
+                                       cudaEventBlockingSync | cudaEventDisableTiming));
     h->cx.alloc.fn_alloc = o.dev_alloc;
     h->cx.alloc.fn_free = o.dev_free;
     h->cx.alloc.ctx = o.alloc_ctx;
@@ -546,6 +549,7 @@ int hg_destroy(hg_t* h) {
   if (h->cx.d_status) h->cx.alloc.put(h->cx.d_status);
   h->cx.d_status = nullptr;
   cudaStreamSynchronize(h->cx.stream);
+  if (h->cx.sync_event) cudaEventDestroy(h->cx.sync_event);
   delete h;
   return HG_OK;
 }

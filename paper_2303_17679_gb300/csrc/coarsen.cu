@@ -1473,6 +1473,7 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   if (cx.launches) *cx.launches += 5;
 
   std::vector<int32_t> hcount(nkeys);
+  wait_stream(cx);
   HG_CUDA(cudaMemcpyAsync(hcount.data(), kcount.p, sizeof(int32_t) * nkeys, cudaMemcpyDeviceToHost,
                           cx.stream));
   check_status(cx);
@@ -1518,6 +1519,7 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
     check_launch("widen");
     std::vector<int32_t> hio((size_t)nsplit + 1), hso((size_t)nsplit + 1);
     std::vector<int64_t> hto((size_t)nsplit + 1);
+    wait_stream(cx);
     HG_CUDA(cudaMemcpyAsync(hio.data(), sp.item_off.p, sizeof(int32_t) * hio.size(),
                             cudaMemcpyDeviceToHost, cx.stream));
     HG_CUDA(cudaMemcpyAsync(hso.data(), sp.part_off.p, sizeof(int32_t) * hso.size(),
@@ -1679,6 +1681,7 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   HG_CUDA(cudaMemcpy2DAsync(cw_out.p, sizeof(int32_t), cst.p, sizeof(int2), sizeof(int32_t),
                             (size_t)n, cudaMemcpyDeviceToDevice, cx.stream));
   unsigned long long hs[ST_WORDS * NCLASS];
+  wait_stream(cx);
   HG_CUDA(cudaMemcpyAsync(hs, stats.p, sizeof(hs), cudaMemcpyDeviceToHost, cx.stream));
   check_status(cx);
   for (int c = 0; c < NCLASS; ++c) {

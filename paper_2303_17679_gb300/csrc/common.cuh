@@ -217,6 +217,7 @@ struct Ctx {
   int64_t* launches = nullptr;   // host counter
   bool timing = false;           // per-phase event timing (synchronizes at phase ends)
   bool kernel_timing = false;    // event pair around every rating / gain launch (no sync)
+  cudaEvent_t sync_event = nullptr;  // blocking-sync event: waits sleep instead of spinning
 };
 
 // Grid size helper: enough blocks for `work` items of `per_block` each,
@@ -270,6 +271,10 @@ int64_t read_i64(const Ctx& cx, const int64_t* d);
 void check_status(const Ctx& cx);
 
 void fill_i32(const Ctx& cx, int32_t* p, int32_t value, int64_t n);
+// Waits until the stream's work is done: spinning, or sleeping on the
+// handle's blocking-sync event when it has one.  A following copy to pageable
+// host memory then finds the stream idle.
+void wait_stream(const Ctx& cx);
 void iota_i32(const Ctx& cx, int32_t* p, int64_t n);
 
 // ---------------------------------------------------- structure (structure.cu)

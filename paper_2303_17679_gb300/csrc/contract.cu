@@ -376,6 +376,7 @@ void contract_level(const Ctx& cx, Level& L, const int32_t* cw, Level& out, int 
   k_classify_nets<<<gm, 256, 0, cx.stream>>>(L.eoff.p, m, lists.p, counts.p);
   check_launch("classify_nets");
   int32_t hc[4];
+  wait_stream(cx);
   HG_CUDA(cudaMemcpyAsync(hc, counts.p, sizeof(hc), cudaMemcpyDeviceToHost, cx.stream));
   check_status(cx);
   if (hc[0])
@@ -454,6 +455,7 @@ void contract_level(const Ctx& cx, Level& L, const int32_t* cw, Level& out, int 
   scan_exclusive_i32(cx, kflag.p, newid.p, m, d_tot.p);      // keep flag -> new id
   scan_exclusive_i32(cx, ksize.p, ksize.p, m, d_tot.p + 1);  // kept size -> coarse offset
   int32_t tot[2];
+  wait_stream(cx);
   HG_CUDA(cudaMemcpyAsync(tot, d_tot.p, sizeof(tot), cudaMemcpyDeviceToHost, cx.stream));
   check_status(cx);
   out.m = tot[0];

@@ -60,7 +60,8 @@ struct hg_exec_t {
 
 namespace {
 
-void run_job(hg_exec_t* ex, cudaStream_t st, const Pending& pj, hg_job_result& r) {
+void run_job(hg_exec_t* ex, cudaStream_t st, cudaEvent_t waiter, const Pending& pj,
+             hg_job_result& r) {
   const hg_job& j = pj.job;
   hg_t* h = nullptr;
   int rc = hg_create(j.n, j.m, j.net_offsets, j.pins, j.net_weights, j.node_weights, HG_MEM_HOST,
@@ -76,6 +77,7 @@ void run_job(hg_exec_t* ex, cudaStream_t st, const Pending& pj, hg_job_result& r
                                      cudaMemcpyDeviceToHost, st) != cudaSuccess)
     rc = HG_ERR_CUDA;
   if (dpart) cudaFreeAsync(dpart, st);
+  if (waiter && cudaEventRecord(waiter, st) == cudaSuccess) cudaEventSynchronize(waiter);
   if (cudaStreamSynchronize(st) != cudaSuccess && rc == HG_OK) rc = HG_ERR_CUDA;
   int32_t levels = 0;
   int64_t pins = 0;
@@ -96,6 +98,10 @@ void slot_main(hg_exec_t* ex) {
   cudaSetDevice(ex->device);
   cudaStream_t st = nullptr;
   const bool have_stream = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+  cudaEvent_t waiter = nullptr;
+  if (cudaEventCreateWithFlags(&waiter, cudaEventBlockingSync | cudaEventDisableTiming) !=
+      cudaSuccess)
+    waiter = nullptr;
   while (true) {
     Pending pj;
     {
@@ -117,7 +123,7 @@ void slot_main(hg_exec_t* ex) {
     r.est_bytes = pj.est;
     r.t_submit_ns = pj.t_submit;
     r.t_start_ns = now_ns();
-    if (have_stream) run_job(ex, st, pj, r);
+    if (have_stream) run_job(ex, st, waiter, pj, r);
     else r.status = HG_ERR_CUDA;
     r.t_end_ns = now_ns();
     {
@@ -129,6 +135,7 @@ void slot_main(hg_exec_t* ex) {
     ex->cv_done.notify_all();
     ex->cv_work.notify_all();
   }
+  if (waiter) cudaEventDestroy(waiter);
   if (have_stream) cudaStreamDestroy(st);
 }
 
@@ -145,6 +152,7 @@ int hg_exec_create(int32_t slots, int64_t mem_budget_bytes, const hg_options* op
   if (!ex) return HG_ERR_OOM;
   if (opt) ex->opt = *opt;
   else hg_default_options(&ex->opt);
+  ex->opt.blocking_sync = 1;  // slot threads sleep while their jobs run
   if (cudaGetDevice(&ex->device) != cudaSuccess) {
     delete ex;
     return HG_ERR_CUDA;

@@ -172,7 +172,17 @@ void iota_i32(const Ctx& cx, int32_t* p, int64_t n) {
   if (cx.launches) *cx.launches += 1;
 }
 
+void wait_stream(const Ctx& cx) {
+  if (cx.sync_event) {
+    HG_CUDA(cudaEventRecord(cx.sync_event, cx.stream));
+    HG_CUDA(cudaEventSynchronize(cx.sync_event));
+  } else {
+    HG_CUDA(cudaStreamSynchronize(cx.stream));
+  }
+}
+
 void check_status(const Ctx& cx) {
+  wait_stream(cx);
   int32_t st = 0;
   HG_CUDA(cudaMemcpyAsync(&st, cx.d_status, sizeof(st), cudaMemcpyDeviceToHost, cx.stream));
   HG_CUDA(cudaStreamSynchronize(cx.stream));
@@ -190,6 +200,7 @@ void check_status(const Ctx& cx) {
 
 int32_t read_i32(const Ctx& cx, const int32_t* d) {
   int32_t v = 0;
+  wait_stream(cx);
   HG_CUDA(cudaMemcpyAsync(&v, d, sizeof(v), cudaMemcpyDeviceToHost, cx.stream));
   check_status(cx);
   return v;
@@ -197,6 +208,7 @@ int32_t read_i32(const Ctx& cx, const int32_t* d) {
 
 int64_t read_i64(const Ctx& cx, const int64_t* d) {
   int64_t v = 0;
+  wait_stream(cx);
   HG_CUDA(cudaMemcpyAsync(&v, d, sizeof(v), cudaMemcpyDeviceToHost, cx.stream));
   check_status(cx);
   return v;

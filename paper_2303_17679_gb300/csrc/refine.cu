@@ -948,8 +948,9 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
     else enqueue_pass(true, cx.stream);
     if (cx.launches) *cx.launches += per_pass_launches;
     unsigned long long hc[2];
+    wait_stream(cx);  // the pass is done, so the graph is idle before its next update
     HG_CUDA(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, cx.stream));
-    check_status(cx);  // also waits for the pass, so the graph is idle before its next update
+    check_status(cx);
     res.passes = pass + 1;
     res.moves += (int64_t)hc[0];
     rc.lp_incidences += (int64_t)hc[1];

@@ -48,6 +48,7 @@ class hg_options(ctypes.Structure):
         ("rate_quad_max_d", ctypes.c_int32),
         ("rate_block_max_d", ctypes.c_int32),
         ("lp_block_min_deg", ctypes.c_int32),
+        ("blocking_sync", ctypes.c_int32),
     ]
 
     TUNABLE = ("rate_warp_max_d", "rate_pair_max_d", "rate_quad_max_d", "rate_block_max_d",
