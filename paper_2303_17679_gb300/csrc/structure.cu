@@ -86,6 +86,97 @@ __global__ void k_validate_nodes(const int32_t* __restrict__ c, int32_t n, int32
   if (lane_id() == 0 && local) atomicAdd(total_c, (unsigned long long)local);
 }
 
+// No node twice in a net.  One warp per net of at most DISTINCT_SMALL pins:
+// nets of at most 32 pins compare lanes with a match; larger ones insert
+// their pins into a per-warp hash set in shared memory (a pin found already
+// present is a repeat).  Larger nets are left to k_distinct_big.  Runs only
+// on offsets and pins already checked, so every read stays in bounds.
+constexpr int DISTINCT_WARPS = 4;
+constexpr int DISTINCT_SMALL = 1024;
+constexpr int DISTINCT_SET = 2 * DISTINCT_SMALL;
+
+__device__ __forceinline__ bool set_insert_new(int32_t* set, uint32_t mask, int32_t v) {
+  uint32_t h = ((uint32_t)v * 0x9E3779B1u) & mask;
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    const int32_t old = atomicCAS(&set[h], -1, v);
+    if (old == -1) return true;
+    if (old == v) return false;
+    h = (h + 1) & mask;
+  }
+  return false;  // full: cannot happen at load <= 1/2
+}
+
+// Removes v (probing past empty slots: other pins of the net are erased at
+// the same time and leave holes in the probe chains).
+__device__ __forceinline__ void set_erase(int32_t* set, uint32_t mask, int32_t v) {
+  uint32_t h = ((uint32_t)v * 0x9E3779B1u) & mask;
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    if (set[h] == v) {
+      set[h] = -1;
+      return;
+    }
+    h = (h + 1) & mask;
+  }
+}
+
+__global__ void __launch_bounds__(DISTINCT_WARPS * 32)
+k_distinct_small(const int32_t* __restrict__ eoff, const int32_t* __restrict__ pins, int32_t m,
+                 int32_t* status) {
+  __shared__ int32_t s_set[DISTINCT_WARPS][DISTINCT_SET];
+  const int wv = warp_in_block(), lane = lane_id();
+  int32_t* set = s_set[wv];
+  for (int i = lane; i < DISTINCT_SET; i += 32) set[i] = -1;
+  __syncwarp();
+  for (int64_t e = (int64_t)blockIdx.x * DISTINCT_WARPS + wv; e < m;
+       e += (int64_t)gridDim.x * DISTINCT_WARPS) {
+    const int32_t b = eoff[e], sz = eoff[e + 1] - b;
+    if (sz > DISTINCT_SMALL) continue;
+    bool dup = false;
+    if (sz <= 32) {
+      const int32_t v = lane < sz ? pins[b + lane] : -1 - lane;
+      dup = __popc(__match_any_sync(FULL, v)) > 1;
+    } else {
+      for (int32_t q = lane; q < sz; q += 32) dup |= !set_insert_new(set, DISTINCT_SET - 1, pins[b + q]);
+      __syncwarp();
+      for (int32_t q = lane; q < sz; q += 32) set_erase(set, DISTINCT_SET - 1, pins[b + q]);
+      __syncwarp();
+    }
+    if (__any_sync(FULL, dup) && lane == 0) dev_fail(status, DEV_BAD_INPUT);
+  }
+}
+
+// Nets above DISTINCT_SMALL pins: one block per net with a hash set of `cap`
+// slots (a power of two >= twice the largest net) in this block's region of
+// `scratch` (all slots -1 on entry, restored before the block moves on).
+__global__ void k_distinct_big(const int32_t* __restrict__ eoff, const int32_t* __restrict__ pins,
+                               int32_t m, int32_t* __restrict__ scratch, uint32_t cap,
+                               int32_t* status) {
+  int32_t* set = scratch + (size_t)blockIdx.x * cap;
+  __shared__ int s_dup;
+  for (int64_t e = blockIdx.x; e < m; e += gridDim.x) {
+    const int32_t b = eoff[e], sz = eoff[e + 1] - b;
+    if (sz <= DISTINCT_SMALL) continue;
+    if (threadIdx.x == 0) s_dup = 0;
+    __syncthreads();
+    bool dup = false;
+    for (int32_t q = threadIdx.x; q < sz; q += blockDim.x) dup |= !set_insert_new(set, cap - 1, pins[b + q]);
+    if (dup) s_dup = 1;
+    __syncthreads();
+    for (int32_t q = threadIdx.x; q < sz; q += blockDim.x) set_erase(set, cap - 1, pins[b + q]);
+    if (threadIdx.x == 0 && s_dup) dev_fail(status, DEV_BAD_INPUT);
+    __syncthreads();
+  }
+}
+
+__global__ void k_max_net_size(const int32_t* __restrict__ eoff, int32_t m, int32_t* out) {
+  int32_t mx = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x)
+    mx = max(mx, eoff[e + 1] - eoff[e]);
+  mx = warp_max(mx);
+  if (lane_id() == 0 && mx) atomicMax(out, mx);
+}
+
 }  // namespace
 
 void build_tile_index(const Ctx& cx, const int32_t* eoff, int32_t m, int64_t p, int32_t* tile_net) {
@@ -149,6 +240,37 @@ bool validate_level_device(const Ctx& cx, const Level& L, int64_t* total_node_w,
     int32_t zero = 0;
     HG_CUDA(cudaMemcpy(cx.d_status, &zero, sizeof(zero), cudaMemcpyHostToDevice));
     return false;
+  }
+  // offsets and pins are sound: no node twice in a net
+  if (L.m > 0) {
+    DBuf<int32_t> mx;
+    mx.alloc(&cx.alloc, 1);
+    HG_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(int32_t), cx.stream));
+    k_max_net_size<<<grid_for(L.m, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(L.eoff.p, L.m, mx.p);
+    check_launch("max_net_size");
+    k_distinct_small<<<grid_for(L.m, DISTINCT_WARPS, cx.num_sms, 16), DISTINCT_WARPS * 32, 0,
+                       cx.stream>>>(L.eoff.p, L.pins.p, L.m, cx.d_status);
+    check_launch("distinct_small");
+    const int32_t biggest = read_i32(cx, mx.p);
+    if (biggest > DISTINCT_SMALL) {
+      uint32_t cap = 1;
+      while (cap < 2u * (uint32_t)biggest) cap <<= 1;
+      const int blocks = cx.num_sms;
+      DBuf<int32_t> scratch;
+      scratch.alloc(&cx.alloc, (size_t)blocks * cap);
+      HG_CUDA(cudaMemsetAsync(scratch.p, 0xff, scratch.bytes(), cx.stream));
+      k_distinct_big<<<blocks, 256, 0, cx.stream>>>(L.eoff.p, L.pins.p, L.m, scratch.p, cap,
+                                                    cx.d_status);
+      check_launch("distinct_big");
+    }
+    wait_stream(cx);
+    HG_CUDA(cudaMemcpyAsync(&st, cx.d_status, sizeof(st), cudaMemcpyDeviceToHost, cx.stream));
+    HG_CUDA(cudaStreamSynchronize(cx.stream));
+    if (st != DEV_OK) {
+      int32_t zero = 0;
+      HG_CUDA(cudaMemcpy(cx.d_status, &zero, sizeof(zero), cudaMemcpyHostToDevice));
+      return false;
+    }
   }
   *total_node_w = (int64_t)h[0];
   *total_net_w = (int64_t)h[1];

@@ -379,3 +379,26 @@ def test_gain_table_and_objective_reject_bad_block_ids():
         assert hg.hg_objective(h, 0, 4, good) == 0
     finally:
         hg.hg_destroy(h)
+
+
+def test_device_input_with_repeated_pins_rejected():
+    """hg_create on device arrays rejects a node repeated inside a net, for
+    small nets (warp match), mid-size nets (shared hash set) and nets above
+    1024 pins (global hash set); the valid versions are accepted."""
+    stream = torch.cuda.current_stream()
+    n = 5000
+    for size in (5, 300, 3000):
+        pins = np.arange(size, dtype=np.int32)
+        off = np.array([0, size, size + 2], np.int32)
+        good = np.concatenate([pins, [0, 1]]).astype(np.int32)
+        bad = good.copy()
+        bad[size - 1] = bad[size // 2]  # a repeat inside net 0
+        for arr, ok in ((good, True), (bad, False)):
+            args = (dev(off), dev(arr), dev(np.ones(2, np.int32)), dev(np.ones(n, np.int32)))
+            if ok:
+                h = hg.hg_create(n, 2, *args, hg.HG_MEM_DEVICE, make_opt(), stream)
+                hg.hg_destroy(h)
+            else:
+                with pytest.raises(hg.HgError) as ei:
+                    hg.hg_create(n, 2, *args, hg.HG_MEM_DEVICE, make_opt(), stream)
+                assert ei.value.status == hg.HG_ERR_INVALID
