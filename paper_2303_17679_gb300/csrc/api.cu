@@ -6,6 +6,7 @@
 #include <cstring>
 #include <memory>
 #include <numeric>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -50,21 +51,57 @@ bool valid_level(const hg_t* h, int32_t level) {
   return level >= 0 && level < (int32_t)h->levels.size();
 }
 
-// Host-side checks of a host CSR (hg_create contract).
+// Pins of nets [e0, e1) in [0, n) and no node twice in a net: nets of up to
+// 16 pins compare their pins pairwise, larger nets stamp their nodes in
+// `stamp` (n entries, allocated on first use).
+bool check_pins_range(int32_t n, const int32_t* off, const int32_t* pins, int32_t e0, int32_t e1,
+                      std::vector<int32_t>& stamp) {
+  for (int32_t e = e0; e < e1; ++e) {
+    const int32_t b = off[e], sz = off[e + 1] - b;
+    for (int32_t q = b; q < b + sz; ++q)
+      if (pins[q] < 0 || pins[q] >= n) return false;
+    if (sz <= 16) {
+      for (int32_t i = 1; i < sz; ++i)
+        for (int32_t j = 0; j < i; ++j)
+          if (pins[b + i] == pins[b + j]) return false;
+    } else {
+      if (stamp.empty()) stamp.assign((size_t)n, -1);
+      for (int32_t q = b; q < b + sz; ++q) {
+        if (stamp[pins[q]] == e) return false;
+        stamp[pins[q]] = e;
+      }
+    }
+  }
+  return true;
+}
+
+// Host-side checks of a host CSR (hg_create contract).  The pin checks run
+// on up to 8 host threads over ranges of nets.
 int check_host_csr(int32_t n, int32_t m, const int32_t* off, const int32_t* pins, const int32_t* w,
                    const int32_t* c, int64_t* W) {
   if (off[0] != 0) return HG_ERR_INVALID;
   for (int32_t e = 0; e < m; ++e)
     if (off[e + 1] <= off[e]) return HG_ERR_INVALID;  // decreasing or empty net
   const int64_t p = off[m];
-  std::vector<int32_t> stamp((size_t)n, -1);
-  for (int32_t e = 0; e < m; ++e)
-    for (int32_t q = off[e]; q < off[e + 1]; ++q) {
-      const int32_t v = pins[q];
-      if (v < 0 || v >= n) return HG_ERR_INVALID;
-      if (stamp[v] == e) return HG_ERR_INVALID;  // repeated pin
-      stamp[v] = e;
-    }
+  const int threads = (int)std::max<int64_t>(
+      1, std::min<int64_t>({8, (int64_t)std::thread::hardware_concurrency(), p / (1 << 20) + 1}));
+  std::vector<char> ok((size_t)threads, 1);
+  if (threads == 1) {
+    std::vector<int32_t> stamp;
+    ok[0] = check_pins_range(n, off, pins, 0, m, stamp);
+  } else {
+    std::vector<std::thread> pool;
+    for (int t = 0; t < threads; ++t)
+      pool.emplace_back([&, t] {
+        std::vector<int32_t> stamp;
+        const int32_t e0 = (int32_t)((int64_t)m * t / threads);
+        const int32_t e1 = (int32_t)((int64_t)m * (t + 1) / threads);
+        ok[t] = check_pins_range(n, off, pins, e0, e1, stamp);
+      });
+    for (auto& th : pool) th.join();
+  }
+  for (char x : ok)
+    if (!x) return HG_ERR_INVALID;
   int64_t sw = 0, sc = 0;
   if (w)
     for (int32_t e = 0; e < m; ++e) {
