@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(TW * 32 * TEAMS, 1024 / (TW * 32 * TEAMS)) k_r
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ VT s_rv[TEAMS][TW];
   __shared__ int32_t s_rc[TEAMS][TW];
-  __shared__ int32_t s_nused[TEAMS];
+  __shared__ int32_t s_nused[TEAMS][2];
   if (subround_stopped(A)) return;
   const int team = warp_in_block() / TW, wt = warp_in_block() % TW;
   const int tid = threadIdx.x % (TW * 32), nthr = TW * 32;
@@ -457,24 +457,29 @@ __global__ void __launch_bounds__(TW * 32 * TEAMS, 1024 / (TW * 32 * TEAMS)) k_r
   H tab = make_hash<H>(base, slots);
   int32_t* used = reinterpret_cast<int32_t*>(base + (size_t)slots * H::BYTES_PER_SLOT);
   for (uint32_t i = tid; i < slots; i += nthr) tab.init(i);
-  if (tid == 0) s_nused[team] = 0;
+  if (tid == 0) s_nused[team][0] = s_nused[team][1] = 0;
   team_sync<TW>(team);
   int64_t visits = 0, incid = 0, nodes = 0;
+  int it = 0;
   for (int32_t i = blockIdx.x * TEAMS + team; i < A.count; i += gridDim.x * TEAMS) {
     const int32_t u = A.list[i];
     if (A.cst[u].y < 0) continue;  // joined a cluster in an earlier sub-round
     const int32_t cu = A.c[u], beg = A.ioff[u], end = A.ioff[u + 1];
+    // the used-slot counter of this node; the other one is cleared for the
+    // next node once every thread has read this one
+    int32_t* nused = &s_nused[team][it & 1];
     int32_t run = 0;
     visits += rate_groups<VT>(A, u, cu, beg, end, 32, wt, TW, run,
                               each_visit<VT>([&](int32_t C, VT r) HG_INLINE {
                                 const int32_t sl = tab.add(C, r);
-                                if (sl >= 0) used[atomicAdd(&s_nused[team], 1)] = sl;
+                                if (sl >= 0) used[atomicAdd(nused, 1)] = sl;
                                 else if (sl == ADD_FULL) dev_fail(A.status_word, DEV_HASH_FULL);
                               }));
     team_sync<TW>(team);
     VT bv = 0;
     int32_t bc = -1;
-    const int32_t nu = s_nused[team];
+    const int32_t nu = *nused;
+    if (tid == 0) s_nused[team][(it + 1) & 1] = 0;
     for (int32_t x = tid; x < nu; x += nthr) {
       int32_t C;
       VT v;
@@ -488,16 +493,21 @@ __global__ void __launch_bounds__(TW * 32 * TEAMS, 1024 / (TW * 32 * TEAMS)) k_r
         s_rc[team][wt] = bc;
       }
       team_sync<TW>(team);
-      if (tid == 0)
-        for (int x = 1; x < TW; ++x) better(bv, bc, s_rv[team][x], s_rc[team][x]);
+      // the team's first warp combines and publishes while the others go on
+      // to the next node (the slots and results it reads are not written
+      // again before the next node's first barrier)
+      if (wt == 0) {
+        bv = lane_id() < TW ? s_rv[team][lane_id()] : (VT)0;
+        bc = lane_id() < TW ? s_rc[team][lane_id()] : -1;
+        warp_argmax(bv, bc);
+      }
+    } else {
+      __syncwarp();
     }
-    if (tid == 0) {
-      s_nused[team] = 0;
-      publish(A, u, bc);
-    }
-    team_sync<TW>(team);
+    if (tid == 0) publish(A, u, bc);
     incid += end - beg;
     ++nodes;
+    ++it;
   }
   if (lane_id() == 0 && visits) atomicAdd(&A.stats[ST_PINS], (unsigned long long)visits);
   if (tid == 0 && nodes) {
@@ -656,6 +666,15 @@ k_rate_split_acc(RateArgs A, const int32_t* __restrict__ split, const int32_t* _
 // otherwise each part leaves its best (rating, cluster) for the per-node
 // combine in k_rate_split_argmax.  All warps of the block walk the node's
 // groups of 32 nets, sharing the chunks in turn.
+// Capacity of a part block's list of inserted slots (32-bit ratings: every
+// slot; 64-bit: what fits beside the table, else the whole table is scanned).
+template <typename VT> struct PartUsed { static constexpr uint32_t CAP = 2048; };
+template <> struct PartUsed<uint32_t> { static constexpr uint32_t CAP = PART_SLOTS; };
+template <typename VT>
+constexpr size_t part_bytes() {
+  return (size_t)PART_SLOTS * HashOf<VT>::type::BYTES_PER_SLOT + (size_t)PartUsed<VT>::CAP * 4;
+}
+
 __device__ __forceinline__ int32_t part_of(int32_t C, int32_t P) {
   return (int32_t)(((uint64_t)((uint32_t)C * 0x85EBCA77u) * (uint32_t)P) >> 32);
 }
@@ -667,21 +686,30 @@ k_rate_part(RateArgs A, const int32_t* __restrict__ split, const int32_t* __rest
             VT* __restrict__ res_v, int32_t* __restrict__ res_c) {
   using H = typename HashOf<VT>::type;
   constexpr int NW = PART_THREADS / 32, TW = NW / PART_TEAMS;
+  constexpr uint32_t CAP = PartUsed<VT>::CAP;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ VT s_rv[NW];
   __shared__ int32_t s_rc[NW];
+  __shared__ int32_t s_nused[2];
   if (subround_stopped(A)) return;
   H tab = make_hash<H>(smem, PART_SLOTS);
+  int32_t* used = reinterpret_cast<int32_t*>(smem + (size_t)PART_SLOTS * H::BYTES_PER_SLOT);
   for (uint32_t x = threadIdx.x; x < PART_SLOTS; x += blockDim.x) tab.init(x);
+  if (threadIdx.x == 0) s_nused[0] = s_nused[1] = 0;
   __syncthreads();
   const int wv = warp_in_block(), team = wv / TW, wt = wv % TW;
   int64_t visits = 0, incid = 0, nodes = 0;
+  int it = 0;
   for (int32_t t = part_lo + blockIdx.x; t < part_hi; t += gridDim.x) {
     const int32_t i = part_node[t];
     const int32_t u = split[i];
     if (A.cst[u].y < 0) continue;  // joined a cluster in an earlier sub-round
     const int32_t P = part_off[i + 1] - part_off[i], k = t - part_off[i];
     const int32_t cu = A.c[u], beg = A.ioff[u], end = A.ioff[u + 1];
+    // slots inserted for this part (listed while they fit the list); the
+    // other counter is cleared for the next part once every thread has read
+    // this one
+    int32_t* nused = &s_nused[it & 1];
     auto visit = [&](const int32_t(&q)[RATE_ILP], const VT(&rr)[RATE_ILP]) HG_INLINE {
       int32_t C[RATE_ILP];
 #pragma unroll
@@ -696,7 +724,13 @@ k_rate_part(RateArgs A, const int32_t* __restrict__ split, const int32_t* __rest
 #pragma unroll
       for (int j = 0; j < RATE_ILP; ++j) {
         if (!own[j] || cs[j].y == A.s || (long long)cs[j].x + cu > (long long)A.c_max) continue;
-        if (tab.add(C[j], rr[j]) == ADD_FULL) dev_fail(A.status_word, DEV_HASH_FULL);
+        const int32_t sl = tab.add(C[j], rr[j]);
+        if (sl >= 0) {
+          const int32_t x = atomicAdd(nused, 1);
+          if (x < (int32_t)CAP) used[x] = sl;
+        } else if (sl == ADD_FULL) {
+          dev_fail(A.status_word, DEV_HASH_FULL);
+        }
       }
     };
     int32_t run = 0;
@@ -704,13 +738,24 @@ k_rate_part(RateArgs A, const int32_t* __restrict__ split, const int32_t* __rest
                                           visit);
     if (k == 0) visits += v;
     __syncthreads();
+    const int32_t nu = *nused;
+    if (threadIdx.x == 0) s_nused[(it + 1) & 1] = 0;
     VT bv = 0;
     int32_t bc = -1;
-    for (uint32_t x = threadIdx.x; x < PART_SLOTS; x += blockDim.x) {
-      int32_t C;
-      VT val;
-      tab.take(x, C, val);
-      better(bv, bc, val, C);
+    if (nu <= (int32_t)CAP) {
+      for (int32_t x = threadIdx.x; x < nu; x += blockDim.x) {
+        int32_t C;
+        VT val;
+        tab.take((uint32_t)used[x], C, val);
+        better(bv, bc, val, C);
+      }
+    } else {  // more insertions than the list holds: every slot
+      for (uint32_t x = threadIdx.x; x < PART_SLOTS; x += blockDim.x) {
+        int32_t C;
+        VT val;
+        tab.take(x, C, val);
+        better(bv, bc, val, C);
+      }
     }
     warp_argmax(bv, bc);
     if (lane_id() == 0) {
@@ -718,18 +763,25 @@ k_rate_part(RateArgs A, const int32_t* __restrict__ split, const int32_t* __rest
       s_rc[wv] = bc;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int x = 1; x < NW; ++x) better(bv, bc, s_rv[x], s_rc[x]);
-      if (P == 1) {
-        publish(A, u, bc);
-        ++nodes;
-      } else {
-        res_v[t] = bv;
-        res_c[t] = bc;
+    // warp 0 combines and publishes while the other warps start the next
+    // part (the table is clear, and s_rv / s_rc are written again only after
+    // the next part's first barrier)
+    if (wv == 0) {
+      bv = lane_id() < NW ? s_rv[lane_id()] : (VT)0;
+      bc = lane_id() < NW ? s_rc[lane_id()] : -1;
+      warp_argmax(bv, bc);
+      if (lane_id() == 0) {
+        if (P == 1) {
+          publish(A, u, bc);
+          ++nodes;
+        } else {
+          res_v[t] = bv;
+          res_c[t] = bc;
+        }
+        if (k == 0) incid += end - beg;
       }
-      if (k == 0) incid += end - beg;
     }
-    __syncthreads();
+    ++it;
   }
   if (lane_id() == 0 && visits) atomicAdd(&A.stats[ST_PINS], (unsigned long long)visits);
   if (threadIdx.x == 0 && (incid || nodes)) {
@@ -1293,7 +1345,7 @@ void set_rate_attrs_once() {
   allow_smem(k_rate_team<VT, 8, 4>);
   allow_smem(k_rate_dense<VT>);
   HG_CUDA(cudaFuncSetAttribute(k_rate_part<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(PART_SLOTS * HashOf<VT>::type::BYTES_PER_SLOT)));
+                               (int)part_bytes<VT>()));
 }
 
 // Attributes belong to the functions: set once per process, also when
@@ -1376,8 +1428,7 @@ void rate_subround(const Ctx& cx, RateArgs A, const std::vector<int32_t>& hoff, 
     }
     const int32_t parts = sp.part_hi[s] - sp.part_lo[s];
     if (parts > 0) {
-      using H = typename HashOf<VT>::type;
-      const size_t bytes = (size_t)PART_SLOTS * H::BYTES_PER_SLOT;
+      const size_t bytes = part_bytes<VT>();
       k_rate_part<VT><<<grid_for(parts, 1, cx.num_sms, 1), PART_THREADS, bytes, cx.stream>>>(
           A, sp.split, sp.part_node.p, sp.part_off.p, sp.part_lo[s], sp.part_hi[s],
           reinterpret_cast<VT*>(sp.res_v.p), sp.res_c.p);
