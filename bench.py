@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Benchmark: pins/s of the deterministic multilevel path (coarsen every
 level, initial partition, project + label propagation on every level) on
-the config-2 workload (n = m = 1e6, Zipf(2.2) net sizes in [2, 1024],
+the n = m = 1e6 Zipf workload (n = m = 1e6, Zipf(2.2) net sizes in [2, 1024],
 preferential pins, node and net weights in [1, 10], k = 8, eps = 0.03).
 
 One step = hg_create from the device-resident input CSR (incidence build)
@@ -26,19 +26,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "pins/s per coarsen+LP level on 1 GB300, batched vs plain; serve p50/p99 ms"
 K_BLOCKS, EPS_PPM, PASSES, SEED = 8, 30000, 5, 1
-WORKLOAD = ("config 2: n=m=1,000,000, Zipf(2.2) net sizes in [2,1024], preferential pins, "
+WORKLOAD = ("hypergraph n=m=1,000,000: Zipf(2.2) net sizes in [2,1024], preferential pins, "
             "node/net weights uniform in [1,10], k=8, eps=0.03, S=16, T=1000, f=160, "
             "5 LP passes per level, full V-cycle")
 L2_FLUSH_BYTES = 512 << 20
 
 # DRAM traffic of the rating kernels (k_rate_*), from one ncu capture of
-# every rating launch of the config-2 hierarchy (dram__bytes_read.sum +
+# every rating launch of the n = m = 1e6 Zipf hierarchy (dram__bytes_read.sum +
 # dram__bytes_write.sum, averaged per launch); see
-# profiles/rating_kernels_config2.md.  Reported only while the source the
+# profiles/rating_kernels_zipf1m.md.  Reported only while the source the
 # counters were taken from is unchanged.
 RATING_TRAFFIC = {
-    "source_sha256": "b55a45069c7a1db5c1554b6a77851b9bb642dfa584b46f4478c3e0486befdaba",
-    "bytes_per_launch": 20065077,
+    "source_sha256": "a287fb097f09f6ab0350291e81f9c9909269442bcf2dddbedc0c2c1a37287be7",
+    "bytes_per_launch": 20056204,
 }
 
 
@@ -148,18 +148,18 @@ ORACLE_SAMPLE_N = int(os.environ.get("BENCH_ORACLE_N", "200000"))
 
 def oracle_sample():
     """Times the CPU oracle (as it stands, one core) on a bounded sample of
-    the same workload shape: config 2 scaled to n = m = 200,000 (about ten
+    the same workload shape: the Zipf(2.2) hypergraph scaled to n = m = 200,000 (about ten
     seconds of single-threaded work)."""
     import oracle
     import synth
-    hgr = synth.config2(SEED, n=ORACLE_SAMPLE_N)
+    hgr = synth.zipf_1m(SEED, n=ORACLE_SAMPLE_N)
     t0 = time.perf_counter()
     vc = oracle.multilevel(hgr, K_BLOCKS, EPS_PPM, S=16, T=1000, factor=160, seed=SEED,
                            max_passes=PASSES)
     dt = time.perf_counter() - t0
     pins = sum(int(l.p) for l in vc.levels)
     return dict(value=pins / dt, seconds=dt, pins=pins, levels=len(vc.levels),
-                sample=f"config 2 scaled to n=m={ORACLE_SAMPLE_N:,} ({hgr.p} pins, "
+                sample=f"Zipf(2.2) hypergraph scaled to n=m={ORACLE_SAMPLE_N:,} ({hgr.p} pins, "
                        f"{len(vc.levels)} levels), full V-cycle, one process, single-threaded oracle")
 
 
@@ -205,11 +205,11 @@ def run_plain_job(hg, torch, stream, hgr, k):
 
 
 def run_batch(hg, torch, slots):
-    """Config 4: 512 seeded instances (n log-uniform in [1e3, 2e5]); the plain
+    """Batch of 512 seeded instances (n log-uniform in [1e3, 2e5]); the plain
     form runs them one call after another (host CSR in, partition out), the
     batched form through the executor's slots, largest first."""
     import synth
-    jobs = synth.config4(SEED)
+    jobs = synth.batch_instances(SEED)
     stream = torch.cuda.current_stream()
     for hgr, k in jobs[:8]:
         run_plain_job(hg, torch, stream, hgr, k)
@@ -236,8 +236,8 @@ def run_batch(hg, torch, slots):
     finally:
         ex.close()
     same = all(got[i]["status"] == 0 and got[i]["objective"] == plain[i][0] for i in range(len(jobs)))
-    return {"workload": "config 4: 512 instances, n log-uniform in [1e3, 2e5], m/n in [0.5, 3], "
-                        "config-1 net sizes, weights in [1, 10], k in {2,4,8,16,32}, host CSR in, "
+    return {"workload": "batch of 512 instances: n log-uniform in [1e3, 2e5], m/n in [0.5, 3], "
+                        "net sizes 2 + Geom(0.3) <= 64, weights in [1, 10], k in {2,4,8,16,32}, host CSR in, "
                         "partition out",
             "instances": len(jobs), "level_pins": pins, "slots": slots,
             "plain_s": t_plain, "batched_s": t_batch,
@@ -260,7 +260,7 @@ def serve_stream(hg, arrivals, slots, gen_workers=8):
     try:
         for i in range(min(lookahead, len(arrivals))):
             _, s, p, _ = arrivals[i]
-            futs[i] = pool.submit(synth.config5_request, s, p)
+            futs[i] = pool.submit(synth.poisson_request, s, p)
         t0_ns = hg.hg_exec_now_ns()
         done = 0
 
@@ -283,7 +283,7 @@ def serve_stream(hg, arrivals, slots, gen_workers=8):
             hgr = futs.pop(i).result()
             j = i + lookahead
             if j < len(arrivals):
-                futs[j] = pool.submit(synth.config5_request, arrivals[j][1], arrivals[j][2])
+                futs[j] = pool.submit(synth.poisson_request, arrivals[j][1], arrivals[j][2])
             ex.submit(hgr, k, EPS_PPM, PASSES, tag=i)
             if t_first is None:
                 t_first = t0_ns + int(t_arr * 1e9)
@@ -301,24 +301,24 @@ def serve_stream(hg, arrivals, slots, gen_workers=8):
 
 
 def run_serve(hg, seconds, slots):
-    """Config 5: Poisson(200/s) requests of 1e4..2e6 pins (log-uniform), Zipf
+    """Serving stream: Poisson(200/s) requests of 1e4..2e6 pins (log-uniform), Zipf
     net sizes, k in {2, 8, 32}; continuous batching over the executor's slots
     against the plain form (one request at a time, same arrivals)."""
     import synth
-    arrivals = synth.config5_arrivals(SEED, rate=200.0, duration=seconds)
+    arrivals = synth.poisson_arrivals(SEED, rate=200.0, duration=seconds)
     served, objs_s = serve_stream(hg, arrivals, slots)
     # the plain form cannot keep up with the offered load, so it runs the first
     # second of arrivals only (its queue, and latency, grow without bound)
     head = [a for a in arrivals if a[0] < 1.0]
     plain, objs_p = serve_stream(hg, head, 1)
-    return {"workload": f"config 5: Poisson 200 req/s for {seconds:g} s, 1e4..2e6 pins "
+    return {"workload": f"serving stream: Poisson 200 req/s for {seconds:g} s, 1e4..2e6 pins "
                         "log-uniform, Zipf(2.2) net sizes, k in {2, 8, 32}",
             "served": served, "plain_first_second": plain,
             "identical_objectives": all(objs_s[i] == objs_p[i] for i in objs_p)}
 
 
 def run_gain_recalc(hg, torch, hgr, d_off, d_pins, d_w, d_c, opt, stream, part, peak):
-    """Exact gains of a move sequence (Sec. 6.3) on config 2, level 0: a seeded
+    """Exact gains of a move sequence (Sec. 6.3) on the n = m = 1e6 Zipf hypergraph, level 0: a seeded
     sequence moving 10 % of the nodes (from the V-cycle's partition) to
     random other blocks.  Algorithmic bytes: 16 per move (node, target, index
     write and read), 8 per incidence of a moved node (net id, mark), 20 per
@@ -359,7 +359,7 @@ def run_gain_recalc(hg, torch, hgr, d_off, d_pins, d_w, d_c, opt, stream, part, 
     tpins = int(sizes[touched].sum())
     nbytes = 16 * len(nodes) + 8 * incid + 20 * tpins + 8 * int(touched.sum())
     t = statistics.median(ms) / 1e3
-    out = {"workload": "config 2 level 0, 100,000 seeded moves to random other blocks",
+    out = {"workload": "Zipf(2.2) n=m=1e6 hypergraph, level 0, 100,000 seeded moves to random other blocks",
            "moves": len(nodes), "touched_nets": int(touched.sum()), "touched_pins": tpins,
            "ms": t * 1e3, "moves_per_s": len(nodes) / t,
            "achieved_gbs": nbytes / t / 1e9, "frac_of_hbm": nbytes / t / 1e9 / peak}
@@ -404,18 +404,18 @@ def run_ours(args, world, rank, local):
     libbuild.build()
     hg.load()
     stream = torch.cuda.current_stream()
-    hgr = synth.config2(SEED)
+    hgr = synth.zipf_1m(SEED)
     opt = hg.hg_default_options()
     opt.seed = SEED
     # launch mapping chosen by paper_2303_17679_gb300.autotune for this workload
     # (results are identical under every mapping; only the speed differs)
-    tuned_path = os.path.join(ROOT, "paper_2303_17679_gb300", "tuned_config2_k8.json")
+    tuned_path = os.path.join(ROOT, "paper_2303_17679_gb300", "tuned_zipf1m_k8.json")
     mapping = "built-in defaults"
     if os.path.exists(tuned_path):
         from paper_2303_17679_gb300 import autotune
         with open(tuned_path) as f:
             autotune.apply(opt, json.load(f))
-        mapping = "autotuned (paper_2303_17679_gb300/tuned_config2_k8.json)"
+        mapping = "autotuned (paper_2303_17679_gb300/tuned_zipf1m_k8.json)"
     t_in = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).cuda()
     d_off, d_pins, d_w, d_c = t_in(hgr.offsets), t_in(hgr.pins), t_in(hgr.net_w), t_in(hgr.node_w)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory()
@@ -530,7 +530,7 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": "pins/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic (seeded generator, config 2 shape)",
+        "data": "synthetic (seeded generator: Zipf(2.2) net sizes, preferential pins, n=m=1e6)",
         "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "flushed between steps (512 MiB write outside the timed events)",
                    "launch_mapping": mapping,
@@ -586,9 +586,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end steps")
-    ap.add_argument("--no-batch", action="store_true", help="skip the config-4 batch comparison")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batch comparison")
     ap.add_argument("--serve-seconds", type=float, default=20.0,
-                    help="length of the config-5 serving run (0: skip; the config states 60)")
+                    help="length of the Poisson serving run (0: skip; the workload states 60)")
     ap.add_argument("--slots", type=int, default=16, help="executor slots for batch and serve")
     ap.add_argument("--phases", action="store_true",
                     help="add a per-phase breakdown from one extra, untimed step")

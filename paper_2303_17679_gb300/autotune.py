@@ -8,7 +8,7 @@ whose partition or objective differs from the default mapping's is an error
 (the mapping must never change results).  The fastest candidate is returned
 and can be saved as JSON and applied to hg_options.
 
-    python -m paper_2303_17679_gb300.autotune --workload config2 --k 8 --out tuned.json
+    python -m paper_2303_17679_gb300.autotune --workload zipf1m --k 8 --out tuned.json
 """
 from __future__ import annotations
 
@@ -97,15 +97,15 @@ def autotune(workload, k, cands=None, repeats=2, seed=1):
 def main():
     import synth
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="config2", choices=["config2", "config4"])
+    ap.add_argument("--workload", default="zipf1m", choices=["zipf1m", "batch"])
     ap.add_argument("--k", type=int, default=8)
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
-    if args.workload == "config2":
-        work, k = [synth.config2(1, n=args.n)], args.k
+    if args.workload == "zipf1m":
+        work, k = [synth.zipf_1m(1, n=args.n)], args.k
     else:
-        inst = synth.config4(1, count=16)
+        inst = synth.batch_instances(1, count=16)
         work, k = [g for g, kk in inst if kk == args.k] or [inst[0][0]], args.k
     r = autotune(work, k)
     print(json.dumps({"best": r["best"], "best_ms": r["best_ms"], "default_ms": r["default_ms"]}))

@@ -521,7 +521,7 @@ __global__ void __launch_bounds__(TW * 32 * TEAMS, 1024 / (TW * 32 * TEAMS)) k_r
 template <typename VT>
 __global__ void __launch_bounds__(256, 4) k_rate_dense(RateArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int32_t s_nused;
+  __shared__ int32_t s_nused[2];
   __shared__ VT s_rv[8];
   __shared__ int32_t s_rc[8];
   if (subround_stopped(A)) return;
@@ -529,26 +529,31 @@ __global__ void __launch_bounds__(256, 4) k_rate_dense(RateArgs A) {
   VT* val = reinterpret_cast<VT*>(smem);
   int32_t* used = reinterpret_cast<int32_t*>(val + cap);
   for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) val[i] = 0;
-  if (threadIdx.x == 0) s_nused = 0;
+  if (threadIdx.x == 0) s_nused[0] = s_nused[1] = 0;
   __syncthreads();
   const int nw = blockDim.x >> 5, wv = warp_in_block();
   int64_t visits = 0, incid = 0, nodes = 0;
+  int it = 0;
   for (int32_t i = blockIdx.x; i < A.count; i += gridDim.x) {
     const int32_t u = A.list[i];
     if (A.cst[u].y < 0) continue;
     const int32_t cu = A.c[u], beg = A.ioff[u], end = A.ioff[u + 1];
+    // touched-id counter of this node; the other one is cleared for the next
+    // node once every thread has read this one
+    int32_t* nused = &s_nused[it & 1];
     int32_t run = 0;
     visits += rate_groups<VT>(A, u, cu, beg, end, 32, wv, nw, run,
                               each_visit<VT>([&](int32_t C, VT r) HG_INLINE {
                                 // every term is >= 1, so a zero before the add
                                 // marks the first touch
                                 if (atomicAdd(&val[C], r) == (VT)0)
-                                  used[atomicAdd(&s_nused, 1)] = C;
+                                  used[atomicAdd(nused, 1)] = C;
                               }));
     __syncthreads();
     VT bv = 0;
     int32_t bc = -1;
-    const int32_t nu = s_nused;
+    const int32_t nu = *nused;
+    if (threadIdx.x == 0) s_nused[(it + 1) & 1] = 0;
     for (int32_t x = threadIdx.x; x < nu; x += blockDim.x) {
       const int32_t C = used[x];
       better(bv, bc, val[C], C);
@@ -560,14 +565,18 @@ __global__ void __launch_bounds__(256, 4) k_rate_dense(RateArgs A) {
       s_rc[wv] = bc;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int x = 1; x < nw; ++x) better(bv, bc, s_rv[x], s_rc[x]);
-      s_nused = 0;
-      publish(A, u, bc);
-      incid += end - beg;
-      ++nodes;
+    // warp 0 combines and publishes while the other warps start the next node
+    if (wv == 0) {
+      bv = lane_id() < nw ? s_rv[lane_id()] : (VT)0;
+      bc = lane_id() < nw ? s_rc[lane_id()] : -1;
+      warp_argmax(bv, bc);
+      if (lane_id() == 0) {
+        publish(A, u, bc);
+        incid += end - beg;
+        ++nodes;
+      }
     }
-    __syncthreads();
+    ++it;
   }
   if (lane_id() == 0 && visits) atomicAdd(&A.stats[ST_PINS], (unsigned long long)visits);
   if (threadIdx.x == 0 && nodes) {

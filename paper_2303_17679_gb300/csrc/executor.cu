@@ -25,7 +25,7 @@ int64_t now_ns() {
 }
 
 // Device bytes a job may hold at its peak: the level hierarchy (about eight
-// times the input's pins, net and node arrays on the config-2 shape), the
+// times the input's pins, net and node arrays on a Zipf(2.2) n = m = 1e6 input), the
 // clustering temporaries of the finest level (pin-cluster map: 12 bytes per
 // slot, 4 slots per pin), Phi (m x k int32) and Lambda, plus a fixed margin.
 int64_t estimate_bytes(const hg_job& j, int64_t p) {

@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_lp_gain_warp(GainArgs A) {
 
 // class 1: one block (GAIN_BLOCK_WARPS warps) per node; the warps split I(u)
 // and their partial accumulators are summed in shared memory before the argmax
-constexpr int GAIN_BLOCK_WARPS = 32;
+constexpr int GAIN_BLOCK_WARPS = 16;
 
 __global__ void __launch_bounds__(GAIN_BLOCK_WARPS * 32) k_lp_gain_block(GainArgs A) {
   constexpr int WARPS = GAIN_BLOCK_WARPS;
@@ -410,6 +410,7 @@ __global__ void k_lp_bucket(const int32_t* __restrict__ mv_u, const int32_t* __r
 }
 
 constexpr int SEL_THREADS = 256;
+constexpr int SEL_GATHER_K = 16;
 // Moves per direction sorted in shared memory (more go through global
 // memory): 4096 for k <= 8, 2048 for k <= 16, else 1024 (pairs hold fewer
 // moves as k grows, and a smaller buffer lets more pair blocks share an SM).
@@ -476,11 +477,17 @@ __device__ void block_weight_prefix(const unsigned long long* keys, int cnt,
 // finds the last state (i, j) on the merge path of A[0..na-1] and
 // B[0..nb-1] (ties to A) with -slack_a <= A[i] - B[j] <= slack_b.  Moves in
 // the chosen prefixes are approved.
+// GATHER (small k): no bucket pass; every pair block reads the whole move
+// list of the sub-round and keeps the moves of its two directions (their
+// order is irrelevant, the keys are sorted), and the global offsets of a
+// direction too long for shared memory are summed from dcount.
+template <bool GATHER>
 __global__ void __launch_bounds__(SEL_THREADS)
 k_lp_select(const int32_t* __restrict__ ioff, const int32_t* __restrict__ bucket,
             const int32_t* __restrict__ doff,
             const int32_t* __restrict__ dcount, const int32_t* __restrict__ mv_u,
             const int32_t* __restrict__ mv_to, const long long* __restrict__ mv_g,
+            const int32_t* __restrict__ part,
             const int32_t* __restrict__ c, const long long* __restrict__ bw, long long lmax, int k,
             unsigned long long* __restrict__ gkeys, long long* __restrict__ gpre,
             int32_t* __restrict__ ap_u, int32_t* __restrict__ ap_from,
@@ -503,14 +510,38 @@ k_lp_select(const int32_t* __restrict__ ioff, const int32_t* __restrict__ bucket
   const int dab = a * k + b, dba = b * k + a;
   const int na = dcount[dab], nb = dcount[dba];
   if (na + nb == 0) return;
-  const int oa = doff[dab], ob = doff[dba];
-
   auto pow2 = [](int x) {
     int p = 1;
     while (p < x) p <<= 1;
     return p;
   };
   const int Pa = pow2(na), Pb = pow2(nb);
+  int oa = 0, ob = 0;
+  __shared__ int s_gat[4];  // GATHER: offsets of the two directions, fill counters
+  if constexpr (GATHER) {
+    if (threadIdx.x < 4) s_gat[threadIdx.x] = 0;
+    __syncthreads();
+    if (Pa > cap || Pb > cap) {
+      int sa = 0, sb = 0;
+      for (int d = threadIdx.x; d < k * k; d += blockDim.x) {
+        const int cd = dcount[d];
+        if (d < dab) sa += cd;
+        if (d < dba) sb += cd;
+      }
+      sa = warp_sum(sa);
+      sb = warp_sum(sb);
+      if (lane_id() == 0) {
+        atomicAdd(&s_gat[0], sa);
+        atomicAdd(&s_gat[1], sb);
+      }
+      __syncthreads();
+      oa = s_gat[0];
+      ob = s_gat[1];
+    }
+  } else {
+    oa = doff[dab];
+    ob = doff[dba];
+  }
   // buffers: shared memory when the padded sequence fits, else a global
   // region of 2 * count slots at twice the direction's bucket offset
   unsigned long long* ka = Pa <= cap ? s_keys0 : gkeys + 2 * (int64_t)oa;
@@ -518,20 +549,49 @@ k_lp_select(const int32_t* __restrict__ ioff, const int32_t* __restrict__ bucket
   long long* A = na <= cap ? s_pre0 : gpre + (int64_t)oa + dab;
   long long* B = nb <= cap ? s_pre1 : gpre + (int64_t)ob + dba;
 
-  for (int i = threadIdx.x; i < Pa; i += blockDim.x) {
-    if (i < na) {
-      const int32_t mi = bucket[oa + i];
-      ka[i] = sel_key(mv_g[mi], mv_u[mi]);
-    } else {
-      ka[i] = ~0ull;
+  if constexpr (GATHER) {
+    const int32_t nm = words[SW_MOVES];
+    const unsigned below = (1u << lane_id()) - 1u;
+    for (int32_t b0 = 0; b0 < nm; b0 += blockDim.x) {
+      const int32_t i = b0 + threadIdx.x;
+      bool in_a = false, in_b = false;
+      unsigned long long key = 0;
+      if (i < nm) {
+        const int32_t u = mv_u[i];
+        const int t = mv_to[i], s = part[u];
+        in_a = s == a && t == b;
+        in_b = s == b && t == a;
+        if (in_a || in_b) key = sel_key(mv_g[i], u);
+      }
+      const unsigned ma = __ballot_sync(FULL, in_a), mb = __ballot_sync(FULL, in_b);
+      int base_a = 0, base_b = 0;
+      if (lane_id() == 0) {
+        if (ma) base_a = atomicAdd(&s_gat[2], __popc(ma));
+        if (mb) base_b = atomicAdd(&s_gat[3], __popc(mb));
+      }
+      base_a = __shfl_sync(FULL, base_a, 0);
+      base_b = __shfl_sync(FULL, base_b, 0);
+      if (in_a) ka[base_a + __popc(ma & below)] = key;
+      if (in_b) kb[base_b + __popc(mb & below)] = key;
     }
-  }
-  for (int i = threadIdx.x; i < Pb; i += blockDim.x) {
-    if (i < nb) {
-      const int32_t mi = bucket[ob + i];
-      kb[i] = sel_key(mv_g[mi], mv_u[mi]);
-    } else {
-      kb[i] = ~0ull;
+    for (int i = na + threadIdx.x; i < Pa; i += blockDim.x) ka[i] = ~0ull;
+    for (int i = nb + threadIdx.x; i < Pb; i += blockDim.x) kb[i] = ~0ull;
+  } else {
+    for (int i = threadIdx.x; i < Pa; i += blockDim.x) {
+      if (i < na) {
+        const int32_t mi = bucket[oa + i];
+        ka[i] = sel_key(mv_g[mi], mv_u[mi]);
+      } else {
+        ka[i] = ~0ull;
+      }
+    }
+    for (int i = threadIdx.x; i < Pb; i += blockDim.x) {
+      if (i < nb) {
+        const int32_t mi = bucket[ob + i];
+        kb[i] = sel_key(mv_g[mi], mv_u[mi]);
+      } else {
+        kb[i] = ~0ull;
+      }
     }
   }
   __syncthreads();
@@ -740,12 +800,18 @@ struct PassGraphCache {
   int device = -1;
   int S = -1;
   cudaStream_t capture = nullptr;
+  cudaStream_t side = nullptr;  // second branch of the captured pass
+  cudaEvent_t fork = nullptr, join = nullptr;
   cudaGraphExec_t exec = nullptr;
   void reset() {
     if (exec) cudaGraphExecDestroy(exec);
     if (capture) cudaStreamDestroy(capture);
+    if (side) cudaStreamDestroy(side);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
     exec = nullptr;
-    capture = nullptr;
+    capture = side = nullptr;
+    fork = join = nullptr;
     device = S = -1;
   }
   // Makes exec run `graph` (which it consumes) and returns it.
@@ -779,6 +845,9 @@ PassGraphCache& pass_graph_cache(const Ctx& cx) {
   if (cache.device != dev) {
     cache.reset();
     HG_CUDA(cudaStreamCreateWithFlags(&cache.capture, cudaStreamNonBlocking));
+    HG_CUDA(cudaStreamCreateWithFlags(&cache.side, cudaStreamNonBlocking));
+    HG_CUDA(cudaEventCreateWithFlags(&cache.fork, cudaEventDisableTiming));
+    HG_CUDA(cudaEventCreateWithFlags(&cache.join, cudaEventDisableTiming));
     cache.device = dev;
   }
   (void)cx;
@@ -865,12 +934,21 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   {
     static std::once_flag once;
     std::call_once(once, [] {
-      HG_CUDA(cudaFuncSetAttribute(k_lp_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      HG_CUDA(cudaFuncSetAttribute(k_lp_select<false>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sel_smem_bytes(sel_cap_for(2))));
+      HG_CUDA(cudaFuncSetAttribute(k_lp_select<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)sel_smem_bytes(sel_cap_for(2))));
     });
   }
-  const int per_pass_launches = 3 + 5 * S;
-  auto enqueue_pass = [&](bool timed, cudaStream_t sm) {
+  // k <= SEL_GATHER_K: the pair blocks gather their own moves (k (k - 1) / 2
+  // blocks each reading the move list), no bucket pass
+  const bool gather = k <= SEL_GATHER_K;
+  const int per_pass_launches = 3 + (gather ? 4 : 5) * S;
+  // side != nullptr: the two best-move kernels of a sub-round are captured
+  // as parallel branches (they only meet in atomics on the move list), so
+  // the few high-degree nodes of the block class overlap with the warp class
+  auto enqueue_pass = [&](bool timed, cudaStream_t sm, const PassGraphCache* fj) {
     HG_CUDA(cudaMemsetAsync(sr_cnt.p, 0, sr_cnt.bytes(), sm));
     HG_CUDA(cudaMemsetAsync(sr_fill.p, 0, sr_fill.bytes(), sm));
     HG_CUDA(cudaMemsetAsync(dcnt.p, 0, dcnt.bytes(), sm));
@@ -897,24 +975,41 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
       G.words = w_s;
       {
         EventTimer tm(cx, timed ? &rc.ms_gain : nullptr);
-        if (timed) gain_timer.begin();
-        k_lp_gain_warp<<<g_gain, WARPS * 32, 0, sm>>>(G);
-        if (timed) gain_timer.end();
-        check_launch("lp_gain_warp");
-        if (timed) gain_timer.begin();
-        k_lp_gain_block<<<g_gain_block, GAIN_BLOCK_WARPS * 32, 0, sm>>>(G);
-        if (timed) gain_timer.end();
-        check_launch("lp_gain_block");
+        if (fj) {
+          HG_CUDA(cudaEventRecord(fj->fork, sm));
+          HG_CUDA(cudaStreamWaitEvent(fj->side, fj->fork, 0));
+          k_lp_gain_block<<<g_gain_block, GAIN_BLOCK_WARPS * 32, 0, fj->side>>>(G);
+          check_launch("lp_gain_block");
+          k_lp_gain_warp<<<g_gain, WARPS * 32, 0, sm>>>(G);
+          check_launch("lp_gain_warp");
+          HG_CUDA(cudaEventRecord(fj->join, fj->side));
+          HG_CUDA(cudaStreamWaitEvent(sm, fj->join, 0));
+        } else {
+          if (timed) gain_timer.begin();
+          k_lp_gain_warp<<<g_gain, WARPS * 32, 0, sm>>>(G);
+          if (timed) gain_timer.end();
+          check_launch("lp_gain_warp");
+          if (timed) gain_timer.begin();
+          k_lp_gain_block<<<g_gain_block, GAIN_BLOCK_WARPS * 32, 0, sm>>>(G);
+          if (timed) gain_timer.end();
+          check_launch("lp_gain_block");
+        }
         rc.lp_gain_launches += 2;
       }
       {
         EventTimer tm(cx, timed ? &rc.ms_select : nullptr);
-        k_lp_bucket<<<g_bucket, 256, (kk + 1) * sizeof(int32_t), sm>>>(
-            mv_u.p, mv_to.p, part, k, dc_s, df_s, doff.p, w_s, bucket.p);
-        check_launch("lp_bucket");
-        k_lp_select<<<g_sel, SEL_THREADS, sel_bytes, sm>>>(
-            L.ioff.p, bucket.p, doff.p, dc_s, mv_u.p, mv_to.p, mv_g.p, L.c.p, st.bw.p, lmax, k,
-            gkeys.p, gpre.p, ap_u.p, ap_from.p, ap_to.p, w_s);
+        if (gather) {
+          k_lp_select<true><<<g_sel, SEL_THREADS, sel_bytes, sm>>>(
+              L.ioff.p, bucket.p, doff.p, dc_s, mv_u.p, mv_to.p, mv_g.p, part, L.c.p, st.bw.p,
+              lmax, k, gkeys.p, gpre.p, ap_u.p, ap_from.p, ap_to.p, w_s);
+        } else {
+          k_lp_bucket<<<g_bucket, 256, (kk + 1) * sizeof(int32_t), sm>>>(
+              mv_u.p, mv_to.p, part, k, dc_s, df_s, doff.p, w_s, bucket.p);
+          check_launch("lp_bucket");
+          k_lp_select<false><<<g_sel, SEL_THREADS, sel_bytes, sm>>>(
+              L.ioff.p, bucket.p, doff.p, dc_s, mv_u.p, mv_to.p, mv_g.p, part, L.c.p, st.bw.p,
+              lmax, k, gkeys.p, gpre.p, ap_u.p, ap_from.p, ap_to.p, w_s);
+        }
         check_launch("lp_select");
       }
       {
@@ -934,7 +1029,7 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
     cudaGraph_t graph = nullptr;
     HG_CUDA(cudaStreamBeginCapture(gc.capture, cudaStreamCaptureModeThreadLocal));
     try {
-      enqueue_pass(false, gc.capture);
+      enqueue_pass(false, gc.capture, &gc);
     } catch (...) {
       cudaStreamEndCapture(gc.capture, &graph);
       if (graph) cudaGraphDestroy(graph);
@@ -945,7 +1040,7 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   }
   for (int pass = 0; pass < max_passes; ++pass) {
     if (exec) HG_CUDA(cudaGraphLaunch(exec, cx.stream));
-    else enqueue_pass(true, cx.stream);
+    else enqueue_pass(true, cx.stream, nullptr);
     if (cx.launches) *cx.launches += per_pass_launches;
     unsigned long long hc[2];
     wait_stream(cx);  // the pass is done, so the graph is idle before its next update

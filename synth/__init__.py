@@ -176,9 +176,9 @@ def random_uniform(seed: int, n: int, m: int, geom_p: float = 0.3, cap: int = 64
     return make(seed, n, m, sizes, False, node_w, net_w, name)
 
 
-def config1(seed: int = 1) -> Hypergraph:
+def uniform_10k(seed: int = 1) -> Hypergraph:
     """Plain single level: n = m = 10,000, unit weights, sizes 2 + Geom(0.3) <= 64."""
-    return random_uniform(seed, 10_000, 10_000, name="cfg1")
+    return random_uniform(seed, 10_000, 10_000, name="uniform10k")
 
 
 def zipf_preferential(seed: int, n: int, m: int, s: float = 2.2, lo: int = 2, hi: int = 1024,
@@ -188,10 +188,10 @@ def zipf_preferential(seed: int, n: int, m: int, s: float = 2.2, lo: int = 2, hi
     return make(seed, n, m, sizes, True, (w_lo, w_hi), (w_lo, w_hi), name)
 
 
-def config2(seed: int = 1, n: int = 1_000_000, m: int | None = None) -> Hypergraph:
+def zipf_1m(seed: int = 1, n: int = 1_000_000, m: int | None = None) -> Hypergraph:
     """Full hierarchy workload: n = m = 1e6, Zipf(2.2) sizes in [2, 1024],
     heavy-tailed node degrees, node and net weights uniform in [1, 10]."""
-    return zipf_preferential(seed, n, n if m is None else m, name=f"cfg2_n{n}")
+    return zipf_preferential(seed, n, n if m is None else m, name=f"zipf_n{n}")
 
 
 def large_net_stress(seed: int, n: int, m: int, big_every: int = 100, big_lo: int = 1000,
@@ -208,14 +208,14 @@ def large_net_stress(seed: int, n: int, m: int, big_every: int = 100, big_lo: in
     return make(seed, n, m, sizes, False, None, (1, 100), name)
 
 
-def config3(seed: int = 1, n: int = 4_000_000, m: int = 2_000_000) -> Hypergraph:
+def large_net_4m(seed: int = 1, n: int = 4_000_000, m: int = 2_000_000) -> Hypergraph:
     """Large-net stress: n = 4e6, m = 2e6, 1 % nets of 1k-100k pins, net 0 = 100k pins."""
-    return large_net_stress(seed, n, m, force_first=100_000, name=f"cfg3_n{n}")
+    return large_net_stress(seed, n, m, force_first=100_000, name=f"large_net_n{n}")
 
 
-def config4(seed: int = 1, count: int = 512, n_lo: int = 1000, n_hi: int = 200_000):
+def batch_instances(seed: int = 1, count: int = 512, n_lo: int = 1000, n_hi: int = 200_000):
     """Batch of independent instances: n log-uniform in [n_lo, n_hi], m/n in
-    [0.5, 3], sizes as config 1, weights in [1, 10], k in {2,4,8,16,32}."""
+    [0.5, 3], sizes as uniform_10k, weights in [1, 10], k in {2,4,8,16,32}."""
     u = uniform_doubles(sub_seed(seed, 40), 3 * count).reshape(count, 3)
     ks = (2, 4, 8, 16, 32)
     out = []
@@ -224,12 +224,12 @@ def config4(seed: int = 1, count: int = 512, n_lo: int = 1000, n_hi: int = 200_0
         m = max(1, int(round(n * (0.5 + 2.5 * u[i, 1]))))
         k = ks[min(4, int(u[i, 2] * 5))]
         hg = random_uniform(sub_seed(seed, 41, i), n, m, node_w=(1, 10), net_w=(1, 10),
-                            name=f"cfg4_{i}")
+                            name=f"batch_{i}")
         out.append((hg, k))
     return out
 
 
-def config5_arrivals(seed: int = 1, rate: float = 200.0, duration: float = 60.0,
+def poisson_arrivals(seed: int = 1, rate: float = 200.0, duration: float = 60.0,
                      pins_lo: float = 1e4, pins_hi: float = 2e6):
     """Poisson arrivals: list of (arrival_s, request_seed, target_pins, k)."""
     cap = int(rate * duration * 2 + 100)
@@ -246,9 +246,9 @@ def config5_arrivals(seed: int = 1, rate: float = 200.0, duration: float = 60.0,
     return out
 
 
-def config5_request(req_seed: int, target_pins: int) -> Hypergraph:
+def poisson_request(req_seed: int, target_pins: int) -> Hypergraph:
     """One serving request: m = n = round(pins / 6.8), Zipf(2.2) sizes in [2, 1024]."""
     m = max(2, int(round(target_pins / 6.8)))
     sizes = sizes_zipf(sub_seed(req_seed, 1), m, 2.2, 2, min(1024, m))
-    return make(req_seed, m, m, sizes, False, None, None, name="cfg5_req")
+    return make(req_seed, m, m, sizes, False, None, None, name="poisson_req")
 

@@ -50,7 +50,7 @@ def run_all(ex, jobs):
 
 
 def test_batch_equals_plain_and_oracle(oracle_mod):
-    jobs = synth.config4(7, count=24, n_lo=1000, n_hi=20_000)
+    jobs = synth.batch_instances(7, count=24, n_lo=1000, n_hi=20_000)
     ex = hg.Executor(slots=6)
     try:
         got = run_all(ex, jobs)
@@ -71,7 +71,7 @@ def test_batch_equals_plain_and_oracle(oracle_mod):
 
 
 def test_admission_respects_the_memory_budget():
-    jobs = synth.config4(9, count=12, n_lo=2000, n_hi=30_000)
+    jobs = synth.batch_instances(9, count=12, n_lo=2000, n_hi=30_000)
     ex = hg.Executor(slots=8, mem_budget_bytes=600 << 20)
     try:
         got = run_all(ex, jobs)
@@ -91,8 +91,8 @@ def test_admission_respects_the_memory_budget():
 
 
 def test_serving_stream_results_match_alone():
-    arrivals = synth.config5_arrivals(3, rate=400.0, duration=0.1, pins_lo=2e4, pins_hi=3e5)
-    reqs = [(synth.config5_request(s, pins), k) for (_, s, pins, k) in arrivals]
+    arrivals = synth.poisson_arrivals(3, rate=400.0, duration=0.1, pins_lo=2e4, pins_hi=3e5)
+    reqs = [(synth.poisson_request(s, pins), k) for (_, s, pins, k) in arrivals]
     assert len(reqs) >= 10
     ex = hg.Executor(slots=4)
     got = {}
@@ -126,7 +126,7 @@ def test_serving_stream_results_match_alone():
 def test_submit_rejects_bad_jobs():
     ex = hg.Executor(slots=1)
     try:
-        hgr = synth.config1(1)
+        hgr = synth.uniform_10k(1)
         with pytest.raises(hg.HgError):
             ex.submit(hgr, 1)
         with pytest.raises(hg.HgError):

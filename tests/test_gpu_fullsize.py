@@ -1,4 +1,5 @@
-"""Full-size configs 2 and 3 on the GPU, in the configuration bench.py times
+"""Full-size inputs on the GPU (the n = m = 1e6 Zipf hypergraph and the 4M-node
+large-net hypergraph), in the configuration bench.py times
 (S = 16, T = 1000, f = 160).  The oracle cannot run these sizes in a test,
 so the results are checked by
   * sampled outputs: the target of sampled nodes that joined a cluster in the
@@ -182,18 +183,18 @@ def check_vcycle(hgr, k, oracle_mod):
     assert bw.max() <= oracle_mod.balance_limit(W, k, 30000)
 
 
-def test_config2_level0_full_size():
-    n1 = check_level0(synth.config2(SEED), 8)
+def test_zipf1m_level0_full_size():
+    n1 = check_level0(synth.zipf_1m(SEED), 8)
     assert n1 < 1_000_000
 
 
-def test_config2_vcycle_full_size(oracle_mod):
-    check_vcycle(synth.config2(SEED), 8, oracle_mod)
+def test_zipf1m_vcycle_full_size(oracle_mod):
+    check_vcycle(synth.zipf_1m(SEED), 8, oracle_mod)
 
 
-def test_config3_level0_full_size():
-    check_level0(synth.config3(SEED), 64, samples=200)
+def test_large_net_4m_level0_full_size():
+    check_level0(synth.large_net_4m(SEED), 64, samples=200)
 
 
-def test_config3_vcycle_full_size(oracle_mod):
-    check_vcycle(synth.config3(SEED), 64, oracle_mod)
+def test_large_net_4m_vcycle_full_size(oracle_mod):
+    check_vcycle(synth.large_net_4m(SEED), 64, oracle_mod)

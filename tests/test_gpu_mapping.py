@@ -49,7 +49,7 @@ def run(hgr, k, mapping):
 @pytest.mark.parametrize("name", ["zipf", "stress", "weighted"])
 def test_mapping_does_not_change_results(name):
     hgr, k = {
-        "zipf": (synth.config2(3, n=30_000), 8),
+        "zipf": (synth.zipf_1m(3, n=30_000), 8),
         "stress": (synth.large_net_stress(4, 40_000, 20_000, big_lo=300, big_hi=9000), 16),
         "weighted": (synth.random_uniform(5, 5000, 8000, node_w=(1, 50), net_w=(1, 1000)), 4),
     }[name]

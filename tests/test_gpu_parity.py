@@ -60,8 +60,8 @@ def tiny_cases():
 
 def medium_cases():
     return {
-        "cfg1": synth.config1(1),
-        "zipf20k": synth.config2(3, n=20_000),
+        "uniform10k": synth.uniform_10k(1),
+        "zipf20k": synth.zipf_1m(3, n=20_000),
         "stress": synth.large_net_stress(4, 40_000, 20_000, big_lo=300, big_hi=9000,
                                          force_first=9000),
         "weighted": synth.random_uniform(5, 5000, 8000, node_w=(1, 50), net_w=(1, 1000)),
@@ -70,7 +70,7 @@ def medium_cases():
 
 # ---------------------------------------------------------------- structure
 
-@pytest.mark.parametrize("name", ["cfg1", "stress"])
+@pytest.mark.parametrize("name", ["uniform10k", "stress"])
 @pytest.mark.parametrize("device_input", [False, True])
 def test_incidence_is_the_transpose(name, device_input):
     hgr = medium_cases()[name]
@@ -140,11 +140,11 @@ def check_one_level(oracle_mod, hgr, k, opt, level=0):
         hg.hg_destroy(h)
 
 
-@pytest.mark.parametrize("name", ["cfg1", "zipf20k", "stress", "weighted"])
+@pytest.mark.parametrize("name", ["uniform10k", "zipf20k", "stress", "weighted"])
 def test_coarsen_level_parity(oracle_mod, name):
     hgr = medium_cases()[name]
-    k = {"cfg1": 2, "zipf20k": 8, "stress": 64, "weighted": 4}[name]
-    factor = {"cfg1": 160, "zipf20k": 20, "stress": 4, "weighted": 40}[name]
+    k = {"uniform10k": 2, "zipf20k": 8, "stress": 64, "weighted": 4}[name]
+    factor = {"uniform10k": 160, "zipf20k": 20, "stress": 4, "weighted": 40}[name]
     check_one_level(oracle_mod, hgr, k, make_opt(seed=3, factor=factor))
 
 
@@ -155,7 +155,7 @@ def test_coarsen_tiny_cases(oracle_mod, name):
 
 
 def test_coarsen_small_threshold_and_subrounds(oracle_mod):
-    hgr = synth.config2(8, n=6000)
+    hgr = synth.zipf_1m(8, n=6000)
     check_one_level(oracle_mod, hgr, 2, make_opt(seed=8, S=3, T=8, factor=10))
 
 
@@ -167,7 +167,7 @@ def test_fingerprint_collisions_resolved(oracle_mod):
 
 
 def test_hierarchy_parity(oracle_mod):
-    hgr = synth.config2(11, n=30_000)
+    hgr = synth.zipf_1m(11, n=30_000)
     k, factor = 8, 10
     opt = make_opt(seed=11, factor=factor)
     vc = oracle_mod.multilevel(hgr, k, seed=11, factor=factor, max_passes=0)
@@ -187,7 +187,7 @@ def test_hierarchy_parity(oracle_mod):
 # ---------------------------------------------------------------- refinement
 
 def test_initial_partition_and_projection(oracle_mod):
-    hgr = synth.config2(12, n=8000)
+    hgr = synth.zipf_1m(12, n=8000)
     k = 8
     h = create(hgr, make_opt(seed=12, factor=10))
     try:
@@ -206,8 +206,8 @@ def test_initial_partition_and_projection(oracle_mod):
         hg.hg_destroy(h)
 
 
-@pytest.mark.parametrize("k,passes,name", [(2, 5, "cfg1"), (8, 3, "zipf20k"), (64, 2, "stress"),
-                                           (4, 5, "weighted"), (3, 1, "cfg1")])
+@pytest.mark.parametrize("k,passes,name", [(2, 5, "uniform10k"), (8, 3, "zipf20k"), (64, 2, "stress"),
+                                           (4, 5, "weighted"), (3, 1, "uniform10k")])
 def test_lp_parity(oracle_mod, k, passes, name):
     hgr = medium_cases()[name]
     seed = 21
@@ -240,7 +240,7 @@ def test_lp_large_slack_and_tight_balance(oracle_mod):
             hg.hg_destroy(h)
 
 
-@pytest.mark.parametrize("name,k,factor", [("cfg1", 2, 160), ("zipf20k", 8, 10)])
+@pytest.mark.parametrize("name,k,factor", [("uniform10k", 2, 160), ("zipf20k", 8, 10)])
 def test_partition_vcycle_parity(oracle_mod, name, k, factor):
     hgr = medium_cases()[name]
     seed = 31
@@ -257,7 +257,7 @@ def test_partition_vcycle_parity(oracle_mod, name, k, factor):
 
 
 def test_repeated_runs_identical():
-    hgr = synth.config2(41, n=50_000)
+    hgr = synth.zipf_1m(41, n=50_000)
     results = []
     for _ in range(2):
         h = create(hgr, make_opt(seed=41, factor=10))
@@ -311,7 +311,7 @@ def test_gain_recalculation_parity(oracle_mod, name, k, frac, level):
 
 
 def test_gain_recalculation_rejects_bad_sequences():
-    hgr = medium_cases()["cfg1"]
+    hgr = medium_cases()["uniform10k"]
     h = create(hgr, make_opt())
     try:
         part = dev(np.zeros(hgr.n, np.int32))
@@ -329,7 +329,7 @@ def test_gain_recalculation_rejects_bad_sequences():
 # ------------------------------------------------------ gain table (Sec. 6.2)
 
 @pytest.mark.parametrize("name,k,frac", [("zipf20k", 8, 0.2), ("stress", 64, 0.1),
-                                         ("weighted", 3, 1.0), ("cfg1", 2, 0.5)])
+                                         ("weighted", 3, 1.0), ("uniform10k", 2, 0.5)])
 def test_gain_table_build_and_moves(oracle_mod, name, k, frac):
     hgr = medium_cases()[name]
     h = create(hgr, make_opt())
@@ -357,7 +357,7 @@ def test_gain_table_build_and_moves(oracle_mod, name, k, frac):
 
 
 def test_gain_table_and_objective_reject_bad_block_ids():
-    hgr = medium_cases()["cfg1"]
+    hgr = medium_cases()["uniform10k"]
     h = create(hgr, make_opt())
     try:
         part = np.zeros(hgr.n, np.int32)

@@ -162,7 +162,7 @@ def test_clustering_invariants_random(oracle_mod, seed):
 
 
 def test_clustering_invariants_heavy_tailed(oracle_mod):
-    hg = synth.config2(5, n=3000)
+    hg = synth.zipf_1m(5, n=3000)
     W = int(hg.node_w.sum())
     k, S, T, factor = 2, 8, 200, 2
     r = oracle_mod.coarsen(hg, W, k, S=S, T=T, factor=factor, seed=5, level=0)

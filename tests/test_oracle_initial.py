@@ -28,7 +28,7 @@ def test_initial_partition_weighted_spread(oracle_mod):
 
 
 def test_multilevel_projection_preserves_objective(oracle_mod):
-    hg = synth.config2(2, n=4000)
+    hg = synth.zipf_1m(2, n=4000)
     k = 4
     vc = oracle_mod.multilevel(hg, k, seed=2, factor=20)
     L = len(vc.levels) - 1

@@ -39,9 +39,9 @@ def test_sizes_beyond_the_scratch_are_rejected_on_the_host(hg):
 
 def _cases():
     return {
-        "zipf20k_k8": (synth.config2(3, n=20_000), 8),
+        "zipf20k_k8": (synth.zipf_1m(3, n=20_000), 8),
         "weighted_k64": (synth.random_uniform(5, 5000, 8000, node_w=(1, 50), net_w=(1, 1000)), 64),
-        "zipf200k_k2": (synth.config2(7, n=200_000), 2),
+        "zipf200k_k2": (synth.zipf_1m(7, n=200_000), 2),
     }
 
 
@@ -85,7 +85,7 @@ def test_matches_the_handle_entry_points_twice_in_a_row(hg, name):
 def test_bad_block_id_is_reported_and_the_next_call_is_clean(hg):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    hgr = synth.config1(1)
+    hgr = synth.uniform_10k(1)
     k = 4
     stream = torch.cuda.current_stream()
     off, pins = _dev(hgr.offsets), _dev(hgr.pins)
