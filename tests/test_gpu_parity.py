@@ -225,6 +225,34 @@ def test_lp_parity(oracle_mod, k, passes, name):
     assert obj == ref["objective"]
 
 
+@pytest.mark.parametrize("n,k,eps", [(600_000, 2, 30000), (200_000, 32, 2_000_000_000)])
+def test_lp_parity_long_directions(oracle_mod, n, k, eps):
+    """Sub-rounds with more candidate moves in one direction than the pair
+    selection sorts in shared memory (4096 for k <= 8, 1024 for k > 16): the
+    sorted sequences and weight prefixes of that direction go through global
+    memory, at offsets the pair block sums from the direction counts (k <= 16)
+    or at the bucket offsets (larger k).  Only blocks 0 and 1 are used at the
+    start, so every candidate move is between them (a move into an empty
+    block has no positive gain)."""
+    hgr = synth.random_uniform(61 + k, n, n)
+    part0 = synth.uniform_ints(n + k, n, 0, 1)
+    seed = 7
+    _, mv = oracle_mod.lp_subround(hgr, k, part0, eps, 16, seed, 0, 0, 0)
+    longest = int(np.bincount(mv["src"] * k + mv["dst"], minlength=k * k).max())
+    assert longest > (4096 if k <= 8 else 1024)
+    ref = oracle_mod.lp_refine(hgr, k, part0, eps, 16, seed, 0, 2)
+    h = create(hgr, make_opt(seed=seed))
+    try:
+        dpart = dev(part0)
+        obj, moves = hg.hg_lp_refine(h, 0, k, eps, 2, dpart)
+        got = dpart.cpu().numpy()
+    finally:
+        hg.hg_destroy(h)
+    assert moves == ref["moves"]
+    assert np.array_equal(got, ref["part"])
+    assert obj == ref["objective"]
+
+
 def test_lp_large_slack_and_tight_balance(oracle_mod):
     hgr = synth.random_uniform(22, 4000, 4000, node_w=(1, 9))
     for eps in (0, 1_000_000):
