@@ -90,7 +90,7 @@ typedef struct {
    * <= 2048, default 2048), sixteen warps (rate_block_max_d, <= 4096,
    * default 4096), else the grid-split path.  In label propagation, nodes
    * with more than lp_block_min_deg incident nets (default 64, <= 2^20) are
-   * evaluated by a block of eight warps, the others by one warp. */
+   * evaluated by a block of sixteen warps, the others by one warp. */
   int32_t rate_warp_max_d;
   int32_t rate_pair_max_d;
   int32_t rate_quad_max_d;
@@ -114,7 +114,7 @@ typedef struct {
   double ms_project;    /* projection (a9) */
   double ms_phi;        /* pin counts, connectivity sets, block weights (a10) */
   double ms_lp_gain;    /* label-propagation best moves (a11) */
-  double ms_lp_select;  /* pair bucketing and prefix selection (a12) */
+  double ms_lp_select;  /* move gathering or bucketing and prefix selection (a12) */
   double ms_lp_apply;   /* move application (a13) */
   double ms_objective;  /* objective (a14) */
   double ms_initial;    /* host initial partition incl. copies */
