@@ -5,8 +5,10 @@
 //
 // Layout: Phi is a dense m x k int32 table (row = net), Lambda one 64-bit
 // mask per net (k <= 64), block weights int64[k].  One label-propagation
-// sub-round is four launches: best moves (a11), bucketing by block pair and
-// per-pair prefix selection (a12), application (a13).
+// sub-round is four launches for k <= 16 and five above: best moves of the
+// warp and block node classes (a11, parallel branches of the captured
+// pass), bucketing by block pair (k > 16 only), per-pair prefix selection
+// (a12), application (a13).
 #include <climits>
 #include <mutex>
 
