@@ -148,6 +148,34 @@ def test_coarsen_level_parity(oracle_mod, name):
     check_one_level(oracle_mod, hgr, k, make_opt(seed=3, factor=factor))
 
 
+def hub_hypergraph(oracle_mod, seed=71, n=200_000, m_base=150_000, hub_nets=45_000, sub_seed=3):
+    """Random 2 + Geom(0.3) nets plus one hub in hub_nets extra 3-pin nets with
+    two random other nodes each.  The hub is the smallest id of sub-round 0
+    (so it is rated before any node can join it), and its candidate bound
+    D = min(W, n) >= 135,000 is above what eight shared-memory parts hold, so
+    its rating runs through the global hash table split over the grid."""
+    hub = next(u for u in range(n) if oracle_mod.subround_clustering(sub_seed, 0, u, 16) == 0)
+    base = synth.random_uniform(seed, n, m_base)
+    a = synth.uniform_ints(seed + 1, hub_nets, 0, n // 2 - 1)
+    b = synth.uniform_ints(seed + 2, hub_nets, n // 2, n - 1)
+    a[a == hub] = (hub + 1) % (n // 2)
+    extra = np.stack([np.full(hub_nets, hub, np.int32), a, b], axis=1).reshape(-1)
+    off = np.concatenate([base.offsets,
+                          base.p + 3 * np.arange(1, hub_nets + 1, dtype=np.int64)]).astype(np.int32)
+    pins = np.concatenate([base.pins, extra]).astype(np.int32)
+    w = np.concatenate([base.net_w, np.ones(hub_nets, np.int32)])
+    return hub, synth.Hypergraph(n, m_base + hub_nets, off, pins, w, base.node_w.copy(), "hub")
+
+
+@pytest.mark.parametrize("k", [2, 8])
+def test_coarsen_hub_uses_global_hash_split(oracle_mod, k):
+    hub, hgr = hub_hypergraph(oracle_mod)
+    W = int(hgr.node_w.sum())
+    ref = oracle_mod.coarsen(hgr, W, k, 16, 1000, 160, 3, 0)
+    assert ref["rated_in"][hub] == 0 and ref["target"][hub] >= 0
+    check_one_level(oracle_mod, hgr, k, make_opt(seed=3))
+
+
 @pytest.mark.parametrize("name", ["single_net", "isolated", "identical", "heavy_node"])
 def test_coarsen_tiny_cases(oracle_mod, name):
     hgr = tiny_cases()[name]
