@@ -77,7 +77,10 @@ typedef struct {
    * comparison must resolve; results do not change, only the work. */
   int32_t fingerprint_bits;
   /* Optional device allocator (for example a framework's caching allocator).
-   * Both NULL: stream-ordered cudaMallocAsync / cudaFreeAsync. */
+   * Both NULL: stream-ordered allocations (cudaMallocFromPoolAsync /
+   * cudaFreeAsync) from the library's own memory pool of the device, which
+   * keeps freed blocks for later handles (hg_trim_memory returns them to the
+   * driver); the device's default pool is not touched. */
   void* (*dev_alloc)(size_t bytes, void* ctx);
   void (*dev_free)(void* ptr, void* ctx);
   void* alloc_ctx;
@@ -253,12 +256,13 @@ int hg_gain_table_move(hg_t* h, int32_t level, int32_t k, int32_t* part, int32_t
                        const int32_t* move_nodes, const int32_t* move_targets, int64_t* benefit,
                        int64_t* penalty);
 
-/* The objective f_{lambda-1} (Sec. 2) and the block weights c(V_i) of a
- * partition, for a hypergraph held by the caller in device memory, with no
- * handle and without allocating device memory.  The paper has no
- * counterpart: this serves callers that must not allocate, such as a serving
- * loop where a cudaMalloc/cudaFree would synchronize the device and stall
- * the other streams, a process whose device memory is reserved in full up
+/* The connectivity objective (for every net, its weight times the number of
+ * blocks its pins lie in minus one, summed over the nets) and the weight of
+ * every block, for a partition of a hypergraph that the caller holds in
+ * device memory, with no handle and without allocating device memory.  The
+ * paper has no counterpart.  It serves callers that cannot allocate: a
+ * serving loop in which a cudaMalloc/cudaFree would synchronize the device
+ * and stall the other streams, a process that reserved all device memory up
  * front, or code running inside an hg_options.dev_alloc callback, which must
  * not re-enter the allocator.
  *   n, m, p       nodes (>= 1), nets (>= 0), pins (0 <= p < 2^31)
@@ -269,23 +273,24 @@ int hg_gain_table_move(hg_t* h, int32_t level, int32_t k, int32_t* part, int32_t
  *   k             1..64
  *   part          device, n int32 entries in [0, k)
  *   cuda_stream   cudaStream_t to run on (NULL = legacy default stream)
- *   out_objective host, written: sum over nets of (lambda(e) - 1) w(e); an
- *                 empty net counts 0
+ *   out_objective host, written; an empty net counts 0
  *   out_block_weights host, k int64 entries written, or NULL
  * Scratch: a fixed 9,248-byte device array inside the library (1024 block
  * partials, 64 block-weight counters, a finished-block counter, a status word
  * and a result record), enough for any n, m and p since the grid is capped
- * at 1024 blocks.  Returns HG_ERR_UNSUPPORTED for k > 64 (the scratch holds
+ * at 1024 blocks.  Every GPU that loads the library holds it until the
+ * process exits.  Returns HG_ERR_UNSUPPORTED for k > 64 (the scratch holds
  * 64 block-weight counters), HG_ERR_INVALID for other bad sizes or NULL
  * pointers (checked on the host, nothing launched) and for offsets, pins or
  * block ids out of range (checked on the device; the call then returns
  * after the kernel without writing the outputs), HG_ERR_CUDA / HG_ERR_OOM for
- * a CUDA error.  Synchronizes the stream.
- * The first call on a device (the current device) looks up the scratch
- * address and the SM count once; make that first call before any stream
- * capture begins.  The scratch is shared by all calls on a device: calls
- * that overlap in time on one device (from two host threads, or on two
- * streams) race and must be serialized by the caller. */
+ * a CUDA error (also when the kernel did not complete).  Synchronizes the
+ * stream.
+ * The first call on a device loads the library's device code there; make it
+ * before any stream capture begins.  The scratch is shared by all calls on a
+ * device and keeps the last call's contents (each call clears what must
+ * start at zero): calls that overlap in time on one device (from two host
+ * threads, or on two streams) race and must be serialized by the caller. */
 int hg_objective_noalloc(int32_t n, int32_t m, int64_t p, const int32_t* net_offsets,
                          const int32_t* pins, const int32_t* net_weights,
                          const int32_t* node_weights, int32_t k, const int32_t* part,
@@ -380,7 +385,13 @@ int hg_enable_timing(hg_t* h, int32_t on);
 int hg_get_stats(hg_t* h, hg_stats* out);
 int hg_reset_stats(hg_t* h);
 
-/* Frees everything the handle owns.  Safe on NULL and after any error. */
+/* Returns the device memory cached in the library's own pool of the current
+ * device (blocks freed by destroyed handles, kept for reuse) to the driver.
+ * The paper has no counterpart.  Memory of live handles is not affected. */
+int hg_trim_memory(void);
+
+/* Frees everything the handle owns.  Safe on NULL and after any error.
+ * Its blocks go back to the library's pool (see hg_options.dev_alloc). */
 int hg_destroy(hg_t* h);
 
 /* Static description of a status code. */

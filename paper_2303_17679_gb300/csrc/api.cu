@@ -210,14 +210,7 @@ int hg_create(int32_t n, int32_t m, const int32_t* net_offsets, const int32_t* p
     h->cx.alloc.ctx = o.alloc_ctx;
     h->cx.alloc.stream = h->cx.stream;
     h->cx.launches = &h->launches;
-    if (!o.dev_alloc) {
-      // keep freed blocks in the pool between calls instead of returning them
-      cudaMemPool_t pool;
-      if (cudaDeviceGetDefaultMemPool(&pool, h->device) == cudaSuccess) {
-        uint64_t thr = ~0ull;
-        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-      }
-    }
+    if (!o.dev_alloc) h->cx.alloc.pool = hgk::library_pool(h->device);
     h->cx.d_status = static_cast<int32_t*>(h->cx.alloc.get(sizeof(int32_t) * 4));
     HG_CUDA(cudaMemsetAsync(h->cx.d_status, 0, sizeof(int32_t) * 4, h->cx.stream));
     if (mem == HG_MEM_DEVICE) {
@@ -576,6 +569,23 @@ int hg_reset_stats(hg_t* h) {
   if (!h) return HG_ERR_INVALID;
   h->stats = hg_stats{};
   h->launches = 0;
+  return HG_OK;
+}
+
+int hg_trim_memory(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return HG_ERR_CUDA;
+  }
+  try {
+    if (cudaMemPoolTrimTo(hgk::library_pool(dev), 0) != cudaSuccess) {
+      cudaGetLastError();
+      return HG_ERR_CUDA;
+    }
+  } catch (const HgError& e) {
+    return e.code;
+  }
   return HG_OK;
 }
 

@@ -29,20 +29,29 @@
 // Nodes are bucketed per level by class and sub-round.  With W(u) = sum of
 // |e| over u's rated nets (the pins its rating visits) and D = min(W(u), n)
 // (a bound on its distinct candidates), a team accumulates u's ratings in a
-// shared-memory hash table sized to D:
-//   class 0  D <= 256:  one warp, 512 slots;
-//   class 1  D <= 1024: two warps, 2048 slots;
-//   class 2  D <= 4096 (or the level is small), W <= 16384: one block, 8192
-//            slots, or a table direct-indexed by cluster id on small levels;
-//   class 3  the rest: the node's incident nets are cut into items of 32
-//            nets spread over the whole grid, which accumulate into a per-node
-//            global table (direct-indexed or hashed) with a list of the used
-//            slots; a second kernel takes the argmax per node.
-// Class 3 keeps the heaviest nodes (coarse levels: hundreds of thousands of
+// shared-memory hash table of 2 D slots (rate_class; the D bounds are the
+// autotuner's cutoffs, defaults shown):
+//   class 0  D <= 256: one warp, 512 slots (eight teams per block);
+//   class 1  D <= 1024: four warps, 2048 slots (two teams per block);
+//   class 2  on levels whose n fits a shared table direct-indexed by cluster
+//            id, W <= 32768: one block with that table; on other levels
+//            D <= 2048, W <= 65536: eight warps, 4096 slots;
+//   class 3  D <= 4096, W <= 65536 (other levels): one block of sixteen
+//            warps (eight with 64-bit ratings), 8192 slots;
+//   class 4  the rest, split over the grid: a table in global memory direct-
+//            indexed by cluster id when n <= min(2 W, 65536), filled by items
+//            of 32 incident nets spread over the grid; else P = ceil(D / 9830)
+//            part blocks (P <= 8) of 1024 threads, each owning the candidates
+//            of one hash part in a 16384-slot shared table with a list of its
+//            inserted slots; else a global hash table filled by items.  A
+//            second kernel takes the argmax per node (or the best of the
+//            parts' bests).
+// Class 4 keeps the heaviest nodes (coarse levels: hundreds of thousands of
 // pin visits per node) from serialising a sub-round on one block.  Ratings
 // are accumulated in 32-bit words when the level's largest possible rating
-// fits (then a hash slot packs cluster id and rating into one 64-bit word),
-// else in 64-bit words.
+// fits, else in 64-bit words; a hash table keeps its cluster ids and its
+// ratings in separate arrays (a 32-bit CAS claims a key, an atomic add sums
+// into the value).
 #include <algorithm>
 #include <mutex>
 

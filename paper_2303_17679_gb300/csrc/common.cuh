@@ -171,9 +171,13 @@ struct Alloc {
   void (*fn_free)(void*, void*) = nullptr;
   void* ctx = nullptr;
   cudaStream_t stream = nullptr;
+  cudaMemPool_t pool = nullptr;  // library_pool(device) when no hook is given
   void* get(size_t bytes) const;
   void put(void* p) const;
 };
+
+// The library's private stream-ordered memory pool of a device (prim.cu).
+cudaMemPool_t library_pool(int device);
 
 template <typename T>
 struct DBuf {

@@ -68,8 +68,17 @@ void run_job(hg_exec_t* ex, cudaStream_t st, cudaEvent_t waiter, const Pending& 
                      &ex->opt, st, &h);
   int32_t* dpart = nullptr;
   if (rc == HG_OK) {
-    if (cudaMallocAsync(&dpart, sizeof(int32_t) * (size_t)std::max(j.n, 1), st) != cudaSuccess)
-      rc = HG_ERR_OOM;
+    try {
+      if (cudaMallocFromPoolAsync(reinterpret_cast<void**>(&dpart),
+                                  sizeof(int32_t) * (size_t)std::max(j.n, 1),
+                                  hgk::library_pool(ex->device), st) != cudaSuccess) {
+        cudaGetLastError();
+        dpart = nullptr;
+        rc = HG_ERR_OOM;
+      }
+    } catch (const hgk::HgError& e) {
+      rc = e.code;
+    }
   }
   int64_t obj = 0;
   if (rc == HG_OK) rc = hg_partition(h, j.k, j.eps_ppm, j.max_passes, dpart, &obj);

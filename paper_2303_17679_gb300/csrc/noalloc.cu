@@ -1,21 +1,25 @@
-// hg_objective_noalloc: the connectivity objective f_{lambda-1} (Sec. 2) and
-// the block weights c(V_i) of a partition of a caller-held device CSR, with
-// no handle and no device allocation.  The paper has no counterpart; this is
-// a library convenience for callers that must not allocate.
+// hg_objective_noalloc: the connectivity objective (for every net, its
+// weight times the number of blocks it touches minus one, summed) and the
+// block weights of a partition of a caller-held device CSR, with no handle
+// and no device allocation.  The paper has no counterpart; this is a library
+// convenience for callers that must not allocate.
 //
-// All scratch lives in one file-scope device array, whose address the host
-// takes once per device with cudaGetSymbolAddress:
+// All scratch lives in one file-scope device array.  Host code looks its
+// address up with cudaGetSymbolAddress on every call (cheap, allocates
+// nothing, and stays right if the module is loaded again, for example after
+// cudaDeviceReset or under another context):
 //   [0, NA_BLOCKS)            objective partial of every block (written by
 //                             its block before it is read; no initial value)
 //   [NA_BW, NA_BW + 64)       block-weight accumulators      - must be zero
 //   NA_TICKET                 count of finished blocks       - must be zero
 //   NA_STATUS                 bad-input flag                 - must be zero
 //   [NA_RES, NA_RES + 66)     result record: objective, status, 64 weights
-// The zero words are zero when the module loads and the last block of every
-// launch sets them back to zero after it has read them, so each call leaves
-// the scratch ready for the next one.
+// Before every launch the host clears the zero words and marks the result
+// record's status as unwritten (both with cudaMemsetAsync, which allocates
+// nothing), so a launch that did not finish is reported instead of leaving
+// an earlier call's result to be read; the last block of a launch also sets
+// the zero words back to zero after it has read them.
 #include <algorithm>
-#include <mutex>
 
 #include "common.cuh"
 
@@ -28,7 +32,6 @@ constexpr int NA_TICKET = NA_BW + HG_MAX_K;
 constexpr int NA_STATUS = NA_TICKET + 1;
 constexpr int NA_RES = NA_STATUS + 1;  // objective, status, weights[64]
 constexpr int NA_WORDS = NA_RES + 2 + HG_MAX_K;
-constexpr int NA_MAX_DEVICES = 64;
 
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[NA_WORDS];
 
@@ -110,9 +113,7 @@ k_objective_noalloc(const int32_t* __restrict__ eoff, const int32_t* __restrict_
   if (threadIdx.x == 0) atomicExch(&S[NA_TICKET], 0ull);
 }
 
-std::mutex g_setup_mu;
-unsigned long long* g_scratch_of[NA_MAX_DEVICES];  // per device, set once
-int g_sms_of[NA_MAX_DEVICES];
+constexpr unsigned long long NA_UNWRITTEN = ~0ull;  // result status before the last block
 
 int cuda_fail(cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? HG_ERR_OOM : HG_ERR_CUDA;
@@ -133,29 +134,25 @@ extern "C" int hg_objective_noalloc(int32_t n, int32_t m, int64_t p, const int32
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e);
-  if (dev < 0 || dev >= NA_MAX_DEVICES) return HG_ERR_UNSUPPORTED;
-  unsigned long long* S = nullptr;
+  // the scratch address in the current context (the first call on a device
+  // loads the module, so it should come before any stream capture)
+  void* addr = nullptr;
+  e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail(e);
+  unsigned long long* S = static_cast<unsigned long long*>(addr);
   int sms = 0;
-  {
-    std::lock_guard<std::mutex> g(g_setup_mu);
-    if (g_scratch_of[dev] == nullptr) {
-      // first call on this device (the device is current): look up the
-      // scratch address and the SM count
-      void* addr = nullptr;
-      e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
-      if (e != cudaSuccess) return cuda_fail(e);
-      e = cudaDeviceGetAttribute(&g_sms_of[dev], cudaDevAttrMultiProcessorCount, dev);
-      if (e != cudaSuccess) return cuda_fail(e);
-      g_scratch_of[dev] = static_cast<unsigned long long*>(addr);
-    }
-    S = g_scratch_of[dev];
-    sms = g_sms_of[dev];
-  }
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e);
   const cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const int64_t work = std::max<int64_t>((int64_t)m * 32, n);
   int64_t blocks = (work + NA_THREADS - 1) / NA_THREADS;
   blocks = std::min<int64_t>(blocks, std::min<int64_t>(NA_BLOCKS, (int64_t)sms * 8));
   blocks = std::max<int64_t>(blocks, 1);
+  // zero words cleared, result status marked unwritten
+  e = cudaMemsetAsync(S + NA_BW, 0, sizeof(unsigned long long) * (HG_MAX_K + 2), st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaMemsetAsync(S + NA_RES + 1, 0xff, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return cuda_fail(e);
   k_objective_noalloc<<<(unsigned)blocks, NA_THREADS, 0, st>>>(net_offsets, pins, net_weights,
                                                                node_weights, n, m, p, k, part, S);
   e = cudaGetLastError();
@@ -165,6 +162,7 @@ extern "C" int hg_objective_noalloc(int32_t n, int32_t m, int64_t p, const int32
   if (e != cudaSuccess) return cuda_fail(e);
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e);
+  if (res[1] == NA_UNWRITTEN) return HG_ERR_CUDA;
   if (res[1] != 0) return HG_ERR_INVALID;
   *out_objective = (int64_t)res[0];
   if (out_block_weights)

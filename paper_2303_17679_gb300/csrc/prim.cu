@@ -1,9 +1,38 @@
 // Data-parallel primitives: exclusive prefix sums, fills, scalar readback.
 // The prefix sums are the "parallel prefix sum operations" the contraction
 // algorithm relies on (Sec. 4.2), written here without CUB.
+#include <mutex>
+#include <vector>
+
 #include "common.cuh"
 
 namespace hgk {
+
+// The library's own stream-ordered pool per device, created on first use and
+// kept for the life of the process.  Its release threshold is unlimited, so
+// blocks freed by one handle stay in the pool for the next instead of going
+// back to the driver (and hg_trim_memory returns them); the device's default
+// pool, which other code in the process may use, is left as it is.
+cudaMemPool_t library_pool(int device) {
+  static std::mutex mu;
+  static std::vector<cudaMemPool_t> pools;
+  std::lock_guard<std::mutex> g(mu);
+  if (device < 0) throw HgError(HG_ERR_CUDA, "bad device ordinal");
+  if ((size_t)device >= pools.size()) pools.resize((size_t)device + 1, nullptr);
+  if (!pools[device]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    HG_CUDA(cudaMemPoolCreate(&pool, &props));
+    uint64_t thr = ~0ull;
+    HG_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    pools[device] = pool;
+  }
+  return pools[device];
+}
 
 void* Alloc::get(size_t bytes) const {
   void* p = nullptr;
@@ -13,11 +42,11 @@ void* Alloc::get(size_t bytes) const {
     if (!p) throw HgError(HG_ERR_OOM, "device allocation hook returned NULL");
     return p;
   }
-  cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+  cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool, stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     throw HgError(e == cudaErrorMemoryAllocation ? HG_ERR_OOM : HG_ERR_CUDA,
-                  std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+                  std::string("cudaMallocFromPoolAsync: ") + cudaGetErrorString(e));
   }
   return p;
 }

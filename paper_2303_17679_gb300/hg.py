@@ -144,6 +144,7 @@ def load(path: str | None = None):
             "hg_get_stats": (ctypes.c_int, [H, P(hg_stats)]),
             "hg_reset_stats": (ctypes.c_int, [H]),
             "hg_destroy": (ctypes.c_int, [H]),
+            "hg_trim_memory": (ctypes.c_int, []),
             "hg_exec_create": (ctypes.c_int, [i32, i64, P(hg_options), P(H)]),
             "hg_exec_submit": (ctypes.c_int, [H, P(hg_job), P(i64)]),
             "hg_exec_wait": (ctypes.c_int, [H, i32, i32, P(hg_job_result), P(i32)]),
@@ -167,7 +168,7 @@ def exported_symbols():
             "hg_level_info", "hg_initial_partition", "hg_project", "hg_lp_refine",
             "hg_objective", "hg_pin_counts", "hg_recalculate_gains", "hg_gain_table", "hg_gain_table_move",
             "hg_objective_noalloc", "hg_partition", "hg_get_level", "hg_get_incidence",
-            "hg_truncate", "hg_enable_timing", "hg_get_stats", "hg_reset_stats", "hg_destroy",
+            "hg_truncate", "hg_enable_timing", "hg_get_stats", "hg_reset_stats", "hg_destroy", "hg_trim_memory",
             "hg_exec_create", "hg_exec_submit", "hg_exec_wait", "hg_exec_pending",
             "hg_exec_now_ns", "hg_exec_destroy", "hg_strerror", "hg_version"]
 
@@ -391,6 +392,11 @@ def hg_reset_stats(h):
 def hg_destroy(h):
     if h:
         load().hg_destroy(h)
+
+
+def hg_trim_memory():
+    """Returns the memory cached in the library's pool of the current device."""
+    _check(load().hg_trim_memory(), "hg_trim_memory")
 
 
 # ------------------------------------------------------------------ executor

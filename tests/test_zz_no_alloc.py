@@ -1,8 +1,13 @@
 """hg_objective_noalloc (objective and block weights with no handle and no
-device allocation) against the handle-based entry points hg_objective and
-hg_pin_counts on the same inputs.  All values are integers, so the tolerance
-is zero.  The file name keeps it last in collection, so the entry point is
-also exercised after every other test has run in the same process."""
+device allocation), for callers that cannot allocate device memory, against
+the handle-based entry points hg_objective and hg_pin_counts and against the
+CPU oracle on the same inputs.  All values are integers, so the tolerance is
+zero.  A warm call must leave the device's free memory, PyTorch's allocator
+and the device's default memory pool exactly as they were.  The file name
+keeps it last in collection, so the entry point is also exercised after every
+other test has run in the same process."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -21,6 +26,38 @@ def hg():
 
 def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, np.int32)).cuda()
+
+
+def _cudart():
+    for name in ("libcudart.so.13", "libcudart.so", "/usr/local/cuda/lib64/libcudart.so"):
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    return None
+
+
+def _default_pool_used(rt):
+    """Bytes in use in the current device's default stream-ordered pool, or None."""
+    if rt is None:
+        return None
+    dev = ctypes.c_int(0)
+    pool = ctypes.c_void_p()
+    used = ctypes.c_uint64(0)
+    if rt.cudaGetDevice(ctypes.byref(dev)) != 0:
+        return None
+    if rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), dev) != 0:
+        return None
+    attr_used_mem_current = 5  # cudaMemPoolAttrUsedMemCurrent
+    if rt.cudaMemPoolGetAttribute(pool, attr_used_mem_current, ctypes.byref(used)) != 0:
+        return None
+    return used.value
+
+
+def _memory_state(rt):
+    torch.cuda.synchronize()
+    free, _ = torch.cuda.mem_get_info()
+    return free, torch.cuda.memory_allocated(), torch.cuda.memory_reserved(), _default_pool_used(rt)
 
 
 def test_sizes_beyond_the_scratch_are_rejected_on_the_host(hg):
@@ -47,7 +84,7 @@ def _cases():
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("name", list(_cases()))
-def test_matches_the_handle_entry_points_twice_in_a_row(hg, name):
+def test_matches_the_handle_entry_points_twice_in_a_row(hg, oracle_mod, name):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     hgr, k = _cases()[name]
@@ -61,12 +98,20 @@ def test_matches_the_handle_entry_points_twice_in_a_row(hg, name):
         _, _, want_bw = hg.hg_pin_counts(h, 0, k, part)
     finally:
         hg.hg_destroy(h)
+    hpart = part.cpu().numpy()
+    assert want_obj == oracle_mod.objective(hgr, k, hpart)
+    assert np.array_equal(want_bw, oracle_mod.block_weights(hgr, k, hpart))
     off, pins, w, c = (_dev(a) for a in (hgr.offsets, hgr.pins, hgr.net_w, hgr.node_w))
-    for _ in range(2):
+    rt = _cudart()
+    for i in range(2):
+        before = _memory_state(rt)
         obj, bw = hg.hg_objective_noalloc(hgr.n, hgr.m, len(hgr.pins), off, pins, w, c, k, part,
                                           stream)
+        after = _memory_state(rt)
         assert obj == want_obj
         assert np.array_equal(bw, want_bw)
+        if i == 1:  # a warm call: no device memory taken from any allocator
+            assert after == before, (before, after)
     # unit weights (NULL arrays) against the same partition with unit weights
     ones = np.ones_like
     h = hg.hg_create(hgr.n, hgr.m, hgr.offsets, hgr.pins, ones(hgr.net_w), ones(hgr.node_w),
@@ -106,4 +151,35 @@ def test_bad_block_id_is_reported_and_the_next_call_is_clean(hg):
     for _ in range(2):
         obj, bw = hg.hg_objective_noalloc(hgr.n, hgr.m, len(hgr.pins), off, pins, None, None, k,
                                           dgood, stream)
+        assert obj == want and np.array_equal(bw, want_bw)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("fault", ["offset_beyond_p", "pin_out_of_range"])
+def test_bad_csr_on_the_device_is_reported_and_the_next_call_is_clean(hg, oracle_mod, fault):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    hgr = synth.uniform_10k(2)
+    k = 8
+    stream = torch.cuda.current_stream()
+    p = len(hgr.pins)
+    off = np.array(hgr.offsets, np.int32)
+    pins = np.array(hgr.pins, np.int32)
+    if fault == "offset_beyond_p":
+        off[-1] = p + 1  # the last net would end past the pins
+    else:
+        pins[p // 3] = hgr.n  # a pin naming a node that does not exist
+    good = np.random.default_rng(5).integers(0, k, size=hgr.n).astype(np.int32)
+    dgood = _dev(good)
+    with pytest.raises(hg.HgError) as ei:
+        hg.hg_objective_noalloc(hgr.n, hgr.m, p, _dev(off), _dev(pins), None, None, k, dgood,
+                                stream)
+    assert ei.value.status == hg.HG_ERR_INVALID
+    want = oracle_mod.objective(
+        type(hgr)(hgr.n, hgr.m, hgr.offsets, hgr.pins, np.ones(hgr.m, np.int32),
+                  np.ones(hgr.n, np.int32)), k, good)
+    want_bw = np.bincount(good, minlength=k).astype(np.int64)
+    for _ in range(2):
+        obj, bw = hg.hg_objective_noalloc(hgr.n, hgr.m, p, _dev(hgr.offsets), _dev(hgr.pins), None,
+                                          None, k, dgood, stream)
         assert obj == want and np.array_equal(bw, want_bw)
