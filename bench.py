@@ -31,15 +31,11 @@ WORKLOAD = ("hypergraph n=m=1,000,000: Zipf(2.2) net sizes in [2,1024], preferen
             "5 LP passes per level, full V-cycle")
 L2_FLUSH_BYTES = 512 << 20
 
-# DRAM traffic of the rating kernels (k_rate_*), from one ncu capture of
-# every rating launch of the n = m = 1e6 Zipf hierarchy (dram__bytes_read.sum +
-# dram__bytes_write.sum, averaged per launch); see
-# profiles/rating_kernels_zipf1m.md.  Reported only while the source the
-# counters were taken from is unchanged.
-RATING_TRAFFIC = {
-    "source_sha256": "a287fb097f09f6ab0350291e81f9c9909269442bcf2dddbedc0c2c1a37287be7",
-    "bytes_per_launch": 20056204,
-}
+# DRAM traffic per launch of a kernel family (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture, averaged per launch), reported
+# only while the source the counters were taken from is unchanged; the
+# captures are summarised under profiles/.
+TRAFFIC = {}
 
 
 def _source_sha256(rel: str) -> str:
@@ -390,7 +386,229 @@ def run_gain_recalc(hg, torch, hgr, d_off, d_pins, d_w, d_c, opt, stream, part, 
     return out
 
 
+# ------------------------------------------------------------ byte model
+
+# Algorithmic bytes per level (4-byte ints, 8-byte Lambda, compulsory
+# traffic), phase by phase:
+#   rating      4(n+1) + 4p + 12 sum_e min(|e|, S) + 8 sum_{2<=|e|<=T} |e| min(|e|, S) + 24n
+#   approval    24 per accepted join (n - n')
+#   contraction 32p + 40m + 16n
+#   pin counts  8p + 8m
+#   LP pass     20p + 30n (best moves), plus 24 per incidence of a moved node
+#               (application)
+#   objective   12m
+# Rating, approval and contraction count on the levels that were coarsened;
+# the rest on every level.
+
+def level_accounting(hg, torch, hgr, k, opt, stream, S=16, T=1000):
+    """One untimed V-cycle, level by level, with the statistics reset per
+    level: sizes, the net-size sums of the rating term, LP passes and moved
+    incidences.  Results are deterministic, so these are the timed steps'."""
+    import numpy as np
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).cuda()
+    h = hg.hg_create(hgr.n, hgr.m, t(hgr.offsets), t(hgr.pins), t(hgr.net_w), t(hgr.node_w),
+                     hg.HG_MEM_DEVICE, opt, stream)
+    try:
+        while hg.hg_coarsen_level(h, k)[0] == hg.HG_OK:
+            pass
+        nl = hg.hg_num_levels(h)
+        lv = []
+        for l in range(nl):
+            n, m, p = hg.hg_level_info(h, l)
+            off = hg.hg_get_level(h, l)["offsets"].astype(np.int64)
+            sz = np.diff(off)
+            mn = np.minimum(sz, S)
+            rated = (sz >= 2) & (sz <= T)
+            lv.append({"n": n, "m": m, "p": p, "sum_min": int(mn.sum()),
+                       "sum_visit": int((sz[rated] * mn[rated]).sum())})
+        parts = [torch.empty(max(x["n"], 1), dtype=torch.int32, device="cuda") for x in lv]
+        hg.hg_initial_partition(h, nl - 1, k, parts[-1])
+        for l in range(nl - 1, -1, -1):
+            if l < nl - 1:
+                hg.hg_project(h, l + 1, parts[l + 1], parts[l])
+            hg.hg_reset_stats(h)
+            _, moves = hg.hg_lp_refine(h, l, k, EPS_PPM, PASSES, parts[l])
+            st = hg.hg_get_stats(h)
+            lv[l].update(passes=st["lp_passes"], moves=moves,
+                         moved_incidences=st["lp_moved_incidences"])
+    finally:
+        hg.hg_destroy(h)
+    return lv
+
+
+def byte_model(lv):
+    """Per-phase algorithmic bytes of one V-cycle step from level_accounting."""
+    b = dict(rating=0, approval=0, contraction=0, pin_counts=0, lp_gain=0, lp_apply=0, objective=0)
+    for l, x in enumerate(lv):
+        n, m, p = x["n"], x["m"], x["p"]
+        if l + 1 < len(lv):
+            b["rating"] += 4 * (n + 1) + 4 * p + 12 * x["sum_min"] + 8 * x["sum_visit"] + 24 * n
+            b["approval"] += 24 * (n - lv[l + 1]["n"])
+            b["contraction"] += 32 * p + 40 * m + 16 * n
+        b["pin_counts"] += 8 * p + 8 * m
+        b["lp_gain"] += x["passes"] * (20 * p + 30 * n)
+        b["lp_apply"] += 24 * x["moved_incidences"]
+        b["objective"] += 12 * m
+    b["total"] = sum(b.values())
+    return b
+
+
 # ------------------------------------------------------------ GPU path
+
+def load_mapping(hg, opt):
+    """Launch mapping chosen by paper_2303_17679_gb300.autotune for the Zipf
+    workload (results are identical under every mapping; only speed differs)."""
+    tuned_path = os.path.join(ROOT, "paper_2303_17679_gb300", "tuned_zipf1m_k8.json")
+    if not os.path.exists(tuned_path):
+        return "built-in defaults"
+    from paper_2303_17679_gb300 import autotune
+    with open(tuned_path) as f:
+        autotune.apply(opt, json.load(f))
+    return "autotuned (paper_2303_17679_gb300/tuned_zipf1m_k8.json)"
+
+
+def add_stats(agg, st):
+    for key, val in st.items():
+        if isinstance(val, list):
+            agg[key] = [a + b for a, b in zip(agg.get(key, [0] * len(val)), val)]
+        else:
+            agg[key] = agg.get(key, 0) + val
+
+
+def family_rooflines(agg, steps, bm, peak):
+    """Per-kernel-family achieved GB/s from the byte model and the families'
+    event-timed durations inside the timed steps."""
+    fam = {}
+    spec = [("rating", "k_rate_* (heavy-edge rating, a3)", "ms_rating_kernels", bm["rating"],
+             agg["rating_launches"]),
+            ("lp_gain", "k_lp_gain_* (LP best moves, a11; both branches of a sub-round)",
+             "ms_lp_gain_kernels", bm["lp_gain"], agg["lp_gain_launches"] // 2),
+            ("lp_select", "k_lp_select / k_lp_bucket (a12)", "ms_lp_select_kernels", None, None),
+            ("lp_apply", "k_lp_apply (a13)", "ms_lp_apply_kernels", bm["lp_apply"],
+             agg["lp_gain_launches"] // 2)]
+    for key, name, ms_key, nbytes, launches in spec:
+        ms = agg.get(ms_key, 0.0) / steps
+        rec = {"kernel": name, "ms_per_step": ms}
+        if nbytes is not None and ms > 0:
+            gbs = nbytes / (ms / 1e3) / 1e9
+            rec.update(alg_bytes_per_step=nbytes, achieved_gbs=gbs, frac=gbs / peak,
+                       launches_per_step=int(launches // steps),
+                       ms_per_launch=ms / max(1, launches // steps))
+        fam[key] = rec
+    return fam
+
+
+def timed_vcycle(hg, torch, hgr, k, opt, stream, steps, warmup, flush, instrumented=3):
+    """create (device CSR) + hg_partition + destroy, per-step CUDA events on
+    the library's stream, L2 flushed between steps.  The timed steps run
+    without per-kernel events; `instrumented` further steps with the kernel-
+    family events on (event pairs around every rating launch, event nodes
+    around every phase of the captured LP pass) give the family durations:
+    those events lengthen a step by about a tenth, so they stay out of the
+    headline steps."""
+    import numpy as np
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).cuda()
+    d = (t(hgr.offsets), t(hgr.pins), t(hgr.net_w), t(hgr.node_w))
+    part = torch.empty(hgr.n, dtype=torch.int32, device="cuda")
+
+    def step(kernel_events):
+        h = hg.hg_create(hgr.n, hgr.m, *d, hg.HG_MEM_DEVICE, opt, stream)
+        try:
+            if kernel_events:
+                hg.hg_enable_timing(h, 2)
+            obj = hg.hg_partition(h, k, EPS_PPM, PASSES, part)
+            levels = [hg.hg_level_info(h, i) for i in range(hg.hg_num_levels(h))]
+            return obj, levels, hg.hg_get_stats(h)
+        finally:
+            hg.hg_destroy(h)
+
+    def run(count, kernel_events):
+        ms, agg = [], {}
+        for _ in range(count):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            obj, levels, st = step(kernel_events)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            add_stats(agg, st)
+            results.append((obj, levels))
+        return ms, agg
+
+    results = []
+    for _ in range(warmup):
+        step(False)
+    step(True)
+    torch.cuda.synchronize()
+    step_ms, agg = run(steps, False)
+    instr_ms, iagg = run(instrumented, True)
+    assert all(r == results[0] for r in results), "non-deterministic result"
+    iagg["instrumented_steps"] = instrumented
+    iagg["instrumented_ms_per_step"] = statistics.mean(instr_ms) if instr_ms else None
+    return step_ms, agg, iagg, results[0][0], results[0][1], part
+
+
+def config1_line(hg, torch, stream, flush, peak, steps=20, warmup=5):
+    """n = m = 10,000 uniform hypergraph, k = 2: one clustering + contraction
+    step, seeded initial partition of the fine level, 5 LP passes on it."""
+    import numpy as np
+    import synth
+    hgr = synth.uniform_10k(SEED)
+    opt = hg.hg_default_options()
+    opt.seed = SEED
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).cuda()
+    d = (t(hgr.offsets), t(hgr.pins), t(hgr.net_w), t(hgr.node_w))
+    part = torch.empty(hgr.n, dtype=torch.int32, device="cuda")
+    ms, obj0 = [], None
+    for i in range(warmup + steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h = hg.hg_create(hgr.n, hgr.m, *d, hg.HG_MEM_DEVICE, opt, stream)
+        try:
+            hg.hg_coarsen_level(h, 2)
+            hg.hg_initial_partition(h, 0, 2, part)
+            obj, moves = hg.hg_lp_refine(h, 0, 2, EPS_PPM, PASSES, part)
+        finally:
+            hg.hg_destroy(h)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= warmup:
+            ms.append(e0.elapsed_time(e1))
+        obj0 = obj if obj0 is None else obj0
+        assert obj == obj0, "non-deterministic result"
+    t_ms = statistics.mean(ms)
+    return {"workload": "n=m=10,000 uniform hypergraph, 2 + Geom(0.3) <= 64 sizes, unit weights, k=2: "
+                        "create + one clustering/contraction step + initial partition + 5 LP passes "
+                        "on the fine level", "pins": hgr.p, "ms_per_step": t_ms,
+            "pins_per_s": hgr.p / (t_ms / 1e3), "objective": obj0,
+            "note": "launch-latency bound by design (about 2 MB of algorithmic bytes)"}
+
+
+def config3_line(hg, torch, stream, flush, peak, steps=2, warmup=1):
+    """n = 4e6, m = 2e6 large-net hypergraph, k = 64, full V-cycle."""
+    import synth
+    hgr = synth.large_net_4m(SEED)
+    opt = hg.hg_default_options()
+    opt.seed = SEED
+    step_ms, _, iagg, obj, levels, _ = timed_vcycle(hg, torch, hgr, 64, opt, stream, steps,
+                                                    warmup, flush, instrumented=1)
+    lv = level_accounting(hg, torch, hgr, 64, opt, stream)
+    bm = byte_model(lv)
+    t_ms = statistics.mean(step_ms)
+    pins = sum(p for (_, _, p) in levels)
+    fam = family_rooflines(iagg, 1, bm, peak)
+    return {"workload": "n=4e6, m=2e6: 99% nets 2 + Geom(0.3) <= 16, 1% of 1k-100k pins (x^-4), "
+                        "net 0 = 100k pins; unit node weights, net weights in [1, 100]; k=64, "
+                        "eps=0.03, T=1000, full V-cycle", "levels": len(levels),
+            "pins_per_step": pins, "ms_per_step": t_ms, "pins_per_s": pins / (t_ms / 1e3),
+            "objective": obj, "level_frac": bm["total"] / (t_ms / 1e3) / 1e9 / peak,
+            "alg_bytes_per_step": bm, "families": fam,
+            "instrumented_ms_per_step": iagg["instrumented_ms_per_step"], "level_sizes": [list(x) for x in levels]}
+
 
 def run_ours(args, world, rank, local):
     import numpy as np
@@ -407,46 +625,11 @@ def run_ours(args, world, rank, local):
     hgr = synth.zipf_1m(SEED)
     opt = hg.hg_default_options()
     opt.seed = SEED
-    # launch mapping chosen by paper_2303_17679_gb300.autotune for this workload
-    # (results are identical under every mapping; only the speed differs)
-    tuned_path = os.path.join(ROOT, "paper_2303_17679_gb300", "tuned_zipf1m_k8.json")
-    mapping = "built-in defaults"
-    if os.path.exists(tuned_path):
-        from paper_2303_17679_gb300 import autotune
-        with open(tuned_path) as f:
-            autotune.apply(opt, json.load(f))
-        mapping = "autotuned (paper_2303_17679_gb300/tuned_zipf1m_k8.json)"
-    t_in = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).cuda()
-    d_off, d_pins, d_w, d_c = t_in(hgr.offsets), t_in(hgr.pins), t_in(hgr.net_w), t_in(hgr.node_w)
+    mapping = load_mapping(hg, opt)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory()
     h_off, h_pins, h_w, h_c = pin(hgr.offsets), pin(hgr.pins), pin(hgr.net_w), pin(hgr.node_w)
-    part = torch.empty(hgr.n, dtype=torch.int32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
-
-    def step(kernel_events=False, host_inputs=False, phases=False):
-        if host_inputs:
-            h = hg.hg_create(hgr.n, hgr.m, h_off.numpy(), h_pins.numpy(), h_w.numpy(), h_c.numpy(),
-                             hg.HG_MEM_HOST, opt, stream)
-        else:
-            h = hg.hg_create(hgr.n, hgr.m, d_off, d_pins, d_w, d_c, hg.HG_MEM_DEVICE, opt, stream)
-        try:
-            if kernel_events or phases:
-                hg.hg_enable_timing(h, (2 if kernel_events else 0) | (1 if phases else 0))
-            obj = hg.hg_partition(h, K_BLOCKS, EPS_PPM, PASSES, part)
-            nl = hg.hg_num_levels(h)
-            levels = [hg.hg_level_info(h, i) for i in range(nl)]
-            stats = hg.hg_get_stats(h)
-            if host_inputs:
-                out = part.cpu()
-                assert out.shape[0] == hgr.n
-        finally:
-            hg.hg_destroy(h)
-        return obj, levels, stats
-
-    obj = levels = None
-    for _ in range(args.warmup):
-        obj, levels, _ = step()
-    torch.cuda.synchronize()
+    peak, peak_kind = peaks()
 
     # ---- device-resident timed region
     sampler = ClockSampler(local)
@@ -454,27 +637,8 @@ def run_ours(args, world, rank, local):
     barrier(world)
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    step_ms = []
-    launches = 0
-    agg = {}
-    for _ in range(args.steps):
-        flush.fill_(1)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        obj_k, lv_k, st = step(kernel_events=True)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        launches += st["launches"]
-        for key, val in st.items():
-            if isinstance(val, list):
-                agg[key] = [a + b for a, b in zip(agg.get(key, [0] * len(val)), val)]
-            else:
-                agg[key] = agg.get(key, 0) + val
-        if obj is None:
-            obj, levels = obj_k, lv_k
-        assert obj_k == obj and lv_k == levels, "non-deterministic result"
+    step_ms, agg, iagg, obj, levels, part = timed_vcycle(hg, torch, hgr, K_BLOCKS, opt, stream,
+                                                         args.steps, args.warmup, flush)
     torch.cuda.synchronize()
     barrier(world)
     pins_per_step = sum(p for (_, _, p) in levels)
@@ -483,52 +647,50 @@ def run_ours(args, world, rank, local):
     t_total = max_over_ranks(world, sum(step_ms) / 1e3)
     total_pins = sum_over_ranks(world, pins_per_step * args.steps)
     value = total_pins / t_total
+    launches = agg["launches"]
 
     # ---- end to end through the public API with host buffers
     e2e_ms = []
     for _ in range(0 if args.no_e2e else args.steps):
         flush.fill_(1)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        e0.record(stream)
-        step(host_inputs=True)
-        e1.record(stream)
-        e1.synchronize()
+        h = hg.hg_create(hgr.n, hgr.m, h_off.numpy(), h_pins.numpy(), h_w.numpy(), h_c.numpy(),
+                         hg.HG_MEM_HOST, opt, stream)
+        try:
+            hg.hg_partition(h, K_BLOCKS, EPS_PPM, PASSES, part)
+            out = part.cpu()
+            assert out.shape[0] == hgr.n
+        finally:
+            hg.hg_destroy(h)
+        torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_t = max_over_ranks(world, sum(e2e_ms) / 1e3) if e2e_ms else 0.0
     e2e_value = total_pins / e2e_t if e2e_ms else None
     h2d = 4 * (hgr.m + 1 + hgr.p + hgr.m + hgr.n)
     d2h = 4 * hgr.n
 
-    # ---- roofline of the dominant kernel family (per-launch events inside the timed region)
-    peak, peak_kind = peaks()
-    rating_ms = agg["ms_rating_kernels"]
-    gain_ms = agg["ms_lp_gain_kernels"]
-    # algorithmic bytes per unit: rating = 24 B per rated node (c, cluster weight
-    # and status, target, rep) + 16 B per incidence (net id, two offsets, weight)
-    # + 8 B per pin visit (pin, cluster); LP gain = 30 B per node + 20 B per
-    # incidence (net id, weight, Lambda, Phi(e, from))
-    gain_bytes = 30 * agg["lp_nodes"] + 20 * agg["lp_incidences"]
-    rating_bytes = (24 * agg["rating_nodes"] + 16 * agg["rating_incidences"]
-                    + 8 * agg["rating_pin_visits"])
+    # ---- byte model (untimed accounting pass) and rooflines
+    lv = level_accounting(hg, torch, hgr, K_BLOCKS, opt, stream)
+    bm = byte_model(lv)
+    ms_step = statistics.mean(step_ms)
+    ni = iagg["instrumented_steps"]
+    fam = family_rooflines(iagg, ni, bm, peak)
+    dom = max(("rating", "lp_gain"), key=lambda f: fam[f]["ms_per_step"])
+    d = fam[dom]
     traffic = None
-    if rating_ms >= gain_ms:
-        kname, kms, kbytes, klaunch = ("k_rate_* (heavy-edge rating)", rating_ms, rating_bytes,
-                                       agg["rating_launches"])
-        if (RATING_TRAFFIC["source_sha256"]
-                and RATING_TRAFFIC["source_sha256"]
-                == _source_sha256("paper_2303_17679_gb300/csrc/coarsen.cu")):
-            traffic = RATING_TRAFFIC["bytes_per_launch"]
-    else:
-        kname, kms, kbytes, klaunch = ("k_lp_gain (LP best moves)", gain_ms, gain_bytes,
-                                       agg["lp_gain_launches"])
-    achieved = (kbytes / (kms / 1e3)) / 1e9 if kms > 0 else 0.0
+    tref = TRAFFIC.get(dom)
+    if tref and tref["source_sha256"] == _source_sha256(tref["source"]):
+        traffic = tref["bytes_per_launch"]
+    u32_rate, u64_rate = hg.hg_calibrate_smem_atomics(stream)
+    rating_ms = iagg["ms_rating_kernels"] / ni
+    visits = iagg["rating_pin_visits"] / ni
+    visit_bytes = (24 * iagg["rating_nodes"] + 16 * iagg["rating_incidences"]
+                   + 8 * iagg["rating_pin_visits"]) / ni
 
     line = {
         "metric": METRIC, "value": value, "unit": "pins/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic (seeded generator: Zipf(2.2) net sizes, preferential pins, n=m=1e6)",
         "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
@@ -539,33 +701,65 @@ def run_ours(args, world, rank, local):
                 "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.mean(e2e_ms) if e2e_ms else None},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                     "peak_kind": peak_kind, "launches_per_step": int(klaunch // args.steps),
-                     "algorithmic_bytes_per_launch": kbytes / max(klaunch, 1),
-                     "ms_per_launch": kms / max(klaunch, 1),
-                     "share_of_step": kms / sum(step_ms)},
+        "roofline": {"bound": "hbm", "kernel": d["kernel"], "achieved": d.get("achieved_gbs", 0.0),
+                     "peak": peak, "unit": "GB/s", "frac": d.get("frac", 0.0), "traffic": traffic,
+                     "peak_kind": peak_kind + " (hbm_gbs, copy burst)",
+                     "bytes_model": "survey 8(d) per-phase formulas from per-level statistics",
+                     "durations": f"CUDA events on the library's stream over {ni} instrumented "
+                                  "steps run right after the timed steps (the per-kernel events "
+                                  "stay out of the headline steps)",
+                     "instrumented_ms_per_step": iagg["instrumented_ms_per_step"],
+                     "launches_per_step": d.get("launches_per_step"),
+                     "algorithmic_bytes_per_launch":
+                         d.get("alg_bytes_per_step", 0) / max(1, d.get("launches_per_step") or 1),
+                     "ms_per_launch": d.get("ms_per_launch"),
+                     "share_of_step": d["ms_per_step"] / ms_step,
+                     "level_frac": bm["total"] / (ms_step / 1e3) / 1e9 / peak,
+                     "alg_bytes_per_step": bm, "families": fam,
+                     "rating_visit_model": {
+                         "note": "24 B per rated node + 16 B per incidence + 8 B per pin visit "
+                                 "(visits are served from L2 and shared memory)",
+                         "bytes_per_step": visit_bytes,
+                         "achieved_gbs": visit_bytes / (rating_ms / 1e3) / 1e9 if rating_ms else None},
+                     "smem_atomics": {
+                         "bound": "rating table updates (one shared-memory atomic add per pin visit)",
+                         "visits_per_step": visits,
+                         "achieved_per_s": visits / (rating_ms / 1e3) if rating_ms else None,
+                         "peak_u32_per_s": u32_rate, "peak_u64_per_s": u64_rate,
+                         "peak_kind": "measured (hg_calibrate_smem_atomics, conflict-free adds)",
+                         "frac": (visits / (rating_ms / 1e3)) / u32_rate if rating_ms else None}},
         "clocks": clocks,
         "wall_s": wall,
-        "phase_ms": {"rating_kernels": rating_ms / args.steps, "lp_gain_kernels": gain_ms / args.steps},
+        "phase_ms": {"rating_kernels": rating_ms,
+                     "lp_gain_kernels": iagg["ms_lp_gain_kernels"] / ni,
+                     "lp_select_kernels": iagg["ms_lp_select_kernels"] / ni,
+                     "lp_apply_kernels": iagg["ms_lp_apply_kernels"] / ni,
+                     "timing_failures": int(iagg["timing_failures"]),
+                     "from": f"{ni} instrumented steps"},
         "work_per_step": {key: int(agg[key] // args.steps) for key in (
-            "rating_nodes", "rating_incidences", "rating_pin_visits", "lp_nodes", "lp_incidences")},
+            "rating_nodes", "rating_incidences", "rating_pin_visits", "lp_nodes", "lp_incidences",
+            "lp_moved_incidences", "lp_passes")},
         "rating_classes": [
-            {"class": c, "ms": round(agg["ms_rating_class"][c] / args.steps, 3),
-             "visits": int(agg["rating_visits_class"][c] // args.steps),
-             "Gvisits_per_s": round(agg["rating_visits_class"][c] / agg["ms_rating_class"][c] / 1e6, 2)
-             if agg["ms_rating_class"][c] > 0 else None}
+            {"class": c, "ms": round(iagg["ms_rating_class"][c] / ni, 3),
+             "visits": int(iagg["rating_visits_class"][c] // ni),
+             "Gvisits_per_s": round(iagg["rating_visits_class"][c] / iagg["ms_rating_class"][c] / 1e6, 2)
+             if iagg["ms_rating_class"][c] > 0 else None}
             for c in range(5)],
         "level_sizes": [list(x) for x in levels],
+        "unshrunk_levels": {
+            "note": "levels identical in size to the level they were contracted from (the 1 % "
+                    "rule keeps such a level and runs LP on it)",
+            "count": sum(1 for i in range(1, len(levels)) if levels[i] == levels[i - 1]),
+            "pins_per_step": sum(levels[i][2] for i in range(1, len(levels))
+                                 if levels[i] == levels[i - 1])},
     }
-    if args.phases:
-        # one extra, untimed step with synchronizing per-phase events
-        _, _, pst = step(phases=True)
-        line["phase_breakdown_ms"] = {k: round(v, 3) for k, v in pst.items()
-                                      if k.startswith("ms_") and not isinstance(v, list)}
+    if world == 1 and not args.no_configs:
+        line["config1"] = config1_line(hg, torch, stream, flush, peak)
+        line["config3"] = config3_line(hg, torch, stream, flush, peak)
     if world == 1:
-        line["gain_recalc"] = run_gain_recalc(hg, torch, hgr, d_off, d_pins, d_w, d_c, opt, stream,
-                                              part, peak)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).cuda()
+        line["gain_recalc"] = run_gain_recalc(hg, torch, hgr, t(hgr.offsets), t(hgr.pins),
+                                              t(hgr.net_w), t(hgr.node_w), opt, stream, part, peak)
     if world == 1 and not args.no_batch:
         line["batch"] = run_batch(hg, torch, args.slots)
     if world == 1 and args.serve_seconds > 0:
@@ -587,11 +781,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end steps")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batch comparison")
-    ap.add_argument("--serve-seconds", type=float, default=20.0,
-                    help="length of the Poisson serving run (0: skip; the workload states 60)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="length of the Poisson serving run (0: skip)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the n=m=1e4 and 4e6-node large-net sub-objects")
     ap.add_argument("--slots", type=int, default=16, help="executor slots for batch and serve")
-    ap.add_argument("--phases", action="store_true",
-                    help="add a per-phase breakdown from one extra, untimed step")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":

@@ -130,10 +130,16 @@ typedef struct {
   int64_t lp_nodes;           /* nodes evaluated by the gain kernels */
   int64_t lp_gain_launches;
   double ms_rating_kernels;   /* sum of rating kernel durations (timing on) */
-  double ms_lp_gain_kernels;  /* sum of gain kernel durations (timing on) */
+  double ms_lp_gain_kernels;  /* best-move kernel duration (timing flag 2; inside a captured
+                                 pass the two parallel branches count once) */
   double ms_rating_refresh;   /* per-sub-round refresh of the deduplicated pin clusters */
   double ms_rating_class[8];  /* rating kernel time per node class (timing flag 2) */
   int64_t rating_visits_class[8]; /* pin visits per node class */
+  double ms_lp_select_kernels; /* pair selection (and bucketing) duration (timing flag 2) */
+  double ms_lp_apply_kernels;  /* move application duration (timing flag 2) */
+  int64_t lp_moved_incidences; /* incident nets of the moved nodes */
+  int64_t lp_passes;           /* label-propagation passes run */
+  int64_t timing_failures;     /* kernel-timing event pairs that could not be read */
 } hg_stats;
 
 /* Fills *opt with the defaults listed above (seed 1). */
@@ -393,6 +399,13 @@ int hg_trim_memory(void);
 /* Frees everything the handle owns.  Safe on NULL and after any error.
  * Its blocks go back to the library's pool (see hg_options.dev_alloc). */
 int hg_destroy(hg_t* h);
+
+/* Measures the shared-memory atomic-add rate of the current device (the
+ * ceiling of the rating's table updates, Sec. 4.1): conflict-free 32-bit and
+ * 64-bit atomic adds over every SM, timed with CUDA events on cuda_stream;
+ * writes operations per second.  The paper has no counterpart.
+ * Synchronizes the stream. */
+int hg_calibrate_smem_atomics(void* cuda_stream, double* out_u32_per_s, double* out_u64_per_s);
 
 /* Static description of a status code. */
 const char* hg_strerror(int status);

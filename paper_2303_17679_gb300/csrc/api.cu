@@ -386,6 +386,11 @@ int hg_lp_refine(hg_t* h, int32_t level, int32_t k, int32_t eps_ppm, int32_t max
     h->stats.ms_lp_apply += rc.ms_apply;
     h->stats.ms_objective += rc.ms_objective;
     h->stats.ms_lp_gain_kernels += rc.ms_gain_kernels;
+    h->stats.ms_lp_select_kernels += rc.ms_select_kernels;
+    h->stats.ms_lp_apply_kernels += rc.ms_apply_kernels;
+    h->stats.lp_moved_incidences += rc.lp_moved_incidences;
+    h->stats.lp_passes += rc.lp_passes;
+    h->stats.timing_failures += rc.timing_failures;
     h->stats.lp_incidences += rc.lp_incidences;
     h->stats.lp_nodes += rc.lp_nodes;
     h->stats.lp_gain_launches += rc.lp_gain_launches;

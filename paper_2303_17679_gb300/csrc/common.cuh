@@ -333,9 +333,10 @@ void contract_level(const Ctx& cx, Level& L, const int32_t* cw, Level& out, int 
 // ------------------------------------------------------- refinement (refine.cu)
 
 struct RefineCounters {
-  int64_t lp_incidences = 0, lp_nodes = 0, lp_gain_launches = 0;
+  int64_t lp_incidences = 0, lp_nodes = 0, lp_gain_launches = 0, lp_moved_incidences = 0,
+          lp_passes = 0, timing_failures = 0;
   double ms_phi = 0, ms_gain = 0, ms_select = 0, ms_apply = 0, ms_objective = 0,
-         ms_gain_kernels = 0;
+         ms_gain_kernels = 0, ms_select_kernels = 0, ms_apply_kernels = 0;
 };
 
 void project_partition(const Ctx& cx, const Level& fine, const int32_t* coarse_part,

@@ -33,6 +33,7 @@ k_gt_build(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
   __shared__ long long s_cnt[GT_WARPS][HG_MAX_K];
   const int wv = warp_in_block(), lane = lane_id();
   long long* cnt = s_cnt[wv];
+  const unsigned long long kmask = k == 64 ? ~0ull : ((1ull << k) - 1ull);
   for (int i = lane; i < HG_MAX_K; i += 32) cnt[i] = 0;
   __syncwarp();
   for (int64_t u = (int64_t)blockIdx.x * GT_WARPS + wv; u < n; u += (int64_t)gridDim.x * GT_WARPS) {
@@ -41,25 +42,33 @@ k_gt_build(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
       if (lane == 0) dev_fail(status, DEV_BAD_INPUT);
       continue;
     }
-    long long bu = 0, wsum = 0;
+    // a net in more than k/2 blocks adds w(e) to `full` (every block) and
+    // takes it back from the blocks outside Lambda(e): at most k/2 atomics
+    long long bu = 0, wsum = 0, full = 0;
     for (int32_t j = ioff[u] + lane; j < ioff[u + 1]; j += 32) {
       const int32_t e = inets[j];
       const long long we = w[e];
       wsum += we;
       if (phi[(int64_t)e * k + pu] == 1) bu += we;
       unsigned long long le = lam[e];
+      unsigned long long delta = (unsigned long long)we;
+      if (2 * __popcll(le) > k) {
+        full += we;
+        le = ~le & kmask;
+        delta = (unsigned long long)(-we);
+      }
       while (le) {
-        atomicAdd(reinterpret_cast<unsigned long long*>(&cnt[__ffsll((long long)le) - 1]),
-                  (unsigned long long)we);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&cnt[__ffsll((long long)le) - 1]), delta);
         le &= le - 1;
       }
     }
     bu = warp_sum(bu);
     wsum = warp_sum(wsum);
+    full = warp_sum(full);
     __syncwarp();
     if (lane == 0) b[u] = bu;
     for (int i = lane; i < k; i += 32) {
-      p[u * k + i] = wsum - cnt[i];
+      p[u * k + i] = wsum - (cnt[i] + full);
       cnt[i] = 0;
     }
     __syncwarp();

@@ -161,14 +161,19 @@ enum SubroundWord { SW_MOVES = 0, SW_APPROVED = 1, SW_WORDS = 4 };
 // With b(u) = w(nets where u is the only pin of its block) and W_I = w(I(u)),
 // the gain of Sec. 6 is
 //   g(u, t) = b(u) - W_I + w({e in I(u) : t in Lambda(e)}),
-// evaluated for all t at once: every lane takes one incident net and adds
-// w(e) to the warp's shared counter of each block of Lambda(e), so the work
-// is the sum of lambda(e).  Counters are int32: the total net weight is
-// below 2^31.  A warp handles the chunks c0 = beg + 32 * (first + i * stride)
-// of I(u); acc0 / acc1 are filled from the counters of blocks lane and
-// lane + 32 by gain_collect.
+// evaluated for all t at once.  For k > 16 every lane takes one incident net
+// and adds w(e) to the warp's shared counter of each block of Lambda(e); a
+// net with lambda(e) > k/2 instead adds w(e) to a per-lane scalar `full` (a
+// term of every block's sum) and takes it back from the counters of the
+// blocks outside Lambda(e), so a net costs at most k/2 shared atomics (the
+// 1k-100k-pin nets of large-net inputs touch nearly every block).  Counters
+// are int32: every true sum is below 2^31 (the total net weight), and the
+// wrap-around of intermediate values cancels.  For k <= 16 the warp reduces
+// each block's sum directly.  A warp handles the chunks
+// c0 = beg + 32 * (first + i * stride) of I(u); acc0 / acc1 are filled from
+// the sums of blocks lane and lane + 32 by gain_collect.
 struct GainPart {
-  long long acc0, acc1, ben, wsum;
+  long long acc0, acc1, ben, wsum, full;
 };
 
 constexpr int GAIN_REDUCE_K = 16;
@@ -180,7 +185,8 @@ __device__ __forceinline__ GainPart gain_partial(const int32_t* __restrict__ ine
                                                  int from, int32_t beg, int32_t end, int first,
                                                  int stride, int32_t* s_cnt) {
   const int lane = lane_id();
-  GainPart g{0, 0, 0, 0};
+  const unsigned long long kmask = k == 64 ? ~0ull : ((1ull << k) - 1ull);
+  GainPart g{0, 0, 0, 0, 0};
   for (int32_t c0 = beg + 32 * first; c0 < end; c0 += 32 * stride) {
     const int32_t j = c0 + lane;
     int32_t we = 0;
@@ -200,8 +206,14 @@ __device__ __forceinline__ GainPart gain_partial(const int32_t* __restrict__ ine
         if (lane == t) g.acc0 += x;
       }
     } else {
+      int32_t delta = we;
+      if (2 * __popcll(le) > k) {
+        g.full += we;
+        le = ~le & kmask;
+        delta = -we;
+      }
       while (le) {
-        atomicAdd(&s_cnt[__ffsll((long long)le) - 1], we);
+        atomicAdd(&s_cnt[__ffsll((long long)le) - 1], delta);
         le &= le - 1;
       }
     }
@@ -209,14 +221,17 @@ __device__ __forceinline__ GainPart gain_partial(const int32_t* __restrict__ ine
   return g;
 }
 
-// Moves the warp's block counters into acc0 / acc1 and clears them (k above
-// GAIN_REDUCE_K; for smaller k the counts are in acc0 already).
+// Moves the warp's block counters plus its `full` sum into acc0 / acc1 and
+// clears the counters (k above GAIN_REDUCE_K; for smaller k the sums are in
+// acc0 already).
 __device__ __forceinline__ void gain_collect(GainPart& g, int32_t* s_cnt, int k) {
   if (k <= GAIN_REDUCE_K) return;
   const int lane = lane_id();
+  const long long full = warp_sum(g.full);
+  g.full = 0;
   __syncwarp();
-  g.acc0 = s_cnt[lane];
-  g.acc1 = s_cnt[lane + 32];
+  g.acc0 = (long long)s_cnt[lane] + full;
+  g.acc1 = (long long)s_cnt[lane + 32] + full;
   s_cnt[lane] = 0;
   s_cnt[lane + 32] = 0;
   __syncwarp();
@@ -337,7 +352,7 @@ __global__ void __launch_bounds__(GAIN_BLOCK_WARPS * 32) k_lp_gain_block(GainArg
     }
     __syncthreads();
     if (wv == 0) {
-      GainPart t{0, 0, 0, 0};
+      GainPart t{0, 0, 0, 0, 0};
       for (int x = 0; x < WARPS; ++x) {
         t.acc0 += s_acc[x][lane];
         t.acc1 += s_acc[x][lane + 32];
@@ -662,13 +677,14 @@ k_lp_apply(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
            long long* __restrict__ bw, unsigned long long* __restrict__ moved) {
   const int32_t na = words[SW_APPROVED];
   const int lane = lane_id();
-  unsigned long long nodes = 0;
+  unsigned long long nodes = 0, incid = 0;
   for (int32_t i = blockIdx.x * WARPS + warp_in_block(); i < na; i += gridDim.x * WARPS) {
     const int32_t u = ap_u[i];
     const int32_t fw = ap_from[i];
     const int s = fw & 63, ch = fw >> 6, t = ap_to[i];
     const int32_t j0 = ioff[u] + 32 * ch, j1 = min(ioff[u + 1], j0 + 32);
     const int32_t j = j0 + lane;
+    if (lane == 0 && j1 > j0) incid += (unsigned long long)(j1 - j0);
     if (j < j1) {
       const int32_t e = inets[j];
       if (atomicSub(&phi[(int64_t)e * k + s], 1) == 1) atomicXor(&lam[e], 1ull << s);
@@ -682,6 +698,7 @@ k_lp_apply(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
     }
   }
   if (lane == 0 && nodes) atomicAdd(moved, nodes);
+  if (lane == 0 && incid) atomicAdd(moved + 2, incid);
 }
 
 }  // namespace
@@ -804,8 +821,14 @@ struct PassGraphCache {
   cudaStream_t capture = nullptr;
   cudaStream_t side = nullptr;  // second branch of the captured pass
   cudaEvent_t fork = nullptr, join = nullptr;
+  // kernel timing: 4 events per sub-round recorded by event nodes of the
+  // captured pass (before the best-move kernels, after them, after the
+  // selection, after the application)
+  std::vector<cudaEvent_t> tev;
   cudaGraphExec_t exec = nullptr;
   void reset() {
+    for (cudaEvent_t e : tev) cudaEventDestroy(e);
+    tev.clear();
     if (exec) cudaGraphExecDestroy(exec);
     if (capture) cudaStreamDestroy(capture);
     if (side) cudaStreamDestroy(side);
@@ -836,6 +859,14 @@ struct PassGraphCache {
     }
     S = subrounds;
     return exec;
+  }
+  // At least `count` timing events (created with timing enabled).
+  void timing_events(size_t count) {
+    while (tev.size() < count) {
+      cudaEvent_t e = nullptr;
+      HG_CUDA(cudaEventCreate(&e));
+      tev.push_back(e);
+    }
   }
   ~PassGraphCache() { reset(); }
 };
@@ -896,7 +927,9 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   dfill.alloc(&cx.alloc, (size_t)S * kk);
   doff.alloc(&cx.alloc, (size_t)kk + 1);
   words.alloc(&cx.alloc, (size_t)S * SW_WORDS);
-  counters.alloc(&cx.alloc, 2);  // [0] moved in the pass, [1] incidences read
+  // [0] nodes moved in the pass, [1] incidences read by the gain kernels,
+  // [2] incidences of the moved nodes
+  counters.alloc(&cx.alloc, 4);
   HG_CUDA(cudaMemsetAsync(counters.p, 0, counters.bytes(), cx.stream));
 
   const int nodes_per_sr = (int)((n + S - 1) / S);
@@ -950,6 +983,14 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   // side != nullptr: the two best-move kernels of a sub-round are captured
   // as parallel branches (they only meet in atomics on the move list), so
   // the few high-degree nodes of the block class overlap with the warp class
+  // kernel timing inside the captured pass: event nodes around each phase
+  // of every sub-round, read after each pass (the pass ends with a host wait)
+  const bool graph_events = use_graph && cx.kernel_timing;
+  auto mark = [&](const PassGraphCache* fj, cudaStream_t sm, int s, int which) {
+    if (graph_events && fj)
+      HG_CUDA(cudaEventRecordWithFlags(fj->tev[(size_t)4 * s + which], sm,
+                                       cudaEventRecordExternal));
+  };
   auto enqueue_pass = [&](bool timed, cudaStream_t sm, const PassGraphCache* fj) {
     HG_CUDA(cudaMemsetAsync(sr_cnt.p, 0, sr_cnt.bytes(), sm));
     HG_CUDA(cudaMemsetAsync(sr_fill.p, 0, sr_fill.bytes(), sm));
@@ -978,6 +1019,7 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
       {
         EventTimer tm(cx, timed ? &rc.ms_gain : nullptr);
         if (fj) {
+          mark(fj, sm, s, 0);
           HG_CUDA(cudaEventRecord(fj->fork, sm));
           HG_CUDA(cudaStreamWaitEvent(fj->side, fj->fork, 0));
           k_lp_gain_block<<<g_gain_block, GAIN_BLOCK_WARPS * 32, 0, fj->side>>>(G);
@@ -986,6 +1028,7 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
           check_launch("lp_gain_warp");
           HG_CUDA(cudaEventRecord(fj->join, fj->side));
           HG_CUDA(cudaStreamWaitEvent(sm, fj->join, 0));
+          mark(fj, sm, s, 1);
         } else {
           if (timed) gain_timer.begin();
           k_lp_gain_warp<<<g_gain, WARPS * 32, 0, sm>>>(G);
@@ -996,7 +1039,7 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
           if (timed) gain_timer.end();
           check_launch("lp_gain_block");
         }
-        rc.lp_gain_launches += 2;
+        if (!fj) rc.lp_gain_launches += 2;
       }
       {
         EventTimer tm(cx, timed ? &rc.ms_select : nullptr);
@@ -1013,6 +1056,7 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
               lmax, k, gkeys.p, gpre.p, ap_u.p, ap_from.p, ap_to.p, w_s);
         }
         check_launch("lp_select");
+        mark(fj, sm, s, 2);
       }
       {
         EventTimer tm(cx, timed ? &rc.ms_apply : nullptr);
@@ -1020,14 +1064,18 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
                                                           ap_from.p, ap_to.p, w_s, part, st.phi.p,
                                                           st.lam.p, st.bw.p, counters.p);
         check_launch("lp_apply");
+        mark(fj, sm, s, 3);
       }
     }
     k_lp_next_pass<<<1, 1, 0, sm>>>(d_pass.p);
     check_launch("lp_next_pass");
   };
   cudaGraphExec_t exec = nullptr;
+  PassGraphCache* gcp = nullptr;
   if (use_graph && max_passes > 0) {
     PassGraphCache& gc = pass_graph_cache(cx);
+    gcp = &gc;
+    if (graph_events) gc.timing_events((size_t)4 * S);
     cudaGraph_t graph = nullptr;
     HG_CUDA(cudaStreamBeginCapture(gc.capture, cudaStreamCaptureModeThreadLocal));
     try {
@@ -1041,20 +1089,40 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
     exec = gc.bind(graph, S);
   }
   for (int pass = 0; pass < max_passes; ++pass) {
-    if (exec) HG_CUDA(cudaGraphLaunch(exec, cx.stream));
-    else enqueue_pass(true, cx.stream, nullptr);
+    if (exec) {
+      HG_CUDA(cudaGraphLaunch(exec, cx.stream));
+      rc.lp_gain_launches += 2 * S;
+    } else {
+      enqueue_pass(true, cx.stream, nullptr);
+    }
     if (cx.launches) *cx.launches += per_pass_launches;
-    unsigned long long hc[2];
+    unsigned long long hc[3];
     wait_stream(cx);  // the pass is done, so the graph is idle before its next update
     HG_CUDA(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, cx.stream));
     check_status(cx);
+    if (graph_events) {
+      double* acc[3] = {&rc.ms_gain_kernels, &rc.ms_select_kernels, &rc.ms_apply_kernels};
+      for (int s = 0; s < S; ++s)
+        for (int ph = 0; ph < 3; ++ph) {
+          float ms = 0;
+          if (cudaEventElapsedTime(&ms, gcp->tev[(size_t)4 * s + ph],
+                                   gcp->tev[(size_t)4 * s + ph + 1]) == cudaSuccess) {
+            *acc[ph] += ms;
+          } else {
+            cudaGetLastError();
+            rc.timing_failures += 1;
+          }
+        }
+    }
     res.passes = pass + 1;
     res.moves += (int64_t)hc[0];
     rc.lp_incidences += (int64_t)hc[1];
+    rc.lp_moved_incidences += (int64_t)hc[2];
     if (hc[0] == 0) break;
   }
   rc.ms_gain_kernels += gain_timer.flush();
   rc.lp_nodes += (int64_t)res.passes * n;
+  rc.lp_passes += res.passes;
   {
     EventTimer tm(cx, &rc.ms_objective);
     res.objective = objective_from_lambda(cx, L, st.lam.p);

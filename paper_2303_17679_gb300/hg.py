@@ -87,7 +87,10 @@ class hg_stats(ctypes.Structure):
             "rating_incidences", "lp_incidences", "lp_nodes", "lp_gain_launches")] + [
         ("ms_rating_kernels", ctypes.c_double), ("ms_lp_gain_kernels", ctypes.c_double),
         ("ms_rating_refresh", ctypes.c_double),
-        ("ms_rating_class", ctypes.c_double * 8), ("rating_visits_class", ctypes.c_int64 * 8)]
+        ("ms_rating_class", ctypes.c_double * 8), ("rating_visits_class", ctypes.c_int64 * 8),
+        ("ms_lp_select_kernels", ctypes.c_double), ("ms_lp_apply_kernels", ctypes.c_double),
+        ("lp_moved_incidences", ctypes.c_int64), ("lp_passes", ctypes.c_int64),
+        ("timing_failures", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}
@@ -145,6 +148,8 @@ def load(path: str | None = None):
             "hg_reset_stats": (ctypes.c_int, [H]),
             "hg_destroy": (ctypes.c_int, [H]),
             "hg_trim_memory": (ctypes.c_int, []),
+            "hg_calibrate_smem_atomics": (ctypes.c_int, [vp, P(ctypes.c_double),
+                                                         P(ctypes.c_double)]),
             "hg_exec_create": (ctypes.c_int, [i32, i64, P(hg_options), P(H)]),
             "hg_exec_submit": (ctypes.c_int, [H, P(hg_job), P(i64)]),
             "hg_exec_wait": (ctypes.c_int, [H, i32, i32, P(hg_job_result), P(i32)]),
@@ -168,7 +173,7 @@ def exported_symbols():
             "hg_level_info", "hg_initial_partition", "hg_project", "hg_lp_refine",
             "hg_objective", "hg_pin_counts", "hg_recalculate_gains", "hg_gain_table", "hg_gain_table_move",
             "hg_objective_noalloc", "hg_partition", "hg_get_level", "hg_get_incidence",
-            "hg_truncate", "hg_enable_timing", "hg_get_stats", "hg_reset_stats", "hg_destroy", "hg_trim_memory",
+            "hg_truncate", "hg_enable_timing", "hg_get_stats", "hg_reset_stats", "hg_destroy", "hg_trim_memory", "hg_calibrate_smem_atomics",
             "hg_exec_create", "hg_exec_submit", "hg_exec_wait", "hg_exec_pending",
             "hg_exec_now_ns", "hg_exec_destroy", "hg_strerror", "hg_version"]
 
@@ -392,6 +397,14 @@ def hg_reset_stats(h):
 def hg_destroy(h):
     if h:
         load().hg_destroy(h)
+
+
+def hg_calibrate_smem_atomics(stream=None):
+    """Shared-memory atomic adds per second (32-bit, 64-bit) on the current device."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().hg_calibrate_smem_atomics(_stream(stream), ctypes.byref(a), ctypes.byref(b)),
+           "hg_calibrate_smem_atomics")
+    return a.value, b.value
 
 
 def hg_trim_memory():

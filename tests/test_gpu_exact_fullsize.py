@@ -1,0 +1,224 @@
+"""Bit-exact parity with the oracle at full size and on the shapes that the
+smaller parity cases do not reach.
+
+* The n = m = 1e6 Zipf hypergraph (k = 8, in the launch mapping bench.py
+  times) and the n = 4e6 large-net hypergraph (k = 64): every level of the
+  GPU's V-cycle (canonical CSR, map to the next level, partition after label
+  propagation, objective, moves) against SHA-256 digests that
+  tests/golden/make_fullsize.py wrote by running only the oracle on the same
+  seeded inputs (Algorithm 1 with the deterministic rules of Sec. 11).
+* 36 of the 512 batch instances, through the executor as bench.py runs them,
+  against the oracle's objectives and partition digests (same script).
+* A hypergraph with one 100,000-pin net (n = 200,000, k = 64): the whole
+  V-cycle against the oracle, run here.
+* Two identical 9,000-pin nets (in different pin orders) and a third that
+  differs in one pin: the big-net remap and the exact identical-net
+  comparison of Sec. 4.2 against the oracle's contraction.
+All values are integers; every comparison is exact."""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2303_17679_gb300 import hg  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+GOLDEN = os.path.join(HERE, "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def digest(a) -> str:
+    return hashlib.sha256(np.ascontiguousarray(a, dtype="<i4").tobytes()).hexdigest()
+
+
+def load_golden(name):
+    path = os.path.join(GOLDEN, name)
+    with open(path) as f:
+        return json.load(f)
+
+
+def bench_options(tuned: bool):
+    """The options bench.py uses: defaults with seed 1, and for the Zipf
+    workload the committed autotuned launch mapping."""
+    opt = hg.hg_default_options()
+    opt.seed = 1
+    if tuned:
+        from paper_2303_17679_gb300 import autotune
+        with open(os.path.join(ROOT, "paper_2303_17679_gb300", "tuned_zipf1m_k8.json")) as f:
+            autotune.apply(opt, json.load(f))
+    return opt
+
+
+def gpu_vcycle_records(hgr, k, eps, passes, opt):
+    """Runs Algorithm 1 step by step through the C ABI and returns per-level
+    records in the golden file's form."""
+    stream = torch.cuda.current_stream()
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).cuda()
+    off, pins, w, c = t(hgr.offsets), t(hgr.pins), t(hgr.net_w), t(hgr.node_w)
+    h = hg.hg_create(hgr.n, hgr.m, off, pins, w, c, hg.HG_MEM_DEVICE, opt, stream)
+    del off, pins, w, c
+    try:
+        while hg.hg_coarsen_level(h, k)[0] == hg.HG_OK:
+            pass
+        nl = hg.hg_num_levels(h)
+        recs = []
+        for lv in range(nl):
+            got = hg.hg_get_level(h, lv, with_map=lv < nl - 1)
+            n, m, p = hg.hg_level_info(h, lv)
+            rec = {"n": n, "m": m, "p": p, "offsets": digest(got["offsets"]),
+                   "pins": digest(got["pins"]), "net_w": digest(got["net_w"]),
+                   "node_w": digest(got["node_w"])}
+            if lv < nl - 1:
+                rec["map"] = digest(got["map"])
+            recs.append(rec)
+        top = nl - 1
+        parts = [torch.empty(max(recs[lv]["n"], 1), dtype=torch.int32, device="cuda")
+                 for lv in range(nl)]
+        hg.hg_initial_partition(h, top, k, parts[top])
+        initial = hg.hg_objective(h, top, k, parts[top])
+        for lv in range(top, -1, -1):
+            if lv < top:
+                hg.hg_project(h, lv + 1, parts[lv + 1], parts[lv])
+            obj, moves = hg.hg_lp_refine(h, lv, k, eps, passes, parts[lv])
+            recs[lv]["objective"] = obj
+            recs[lv]["moves"] = moves
+            recs[lv]["part"] = digest(parts[lv][:recs[lv]["n"]].cpu().numpy())
+        return recs, initial
+    finally:
+        hg.hg_destroy(h)
+
+
+def compare_records(got, want):
+    assert len(got) == len(want), f"levels: gpu {len(got)} vs oracle {len(want)}"
+    for lv, (g, w) in enumerate(zip(got, want)):
+        for key in ("n", "m", "p", "offsets", "pins", "net_w", "node_w", "map", "objective",
+                    "moves", "part"):
+            if key in w:
+                assert g.get(key) == w[key], f"level {lv}: {key} differs (gpu {g.get(key)}, oracle {w[key]})"
+
+
+@pytest.mark.parametrize("name,maker,tuned", [
+    ("fullsize_zipf1m_k8.json", lambda: synth.zipf_1m(1), True),
+    ("fullsize_largenet4m_k64.json", lambda: synth.large_net_4m(1), False),
+])
+def test_fullsize_vcycle_matches_oracle_digests(name, maker, tuned):
+    want = load_golden(name)
+    hgr = maker()
+    assert want["seed"] == 1 and want["S"] == 16 and want["T"] == 1000 and want["factor"] == 160
+    recs, initial = gpu_vcycle_records(hgr, want["k"], want["eps_ppm"], want["max_passes"],
+                                       bench_options(tuned))
+    assert initial == want["initial_objective"]
+    compare_records(recs, want["levels"])
+
+
+def test_batch_subset_matches_oracle_digests():
+    want = load_golden("batch_subset.json")
+    jobs = synth.batch_instances(want["seed"])
+    ex = hg.Executor(slots=16)
+    try:
+        for rec in want["instances"]:
+            hgr, k = jobs[rec["index"]]
+            assert (hgr.n, hgr.p, k) == (rec["n"], rec["p"], rec["k"])
+            ex.submit(hgr, k, want["eps_ppm"], want["max_passes"], tag=rec["index"])
+        got = {}
+        while len(got) < len(want["instances"]):
+            for r in ex.wait():
+                got[r["tag"]] = r
+    finally:
+        ex.close()
+    ks = set()
+    for rec in want["instances"]:
+        r = got[rec["index"]]
+        assert r["status"] == hg.HG_OK
+        assert r["levels"] == rec["levels"], rec["index"]
+        assert r["objective"] == rec["objective"], rec["index"]
+        assert digest(r["part"]) == rec["part"], rec["index"]
+        ks.add(rec["k"])
+    assert ks == {2, 4, 8, 16, 32}
+
+
+def test_hundred_thousand_pin_net_vcycle(oracle_mod):
+    hgr = synth.large_net_stress(21, 200_000, 50_000, force_first=100_000, name="net100k")
+    assert hgr.offsets[1] - hgr.offsets[0] == 100_000
+    k, eps, passes, seed = 64, 30000, 2, 21
+    vc = oracle_mod.multilevel(hgr, k, eps, S=16, T=1000, factor=160, seed=seed,
+                               max_passes=passes)
+    opt = hg.hg_default_options()
+    opt.seed = seed
+    recs, initial = gpu_vcycle_records(hgr, k, eps, passes, opt)
+    want = []
+    for lv, L in enumerate(vc.levels):
+        w = {"n": L.n, "m": L.m, "p": L.p, "offsets": digest(L.offsets), "pins": digest(L.pins),
+             "net_w": digest(L.net_w), "node_w": digest(L.node_w), "part": digest(vc.parts[lv]),
+             "objective": vc.objectives[lv], "moves": vc.moves[lv]}
+        if lv < len(vc.maps):
+            w["map"] = digest(vc.maps[lv])
+        want.append(w)
+    assert initial == vc.initial_objective
+    compare_records(recs, want)
+
+
+def duplicated_big_nets(seed=23, n=60_000, m=40_000, size=9000):
+    """Random small nets plus three 9,000-pin nets: the second holds the
+    first's pins in reverse order (identical sets), the third replaces one
+    of them (a near duplicate)."""
+    base = synth.random_uniform(seed, n, m)
+    rng = np.random.default_rng(seed)
+    big = rng.choice(n, size=size, replace=False).astype(np.int32)
+    near = big.copy()
+    outside = np.setdiff1d(np.arange(n, dtype=np.int32), big)
+    near[size // 2] = outside[rng.integers(0, len(outside))]
+    extra = [big, big[::-1].copy(), near]
+    off = list(base.offsets.astype(np.int64))
+    for e in extra:
+        off.append(off[-1] + len(e))
+    pins = np.concatenate([base.pins] + extra).astype(np.int32)
+    w = np.concatenate([base.net_w, np.array([3, 5, 7], np.int32)])
+    return synth.Hypergraph(n, m + 3, np.asarray(off, np.int32), pins, w, base.node_w.copy(),
+                            "dup_big")
+
+
+@pytest.mark.parametrize("fp_bits", [0, 4])
+def test_duplicated_big_nets_merge_exactly(oracle_mod, fp_bits):
+    hgr = duplicated_big_nets()
+    k, seed = 2, 23
+    W = int(hgr.node_w.sum())
+    ref = oracle_mod.coarsen(hgr, W, k, 16, 1000, 160, seed, 0)
+    # the identical pair becomes one coarse net of weight 3 + 5, the near
+    # duplicate stays separate with weight 7
+    sizes = np.diff(ref["level"].offsets)
+    assert (ref["level"].net_w[sizes > 4096] == 8).sum() == 1
+    assert (ref["level"].net_w[sizes > 4096] == 7).sum() == 1
+    opt = hg.hg_default_options()
+    opt.seed = seed
+    opt.fingerprint_bits = fp_bits
+    stream = torch.cuda.current_stream()
+    h = hg.hg_create(hgr.n, hgr.m, hgr.offsets, hgr.pins, hgr.net_w, hgr.node_w, hg.HG_MEM_HOST,
+                     opt, stream)
+    try:
+        rc, lv, n2, m2, p2 = hg.hg_coarsen_level(h, k)
+        assert rc == hg.HG_OK
+        got0 = hg.hg_get_level(h, 0, with_map=True)
+        assert np.array_equal(got0["rep"], ref["rep"])
+        assert np.array_equal(got0["map"], ref["map"])
+        got = hg.hg_get_level(h, 1)
+        for key in ("offsets", "pins", "net_w", "node_w"):
+            assert np.array_equal(got[key], getattr(ref["level"], key)), key
+    finally:
+        hg.hg_destroy(h)
