@@ -135,7 +135,7 @@ typedef struct {
   double ms_rating_refresh;   /* per-sub-round refresh of the deduplicated pin clusters */
   double ms_rating_class[8];  /* rating kernel time per node class (timing flag 2) */
   int64_t rating_visits_class[8]; /* pin visits per node class */
-  double ms_lp_select_kernels; /* pair selection (and bucketing) duration (timing flag 2) */
+  double ms_lp_select_kernels; /* bucketing and pair selection duration (timing flag 2) */
   double ms_lp_apply_kernels;  /* move application duration (timing flag 2) */
   int64_t lp_moved_incidences; /* incident nets of the moved nodes */
   int64_t lp_passes;           /* label-propagation passes run */

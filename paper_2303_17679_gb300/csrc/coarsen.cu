@@ -16,16 +16,22 @@
 //            prefix that fits is accepted.
 //
 // Device state per level:
-//   rpin[q]  = rep[pins[q]] for the pins of rated nets (2 <= |e| <= T), with
-//              every repeat of a cluster inside its net replaced by -1, so a
-//              net contributes once per cluster without any per-visit check.
-//              At the start of a level every cluster is a singleton and rpin
-//              is a copy of the pins; after each sub-round the incidences of
-//              the nodes that joined a cluster update it through a map from
-//              (net, cluster) to the cluster's first pin index in the net.
+//   rinfo[q] = {cluster, weight word} for every pin position q:
+//              the cluster word is rep[pins[q]] for the pins of rated nets
+//              (2 <= |e| <= T), with every repeat of a cluster inside its net
+//              replaced by -1, so a net contributes once per cluster without
+//              any per-visit check (-1 for the pins of unrated nets too).  At
+//              the start of a level every cluster is a singleton and the word
+//              is the pin; after each sub-round the incidences of the nodes
+//              that joined a cluster update it through a map from (net,
+//              cluster) to the cluster's first pin index in the net.
+//              The weight word is refreshed before every sub-round by one
+//              streaming pass: the cluster's weight, or INT32_MAX when the
+//              cluster is an unclustered node of this sub-round (never a
+//              candidate).  A pin visit of the rating is then one coalesced
+//              8-byte load, with no dependent gather.
 //   cst[C]   = {cw[C], status[C]}: cluster weight and status (the node's
-//              sub-round while it is unclustered, -1 once clustered), read by
-//              the rating with one 8-byte load.
+//              sub-round while it is unclustered, -1 once clustered).
 // Nodes are bucketed per level by class and sub-round.  With W(u) = sum of
 // |e| over u's rated nets (the pins its rating visits) and D = min(W(u), n)
 // (a bound on its distinct candidates), a team accumulates u's ratings in a
@@ -90,7 +96,7 @@ struct RateArgs {
   const int32_t* ioff;
   const int32_t* inets;
   const int32_t* eoff;
-  const int32_t* rpin;
+  const int2* rinfo;  // {deduplicated cluster, weight or INT32_MAX} per pin position
   const unsigned long long* rterm;  // Q20 net term of every rated net, 0 otherwise
   const int32_t* c;
   const int2* cst;  // {cw, status}
@@ -235,23 +241,22 @@ __device__ __forceinline__ EachVisit<VT, F> each_visit(F f) {
 }
 
 // Filters a batch of pin positions (-1 = no visit) and hands it to `add`:
-// admissible C is not u, not an unclustered node of this sub-round, and fits
-// c_max.
+// admissible C is not u, not an unclustered node of this sub-round (weight
+// word INT32_MAX), and fits c_max.
 template <typename VT, typename Add>
 __device__ __forceinline__ void visit_filtered(const RateArgs& A, int32_t u, int32_t cu,
                                                const int32_t (&q)[RATE_ILP],
                                                const VT (&rr)[RATE_ILP], Add& add) {
+  int2 ri[RATE_ILP];
+#pragma unroll
+  for (int k = 0; k < RATE_ILP; ++k) ri[k] = q[k] >= 0 ? A.rinfo[q[k]] : make_int2(-1, 0);
   int32_t C[RATE_ILP];
-#pragma unroll
-  for (int k = 0; k < RATE_ILP; ++k) C[k] = q[k] >= 0 ? A.rpin[q[k]] : -1;
-  int2 cs[RATE_ILP];
-#pragma unroll
-  for (int k = 0; k < RATE_ILP; ++k)
-    cs[k] = (C[k] >= 0 && C[k] != u) ? A.cst[C[k]] : make_int2(0x7fffffff, 0);
   bool ok[RATE_ILP];
 #pragma unroll
-  for (int k = 0; k < RATE_ILP; ++k)
-    ok[k] = cs[k].y != A.s && (long long)cs[k].x + cu <= (long long)A.c_max;
+  for (int k = 0; k < RATE_ILP; ++k) {
+    C[k] = ri[k].x;
+    ok[k] = C[k] >= 0 && C[k] != u && (long long)ri[k].y + cu <= (long long)A.c_max;
+  }
   add(C, rr, ok);
 }
 
@@ -729,20 +734,16 @@ k_rate_part(RateArgs A, const int32_t* __restrict__ split, const int32_t* __rest
     // this one
     int32_t* nused = &s_nused[it & 1];
     auto visit = [&](const int32_t(&q)[RATE_ILP], const VT(&rr)[RATE_ILP]) HG_INLINE {
-      int32_t C[RATE_ILP];
+      int2 ri[RATE_ILP];
 #pragma unroll
-      for (int j = 0; j < RATE_ILP; ++j) C[j] = q[j] >= 0 ? A.rpin[q[j]] : -1;
-      bool own[RATE_ILP];
-#pragma unroll
-      for (int j = 0; j < RATE_ILP; ++j)
-        own[j] = C[j] >= 0 && C[j] != u && (P == 1 || part_of(C[j], P) == k);
-      int2 cs[RATE_ILP];
-#pragma unroll
-      for (int j = 0; j < RATE_ILP; ++j) cs[j] = own[j] ? A.cst[C[j]] : make_int2(0x7fffffff, 0);
+      for (int j = 0; j < RATE_ILP; ++j) ri[j] = q[j] >= 0 ? A.rinfo[q[j]] : make_int2(-1, 0);
 #pragma unroll
       for (int j = 0; j < RATE_ILP; ++j) {
-        if (!own[j] || cs[j].y == A.s || (long long)cs[j].x + cu > (long long)A.c_max) continue;
-        const int32_t sl = tab.add(C[j], rr[j]);
+        const int32_t Cj = ri[j].x;
+        if (Cj < 0 || Cj == u || (P != 1 && part_of(Cj, P) != k) ||
+            (long long)ri[j].y + cu > (long long)A.c_max)
+          continue;
+        const int32_t sl = tab.add(Cj, rr[j]);
         if (sl >= 0) {
           const int32_t x = atomicAdd(nused, 1);
           if (x < (int32_t)CAP) used[x] = sl;
@@ -1205,15 +1206,16 @@ __global__ void k_finish(const int32_t* __restrict__ touched, const int32_t* __r
   }
 }
 
-// ------------------------------------------------- rpin maintenance
+// ------------------------------------------ cluster word maintenance
 
 // The first position of every cluster in every rated net is kept in a global
 // hash map keyed by (net, cluster): at the start of a level every pin is its
 // own cluster, so the map holds (e, pins[q]) -> q for all rated pins.  When a
 // node v joins cluster C, for each rated net e of v at pin index q: an
 // atomicMin of q into (e, C) finds whether q becomes C's first position in e
-// (then the position it displaces, if any, is set to -1 in rpin) and, in a
-// second pass, rpin[q] = C if q is the first position of C in e, else -1.
+// (then the position it displaces, if any, gets cluster word -1 in rinfo)
+// and, in a second pass, the cluster word of q becomes C if q is the first
+// position of C in e, else -1.
 // The work per sub-round is the degree of the nodes that joined.
 struct PosMap {
   unsigned long long* key;  // net << 32 | cluster, all ones when empty
@@ -1270,14 +1272,15 @@ struct SubRanges {
 // Pass 1 (JOIN): for a rated incidence (u, e) of a node that joined C, insert
 // (e, C), lower its first position to q and clear the position it displaced;
 // the map slot is kept for pass 2 (all ones for an unrated net).
-// Pass 2: rpin[q] = C where q is now C's first position in the net, else -1.
+// Pass 2: cluster word of q = C where q is now C's first position in the
+// net, else -1.  `rx` is the cluster word of the rinfo records (stride 2).
 template <bool JOIN>
 __global__ void __launch_bounds__(256)
 k_posmap_pass(const int32_t* __restrict__ list, const int32_t* __restrict__ lpre, SubRanges R,
               const int32_t* __restrict__ rep, const int32_t* __restrict__ ioff,
               const int32_t* __restrict__ inets, const int32_t* __restrict__ ipin,
               const int32_t* __restrict__ eoff, int T, PosMap M, uint32_t* __restrict__ jslot,
-              int32_t* __restrict__ rpin, int32_t* status) {
+              int32_t* __restrict__ rx, int32_t* status) {
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gs = (int64_t)gridDim.x * blockDim.x;
 #pragma unroll 1
@@ -1310,7 +1313,7 @@ k_posmap_pass(const int32_t* __restrict__ list, const int32_t* __restrict__ lpre
           } else {
             slot = (uint32_t)sl;
             const int32_t old = atomicMin(&M.pos[sl], q);
-            if (old != 0x7fffffff && q < old) rpin[old] = -1;  // the displaced first position
+            if (old != 0x7fffffff && q < old) rx[2 * (int64_t)old] = -1;  // the displaced first position
           }
         }
         jslot[j] = slot;
@@ -1318,9 +1321,58 @@ k_posmap_pass(const int32_t* __restrict__ list, const int32_t* __restrict__ lpre
         const uint32_t sl = jslot[j];
         if (sl == ~0u) continue;
         const int32_t q = ipin[j];
-        rpin[q] = M.pos[sl] == q ? C : -1;
+        rx[2 * (int64_t)q] = M.pos[sl] == q ? C : -1;
       }
     }
+  }
+}
+
+// rinfo at the start of a level: cluster word = the pin for the pins of
+// rated nets, -1 for the others (pin tiles).
+__global__ void __launch_bounds__(PIN_TILE_THREADS)
+k_rinfo_init(const int32_t* __restrict__ eoff, const int32_t* __restrict__ pins,
+             const int32_t* __restrict__ tile_net, int32_t m, int64_t p, int T,
+             int2* __restrict__ rinfo) {
+  __shared__ int32_t s_off[PIN_TILE + 3];
+  const int64_t ntiles = num_pin_tiles(p);
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    PinTileView v = stage_pin_tile(eoff, tile_net, m, p, t, s_off);
+    for (int64_t q = v.q0 + threadIdx.x; q < v.q1; q += blockDim.x) {
+      const int32_t i = net_in_tile(s_off, v.count, q);
+      const int32_t sz = s_off[i + 1] - s_off[i];
+      rinfo[q] = make_int2(sz >= 2 && sz <= T ? pins[q] : -1, 0);
+    }
+    __syncthreads();
+  }
+}
+
+// Weight words of every record before sub-round s: the cluster's weight, or
+// INT32_MAX for an unclustered node of sub-round s.  Two records per thread
+// and iteration (16-byte loads and stores).
+__global__ void k_rinfo_refresh(int2* __restrict__ rinfo, int64_t p, const int2* __restrict__ cst,
+                                int s) {
+  const int64_t pairs = p >> 1;
+  int4* r4 = reinterpret_cast<int4*>(rinfo);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < pairs; i += stride) {
+    int4 r = r4[i];
+    if (r.x >= 0) {
+      const int2 cs = cst[r.x];
+      r.y = cs.y == s ? 0x7fffffff : cs.x;
+    }
+    if (r.z >= 0) {
+      const int2 cs = cst[r.z];
+      r.w = cs.y == s ? 0x7fffffff : cs.x;
+    }
+    r4[i] = r;
+  }
+  if ((p & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    int2 r = rinfo[p - 1];
+    if (r.x >= 0) {
+      const int2 cs = cst[r.x];
+      r.y = cs.y == s ? 0x7fffffff : cs.x;
+    }
+    rinfo[p - 1] = r;
   }
 }
 
@@ -1475,7 +1527,8 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   cw_out.alloc(&cx.alloc, (size_t)n);
   DBuf<int2> cst;
   DBuf<int32_t> target, gw, gcnt, slot_of, slot_c, slot_off, slot_fill, mv, touched, glist, key_of,
-      wof, kcount, kfill, list, words, clusters, rpin;
+      wof, kcount, kfill, list, words, clusters;
+  DBuf<int2> rinfo;
   DBuf<unsigned long long> stats, max_r;
   const size_t ncap = (size_t)n + 1;
   cst.alloc(&cx.alloc, ncap);
@@ -1498,7 +1551,7 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   clusters.alloc(&cx.alloc, 1);
   max_r.alloc(&cx.alloc, 1);
   stats.alloc(&cx.alloc, (size_t)ST_WORDS * NCLASS);
-  rpin.alloc(&cx.alloc, (size_t)std::max<int64_t>(L.p, 1));
+  rinfo.alloc(&cx.alloc, (size_t)std::max<int64_t>(L.p, 1));
   HG_CUDA(cudaMemsetAsync(gw.p, 0, gw.bytes(), cx.stream));
   HG_CUDA(cudaMemsetAsync(gcnt.p, 0, gcnt.bytes(), cx.stream));
   HG_CUDA(cudaMemsetAsync(slot_fill.p, 0, slot_fill.bytes(), cx.stream));
@@ -1508,9 +1561,15 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   HG_CUDA(cudaMemsetAsync(max_r.p, 0, max_r.bytes(), cx.stream));
   HG_CUDA(cudaMemsetAsync(stats.p, 0, stats.bytes(), cx.stream));
   HG_CUDA(cudaMemcpyAsync(clusters.p, &n, sizeof(int32_t), cudaMemcpyHostToDevice, cx.stream));
-  if (L.p > 0)
-    HG_CUDA(cudaMemcpyAsync(rpin.p, L.pins.p, sizeof(int32_t) * (size_t)L.p,
-                            cudaMemcpyDeviceToDevice, cx.stream));
+  DBuf<int32_t> tiles;
+  if (L.p > 0) {
+    tiles.alloc(&cx.alloc, (size_t)num_pin_tiles(L.p) + 1);
+    build_tile_index(cx, L.eoff.p, L.m, L.p, tiles.p);
+    k_rinfo_init<<<grid_for(num_pin_tiles(L.p), 1, cx.num_sms, 8), PIN_TILE_THREADS, 0,
+                   cx.stream>>>(L.eoff.p, L.pins.p, tiles.p, L.m, L.p, P.T, rinfo.p);
+    check_launch("rinfo_init");
+    if (cx.launches) *cx.launches += 1;
+  }
 
   const int g_nodes = grid_for(n, 256, cx.num_sms, 4);
   k_init_cluster<<<g_nodes, 256, 0, cx.stream>>>(L.c.p, n, P.seed, P.level, S, L.rep.p, cst.p,
@@ -1649,8 +1708,6 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
     pm.key = pm_key.p;
     pm.pos = pm_pos.p;
     pm.mask = cap - 1;
-    DBuf<int32_t> tiles;
-    tiles.alloc(&cx.alloc, (size_t)num_pin_tiles(L.p) + 1);
     const int32_t nlisted = hoff[nkeys];
     lpre.alloc(&cx.alloc, (size_t)nlisted + 1);
     EventTimer tm(cx, &cc.ms_refresh);
@@ -1660,7 +1717,6 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
       check_launch("list_degree");
     }
     scan_exclusive_i32(cx, lpre.p, lpre.p, nlisted, lpre.p + nlisted);
-    build_tile_index(cx, L.eoff.p, L.m, L.p, tiles.p);
     k_posmap_init<<<grid_for(num_pin_tiles(L.p), 1, cx.num_sms, 8), PIN_TILE_THREADS, 0,
                     cx.stream>>>(L.eoff.p, L.pins.p, tiles.p, L.m, L.p, P.T, pm, cx.d_status);
     check_launch("posmap_init");
@@ -1671,7 +1727,7 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   A.ioff = L.ioff.p;
   A.inets = L.inets.p;
   A.eoff = L.eoff.p;
-  A.rpin = rpin.p;
+  A.rinfo = rinfo.p;
   A.rterm = rterm.p;
   A.c = L.c.p;
   A.cst = cst.p;
@@ -1693,6 +1749,13 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
     A.s = s;
     A.words = words.p + (size_t)s * CW_WORDS;
     int32_t* w_s = words.p + (size_t)s * CW_WORDS;
+    if (L.p > 0) {
+      EventTimer tm(cx, &cc.ms_refresh);
+      k_rinfo_refresh<<<grid_for(L.p / 2 + 1, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(
+          rinfo.p, L.p, cst.p, s);
+      check_launch("rinfo_refresh");
+      if (cx.launches) *cx.launches += 1;
+    }
     {
       EventTimer tm(cx, &cc.ms_rating);
       const int64_t before = cc.rating_launches;
@@ -1732,11 +1795,13 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
       const int g = cx.num_sms * 8;
       k_posmap_pass<true><<<g, 256, 0, cx.stream>>>(list.p, lpre.p, R, L.rep.p, L.ioff.p,
                                                     L.inets.p, L.ipin.p, L.eoff.p, P.T, pm,
-                                                    jslot.p, rpin.p, cx.d_status);
+                                                    jslot.p, reinterpret_cast<int32_t*>(rinfo.p),
+                                                    cx.d_status);
       check_launch("posmap_join");
       k_posmap_pass<false><<<g, 256, 0, cx.stream>>>(list.p, lpre.p, R, L.rep.p, L.ioff.p,
                                                      L.inets.p, L.ipin.p, L.eoff.p, P.T, pm,
-                                                     jslot.p, rpin.p, cx.d_status);
+                                                     jslot.p, reinterpret_cast<int32_t*>(rinfo.p),
+                                                    cx.d_status);
       check_launch("posmap_fix");
       if (cx.launches) *cx.launches += 2;
     }

@@ -8,7 +8,11 @@
 // sub-round is four launches for k <= 16 and five above: best moves of the
 // warp and block node classes (a11, parallel branches of the captured
 // pass), bucketing by block pair (k > 16 only), per-pair prefix selection
-// (a12), application (a13).
+// (a12), application (a13).  Every move carries its source block, and the
+// selection reads the block weights of the sub-round's start as the pass's
+// starting weights plus the changes of its earlier sub-rounds, so nothing a
+// kernel of the sub-round reads is changed by another one before the
+// application.
 #include <climits>
 #include <mutex>
 
@@ -149,10 +153,6 @@ __global__ void k_lp_scatter(const int32_t* __restrict__ ioff, int32_t n, uint64
   }
 }
 
-// Advances the pass index read by k_lp_count / k_lp_scatter (the last launch
-// of a pass, so one captured pass can be replayed).
-__global__ void k_lp_next_pass(int32_t* d_pass) { *d_pass += 1; }
-
 // Per sub-round bookkeeping words.
 enum SubroundWord { SW_MOVES = 0, SW_APPROVED = 1, SW_WORDS = 4 };
 
@@ -278,7 +278,7 @@ struct GainArgs {
   const int32_t* sr_off;
   int s;
   int32_t* mv_u;
-  int32_t* mv_to;
+  int32_t* mv_to;  // target | source << 8
   long long* mv_g;
   int32_t* dcount;
   int32_t* words;
@@ -290,7 +290,7 @@ __device__ __forceinline__ void gain_emit(const GainArgs& A, int32_t u, int from
   if (g > 0) {
     const int32_t slot = atomicAdd(&A.words[SW_MOVES], 1);
     A.mv_u[slot] = u;
-    A.mv_to[slot] = t;
+    A.mv_to[slot] = t | (from << 8);  // target block, source block above bit 8
     A.mv_g[slot] = g;
     atomicAdd(&A.dcount[from * A.k + t], 1);
   }
@@ -405,8 +405,7 @@ __device__ void direction_offsets(const int32_t* dcount, int kk, int32_t* s_doff
   __syncthreads();
 }
 
-__global__ void k_lp_bucket(const int32_t* __restrict__ mv_u, const int32_t* __restrict__ mv_to,
-                            const int32_t* __restrict__ part, int k,
+__global__ void k_lp_bucket(const int32_t* __restrict__ mv_to, int k,
                             const int32_t* __restrict__ dcount, int32_t* __restrict__ dfill,
                             int32_t* __restrict__ doff, const int32_t* __restrict__ words,
                             int32_t* __restrict__ bucket) {
@@ -420,7 +419,7 @@ __global__ void k_lp_bucket(const int32_t* __restrict__ mv_u, const int32_t* __r
   for (int32_t b = blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < nm; b += stride) {
     const int32_t i = b + lane_id();
     const bool valid = i < nm;
-    const int d = valid ? part[mv_u[i]] * k + mv_to[i] : -1;
+    const int d = valid ? (mv_to[i] >> 8) * k + (mv_to[i] & 0xff) : -1;
     const int32_t slot = warp_claim_slot(dfill, d, __ballot_sync(FULL, valid));
     if (slot >= 0) bucket[s_doff[d] + slot] = i;
   }
@@ -500,15 +499,18 @@ __device__ void block_weight_prefix(const unsigned long long* keys, int cnt,
 // direction too long for shared memory are summed from dcount.
 template <bool GATHER>
 __global__ void __launch_bounds__(SEL_THREADS)
-k_lp_select(const int32_t* __restrict__ ioff, const int32_t* __restrict__ bucket,
-            const int32_t* __restrict__ doff,
+k_lp_select(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
+            const int32_t* __restrict__ bucket, const int32_t* __restrict__ doff,
             const int32_t* __restrict__ dcount, const int32_t* __restrict__ mv_u,
             const int32_t* __restrict__ mv_to, const long long* __restrict__ mv_g,
-            const int32_t* __restrict__ part,
-            const int32_t* __restrict__ c, const long long* __restrict__ bw, long long lmax, int k,
+            const int32_t* __restrict__ c, const long long* __restrict__ bw_base,
+            long long* __restrict__ dbw, int s, long long lmax, int k,
             unsigned long long* __restrict__ gkeys, long long* __restrict__ gpre,
-            int32_t* __restrict__ ap_u, int32_t* __restrict__ ap_from,
-            int32_t* __restrict__ ap_to, int32_t* __restrict__ words) {
+            const int32_t* __restrict__ words, int32_t* __restrict__ part,
+            int32_t* __restrict__ phi, unsigned long long* __restrict__ lam,
+            unsigned long long* __restrict__ moved, int32_t* __restrict__ ap_u,
+            int32_t* __restrict__ ap_from, int32_t* __restrict__ ap_to,
+            int32_t* __restrict__ ap_count) {
   extern __shared__ __align__(16) unsigned long long sel_smem[];
   const int cap = sel_cap_for(k);
   unsigned long long* s_keys0 = sel_smem;
@@ -569,27 +571,36 @@ k_lp_select(const int32_t* __restrict__ ioff, const int32_t* __restrict__ bucket
   if constexpr (GATHER) {
     const int32_t nm = words[SW_MOVES];
     const unsigned below = (1u << lane_id()) - 1u;
-    for (int32_t b0 = 0; b0 < nm; b0 += blockDim.x) {
-      const int32_t i = b0 + threadIdx.x;
-      bool in_a = false, in_b = false;
-      unsigned long long key = 0;
-      if (i < nm) {
-        const int32_t u = mv_u[i];
-        const int t = mv_to[i], s = part[u];
-        in_a = s == a && t == b;
-        in_b = s == b && t == a;
-        if (in_a || in_b) key = sel_key(mv_g[i], u);
+    // GATHER_ILP moves per thread and round: their directions are loaded
+    // before any is classified (only the pair's own moves load the rest)
+    constexpr int GATHER_ILP = 4;
+    for (int32_t b0 = 0; b0 < nm; b0 += GATHER_ILP * blockDim.x) {
+      int32_t dir[GATHER_ILP];
+#pragma unroll
+      for (int x = 0; x < GATHER_ILP; ++x) {
+        const int32_t i = b0 + x * blockDim.x + threadIdx.x;
+        dir[x] = i < nm ? mv_to[i] : -1;
       }
-      const unsigned ma = __ballot_sync(FULL, in_a), mb = __ballot_sync(FULL, in_b);
-      int base_a = 0, base_b = 0;
-      if (lane_id() == 0) {
-        if (ma) base_a = atomicAdd(&s_gat[2], __popc(ma));
-        if (mb) base_b = atomicAdd(&s_gat[3], __popc(mb));
+#pragma unroll
+      for (int x = 0; x < GATHER_ILP; ++x) {
+        const int32_t i = b0 + x * blockDim.x + threadIdx.x;
+        const int t = dir[x] & 0xff, src = dir[x] >> 8;
+        const bool in_a = dir[x] >= 0 && src == a && t == b;
+        const bool in_b = dir[x] >= 0 && src == b && t == a;
+        unsigned long long key = 0;
+        if (in_a || in_b) key = sel_key(mv_g[i], mv_u[i]);
+        const unsigned ma = __ballot_sync(FULL, in_a), mb = __ballot_sync(FULL, in_b);
+        if ((ma | mb) == 0) continue;
+        int base_a = 0, base_b = 0;
+        if (lane_id() == 0) {
+          if (ma) base_a = atomicAdd(&s_gat[2], __popc(ma));
+          if (mb) base_b = atomicAdd(&s_gat[3], __popc(mb));
+        }
+        base_a = __shfl_sync(FULL, base_a, 0);
+        base_b = __shfl_sync(FULL, base_b, 0);
+        if (in_a) ka[base_a + __popc(ma & below)] = key;
+        if (in_b) kb[base_b + __popc(mb & below)] = key;
       }
-      base_a = __shfl_sync(FULL, base_a, 0);
-      base_b = __shfl_sync(FULL, base_b, 0);
-      if (in_a) ka[base_a + __popc(ma & below)] = key;
-      if (in_b) kb[base_b + __popc(mb & below)] = key;
     }
     for (int i = na + threadIdx.x; i < Pa; i += blockDim.x) ka[i] = ~0ull;
     for (int i = nb + threadIdx.x; i < Pb; i += blockDim.x) kb[i] = ~0ull;
@@ -617,8 +628,19 @@ k_lp_select(const int32_t* __restrict__ ioff, const int32_t* __restrict__ bucket
   block_weight_prefix(ka, na, c, A, s_red);
   block_weight_prefix(kb, nb, c, B, s_red);
 
-  const long long slack_a = (lmax - bw[a] > 0 ? lmax - bw[a] : 0) / (k - 1);
-  const long long slack_b = (lmax - bw[b] > 0 ? lmax - bw[b] : 0) / (k - 1);
+  // block weights at the start of sub-round s: the pass's starting weights
+  // plus the changes applied in its earlier sub-rounds (pair blocks of this
+  // sub-round add theirs to dbw[s] only, so every block reads the same)
+  __shared__ long long s_w[2];
+  if (threadIdx.x < 2) {
+    const int blk = threadIdx.x == 0 ? a : b;
+    long long wv = bw_base[blk];
+    for (int x = 0; x < s; ++x) wv += dbw[(size_t)x * k + blk];
+    s_w[threadIdx.x] = wv;
+  }
+  __syncthreads();
+  const long long slack_a = (lmax - s_w[0] > 0 ? lmax - s_w[0] : 0) / (k - 1);
+  const long long slack_b = (lmax - s_w[1] > 0 ? lmax - s_w[1] : 0) / (k - 1);
   if (threadIdx.x == 0) s_best = 0;
   __syncthreads();
   // diagonal r: i(r) = number of A-steps among the first r steps
@@ -642,21 +664,32 @@ k_lp_select(const int32_t* __restrict__ ioff, const int32_t* __restrict__ bucket
     if (A[mid] <= B[r - 1 - mid]) lo = mid + 1; else hi = mid;
   }
   const int ia = lo, jb = r - lo;
-  // every approved move becomes ceil(deg/32) work items of at most 32
-  // incident nets each, so the application is balanced across warps; the
-  // item's chunk index is packed above the 6 bits of the source block
-  for (int i = threadIdx.x; i < ia + jb; i += blockDim.x) {
-    const bool fromA = i < ia;
-    const unsigned long long key = fromA ? ka[i] : kb[i - ia];
-    const int32_t u = (int32_t)(key & 0xffffffffu);
-    const int32_t deg = ioff[u + 1] - ioff[u];
-    const int32_t nch = deg > 0 ? (deg + 31) / 32 : 1;
-    const int32_t slot = atomicAdd(&words[SW_APPROVED], nch);
-    for (int32_t ch = 0; ch < nch; ++ch) {
-      ap_u[slot + ch] = u;
-      ap_from[slot + ch] = (fromA ? a : b) | (ch << 6);
-      ap_to[slot + ch] = fromA ? b : a;
+  {
+    // every selected move becomes ceil(deg/32) work items of at most 32
+    // incident nets for k_lp_apply, which spreads them over the whole grid
+    // (a block applying its own pair's moves serialises the nodes with
+    // thousands of nets on coarse levels); the item's chunk index is packed
+    // above the 6 bits of the source block
+    for (int i = threadIdx.x; i < ia + jb; i += blockDim.x) {
+      const bool fromA = i < ia;
+      const unsigned long long key = fromA ? ka[i] : kb[i - ia];
+      const int32_t u = (int32_t)(key & 0xffffffffu);
+      const int32_t deg = ioff[u + 1] - ioff[u];
+      const int32_t nch = deg > 0 ? (deg + 31) / 32 : 1;
+      const int32_t slot = atomicAdd(ap_count, nch);
+      for (int32_t ch = 0; ch < nch; ++ch) {
+        ap_u[slot + ch] = u;
+        ap_from[slot + ch] = (fromA ? a : b) | (ch << 6);
+        ap_to[slot + ch] = fromA ? b : a;
+      }
     }
+  }
+  if (threadIdx.x == 0 && ia + jb > 0) {
+    // weight moved a -> b is A[ia], b -> a is B[jb]
+    const long long delta = A[ia] - B[jb];
+    atomic_add_i64(&dbw[(size_t)s * k + a], -delta);
+    atomic_add_i64(&dbw[(size_t)s * k + b], delta);
+    atomicAdd(moved, (unsigned long long)(ia + jb));
   }
 }
 
@@ -667,17 +700,16 @@ k_lp_select(const int32_t* __restrict__ ioff, const int32_t* __restrict__ bucket
 // Phi(e, s) reaches 0 and setting bit t when Phi(e, t) leaves 0 (Algorithm
 // 3's updates; the atomic xor flips commute, so the final masks equal
 // {i : Phi(e, i) > 0} whatever the order of the moves).  The chunk-0 item
-// also sets Pi[u] = t and moves c(u) between the block weights.
+// also sets Pi[u] = t.  The block weights were moved by the selection.
 __global__ void __launch_bounds__(WARPS * 32)
-k_lp_apply(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
-           const int32_t* __restrict__ c, int k, const int32_t* __restrict__ ap_u,
-           const int32_t* __restrict__ ap_from, const int32_t* __restrict__ ap_to,
-           const int32_t* __restrict__ words, int32_t* __restrict__ part,
-           int32_t* __restrict__ phi, unsigned long long* __restrict__ lam,
-           long long* __restrict__ bw, unsigned long long* __restrict__ moved) {
-  const int32_t na = words[SW_APPROVED];
+k_lp_apply(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets, int k,
+           const int32_t* __restrict__ ap_u, const int32_t* __restrict__ ap_from,
+           const int32_t* __restrict__ ap_to, const int32_t* __restrict__ ap_count,
+           int32_t* __restrict__ part, int32_t* __restrict__ phi,
+           unsigned long long* __restrict__ lam, unsigned long long* __restrict__ moved) {
+  const int32_t na = *ap_count;
   const int lane = lane_id();
-  unsigned long long nodes = 0, incid = 0;
+  unsigned long long incid = 0;
   for (int32_t i = blockIdx.x * WARPS + warp_in_block(); i < na; i += gridDim.x * WARPS) {
     const int32_t u = ap_u[i];
     const int32_t fw = ap_from[i];
@@ -690,15 +722,23 @@ k_lp_apply(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
       if (atomicSub(&phi[(int64_t)e * k + s], 1) == 1) atomicXor(&lam[e], 1ull << s);
       if (atomicAdd(&phi[(int64_t)e * k + t], 1) == 0) atomicXor(&lam[e], 1ull << t);
     }
-    if (ch == 0 && lane == 0) {
-      part[u] = t;
-      atomic_add_i64(&bw[s], -(long long)c[u]);
-      atomic_add_i64(&bw[t], (long long)c[u]);
-      ++nodes;
-    }
+    if (ch == 0 && lane == 0) part[u] = t;
   }
-  if (lane == 0 && nodes) atomicAdd(moved, nodes);
   if (lane == 0 && incid) atomicAdd(moved + 2, incid);
+}
+
+// Folds the pass's block-weight changes into the starting weights of the
+// next pass and advances the pass index read by k_lp_count / k_lp_scatter
+// (the last launch of a pass, so one captured pass can be replayed).
+__global__ void k_lp_next_pass(int32_t* d_pass, long long* __restrict__ bw,
+                               const long long* __restrict__ dbw, int S, int k) {
+  const int i = threadIdx.x;
+  if (i < k) {
+    long long wv = bw[i];
+    for (int x = 0; x < S; ++x) wv += dbw[(size_t)x * k + i];
+    bw[i] = wv;
+  }
+  if (i == 0) *d_pass += 1;
 }
 
 }  // namespace
@@ -903,13 +943,11 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   const int kk = k * k;
   const int32_t n = L.n;
 
-  DBuf<int32_t> list, sr_cnt, sr_fill, sr_off, mv_u, mv_to, bucket, ap_u, ap_from, ap_to, dcnt,
-      dfill, doff, words;
-  DBuf<long long> mv_g, gpre;
+  DBuf<int32_t> list, sr_cnt, sr_fill, sr_off, mv_u, mv_to, bucket, dcnt, dfill, doff, words,
+      ap_u, ap_from, ap_to;
+  DBuf<long long> mv_g, gpre, dbw;
   DBuf<unsigned long long> gkeys, counters;
   const size_t ncap = (size_t)n + 1;
-  // work items of the application: one per 32 incident nets of a moved node
-  const size_t acap = ncap + (size_t)(L.p / 32) + 1;
   list.alloc(&cx.alloc, ncap);
   sr_cnt.alloc(&cx.alloc, (size_t)2 * S);
   sr_fill.alloc(&cx.alloc, (size_t)2 * S);
@@ -918,6 +956,10 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   mv_to.alloc(&cx.alloc, ncap);
   mv_g.alloc(&cx.alloc, ncap);
   bucket.alloc(&cx.alloc, ncap);
+  // block-weight change of every sub-round of a pass (k per sub-round)
+  dbw.alloc(&cx.alloc, (size_t)S * k);
+  // work items of the application: one per 32 incident nets of a moved node
+  const size_t acap = ncap + (size_t)(L.p / 32) + 1;
   ap_u.alloc(&cx.alloc, acap);
   ap_from.alloc(&cx.alloc, acap);
   ap_to.alloc(&cx.alloc, acap);
@@ -935,8 +977,8 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   const int nodes_per_sr = (int)((n + S - 1) / S);
   const int g_gain = grid_for(nodes_per_sr, WARPS, cx.num_sms, 16);
   const int g_gain_block = grid_for(nodes_per_sr, 1, cx.num_sms, 8);
-  const int g_apply = grid_for((int64_t)acap / S + 1, WARPS, cx.num_sms, 16);
   const int g_bucket = grid_for(nodes_per_sr, 256, cx.num_sms, 4);
+  const int g_apply = grid_for((int64_t)acap / S + 1, WARPS, cx.num_sms, 16);
   const int g_sel = k * (k - 1) / 2;
   const int g_nodes = grid_for(n, 256, cx.num_sms, 4);
   KernelTimer gain_timer(cx);
@@ -969,11 +1011,11 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   {
     static std::once_flag once;
     std::call_once(once, [] {
+      const int bytes = (int)sel_smem_bytes(sel_cap_for(2));
       HG_CUDA(cudaFuncSetAttribute(k_lp_select<false>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)sel_smem_bytes(sel_cap_for(2))));
-      HG_CUDA(cudaFuncSetAttribute(k_lp_select<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)sel_smem_bytes(sel_cap_for(2))));
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+      HG_CUDA(cudaFuncSetAttribute(k_lp_select<true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     });
   }
   // k <= SEL_GATHER_K: the pair blocks gather their own moves (k (k - 1) / 2
@@ -998,6 +1040,7 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
     HG_CUDA(cudaMemsetAsync(dfill.p, 0, dfill.bytes(), sm));
     HG_CUDA(cudaMemsetAsync(words.p, 0, words.bytes(), sm));
     HG_CUDA(cudaMemsetAsync(counters.p, 0, counters.bytes(), sm));
+    HG_CUDA(cudaMemsetAsync(dbw.p, 0, dbw.bytes(), sm));
     {
       EventTimer tm(cx, timed ? &rc.ms_gain : nullptr);
       k_lp_count<<<g_nodes, 256, 2 * S * sizeof(int32_t), sm>>>(L.ioff.p, n, seed,
@@ -1043,31 +1086,29 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
       }
       {
         EventTimer tm(cx, timed ? &rc.ms_select : nullptr);
-        if (gather) {
-          k_lp_select<true><<<g_sel, SEL_THREADS, sel_bytes, sm>>>(
-              L.ioff.p, bucket.p, doff.p, dc_s, mv_u.p, mv_to.p, mv_g.p, part, L.c.p, st.bw.p,
-              lmax, k, gkeys.p, gpre.p, ap_u.p, ap_from.p, ap_to.p, w_s);
-        } else {
+        if (!gather) {
           k_lp_bucket<<<g_bucket, 256, (kk + 1) * sizeof(int32_t), sm>>>(
-              mv_u.p, mv_to.p, part, k, dc_s, df_s, doff.p, w_s, bucket.p);
+              mv_to.p, k, dc_s, df_s, doff.p, w_s, bucket.p);
           check_launch("lp_bucket");
-          k_lp_select<false><<<g_sel, SEL_THREADS, sel_bytes, sm>>>(
-              L.ioff.p, bucket.p, doff.p, dc_s, mv_u.p, mv_to.p, mv_g.p, part, L.c.p, st.bw.p,
-              lmax, k, gkeys.p, gpre.p, ap_u.p, ap_from.p, ap_to.p, w_s);
         }
+        auto sel = gather ? k_lp_select<true> : k_lp_select<false>;
+        sel<<<g_sel, SEL_THREADS, sel_bytes, sm>>>(
+            L.ioff.p, L.inets.p, bucket.p, doff.p, dc_s, mv_u.p, mv_to.p, mv_g.p, L.c.p, st.bw.p,
+            dbw.p, s, lmax, k, gkeys.p, gpre.p, w_s, part, st.phi.p, st.lam.p, counters.p, ap_u.p,
+            ap_from.p, ap_to.p, w_s + SW_APPROVED);
         check_launch("lp_select");
         mark(fj, sm, s, 2);
       }
       {
         EventTimer tm(cx, timed ? &rc.ms_apply : nullptr);
-        k_lp_apply<<<g_apply, WARPS * 32, 0, sm>>>(L.ioff.p, L.inets.p, L.c.p, k, ap_u.p,
-                                                          ap_from.p, ap_to.p, w_s, part, st.phi.p,
-                                                          st.lam.p, st.bw.p, counters.p);
+        k_lp_apply<<<g_apply, WARPS * 32, 0, sm>>>(L.ioff.p, L.inets.p, k, ap_u.p, ap_from.p,
+                                                    ap_to.p, w_s + SW_APPROVED, part, st.phi.p,
+                                                    st.lam.p, counters.p);
         check_launch("lp_apply");
         mark(fj, sm, s, 3);
       }
     }
-    k_lp_next_pass<<<1, 1, 0, sm>>>(d_pass.p);
+    k_lp_next_pass<<<1, 64, 0, sm>>>(d_pass.p, st.bw.p, dbw.p, S, k);
     check_launch("lp_next_pass");
   };
   cudaGraphExec_t exec = nullptr;
