@@ -610,6 +610,34 @@ def config3_line(hg, torch, stream, flush, peak, steps=2, warmup=1):
             "instrumented_ms_per_step": iagg["instrumented_ms_per_step"], "level_sizes": [list(x) for x in levels]}
 
 
+def graph_line(hg, torch, stream, flush, steps=3, warmup=1):
+    """Graph path (Sec. 10) against the hypergraph path on the same graph:
+    n = 1e6 nodes, m = 4e6 edges with preferential endpoints, weights in
+    [1, 10], k = 8, full V-cycle; identical results are asserted."""
+    import synth
+    hgr = synth.graph_preferential(SEED, 1_000_000, 4_000_000)
+    out = {"workload": "graph n=1e6, m=4e6 edges (nets of two pins), preferential endpoints, "
+                       "node/edge weights in [1,10], k=8, eps=0.03, full V-cycle"}
+    objs = {}
+    for name, gp in (("graph_path", 0), ("hypergraph_path", 1)):
+        opt = hg.hg_default_options()
+        opt.seed = SEED
+        opt.graph_path = gp
+        step_ms, _, iagg, obj, levels, _ = timed_vcycle(hg, torch, hgr, K_BLOCKS, opt, stream,
+                                                        steps, warmup, flush, instrumented=1)
+        t_ms = statistics.mean(step_ms)
+        pins = sum(p for (_, _, p) in levels)
+        objs[name] = (obj, levels)
+        out[name] = {"ms_per_step": t_ms, "pins_per_s": pins / (t_ms / 1e3), "levels": len(levels),
+                     "pins_per_step": pins, "objective": obj,
+                     "rating_kernels_ms": iagg["ms_rating_kernels"],
+                     "lp_kernels_ms": iagg["ms_lp_gain_kernels"] + iagg["ms_lp_select_kernels"]
+                     + iagg["ms_lp_apply_kernels"]}
+    out["identical_results"] = objs["graph_path"] == objs["hypergraph_path"]
+    out["speedup"] = out["hypergraph_path"]["ms_per_step"] / out["graph_path"]["ms_per_step"]
+    return out
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -756,6 +784,7 @@ def run_ours(args, world, rank, local):
     if world == 1 and not args.no_configs:
         line["config1"] = config1_line(hg, torch, stream, flush, peak)
         line["config3"] = config3_line(hg, torch, stream, flush, peak)
+        line["graph"] = graph_line(hg, torch, stream, flush)
     if world == 1:
         t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).cuda()
         line["gain_recalc"] = run_gain_recalc(hg, torch, hgr, t(hgr.offsets), t(hgr.pins),

@@ -104,6 +104,14 @@ typedef struct {
    * wake-up latency per wait; the executor sets it for its jobs).  0 (default):
    * spin. */
   int32_t blocking_sync;
+  /* Graph path (Sec. 10): 0 (default) = a level whose nets all have exactly
+   * two pins is kept as a graph with one adjacency array (the other endpoint
+   * and the edge weight of every incidence); its rating reads neighbours
+   * directly (no per-net deduplication is needed), and its label propagation
+   * computes g(u, t) = w(u, V_t) - w(u, V_Pi(u)) from the neighbours' blocks
+   * without pin counts.  Contraction keeps a graph a graph.  1 = always use
+   * the hypergraph path.  Results are identical either way. */
+  int32_t graph_path;
 } hg_options;
 
 /* Per-phase device time (milliseconds, from CUDA events) and work counters,
@@ -176,6 +184,10 @@ int hg_create(int32_t n, int32_t m, const int32_t* net_offsets, const int32_t* p
  * NULL) receive the new level's index and sizes. */
 int hg_coarsen_level(hg_t* h, int32_t k, int32_t* out_level, int32_t* out_n, int32_t* out_m,
                      int64_t* out_p);
+
+/* 1 in *out_graph when the level runs on the graph path (see
+ * hg_options.graph_path), else 0. */
+int hg_level_is_graph(const hg_t* h, int32_t level, int32_t* out_graph);
 
 /* Number of levels held (1 + coarsening steps done) and the sizes of one. */
 int hg_num_levels(const hg_t* h, int32_t* out_levels);

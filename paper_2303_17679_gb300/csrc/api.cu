@@ -183,7 +183,8 @@ int hg_create(int32_t n, int32_t m, const int32_t* net_offsets, const int32_t* p
   if (o.rate_warp_max_d < 0 || o.rate_warp_max_d > 256 || o.rate_pair_max_d < 0 ||
       o.rate_pair_max_d > 1024 || o.rate_quad_max_d < 0 || o.rate_quad_max_d > 2048 ||
       o.rate_block_max_d < 0 || o.rate_block_max_d > 4096 || o.lp_block_min_deg < 0 ||
-      o.lp_block_min_deg > (1 << 20) || o.blocking_sync < 0 || o.blocking_sync > 1)
+      o.lp_block_min_deg > (1 << 20) || o.blocking_sync < 0 || o.blocking_sync > 1 ||
+      o.graph_path < 0 || o.graph_path > 1)
     return HG_ERR_INVALID;
   int64_t W = 0;
   int64_t p = 0;
@@ -244,6 +245,7 @@ int hg_create(int32_t n, int32_t m, const int32_t* net_offsets, const int32_t* p
     {
       hgk::EventTimer tm(h->cx, &h->stats.ms_transpose);
       hgk::build_incidence(h->cx, *L);
+      if (o.graph_path == 0 && hgk::level_is_graph(h->cx, *L)) hgk::build_graph_adjacency(h->cx, *L);
     }
     hgk::check_status(h->cx);
     h->levels.push_back(std::move(L));
@@ -260,6 +262,13 @@ int hg_create(int32_t n, int32_t m, const int32_t* net_offsets, const int32_t* p
 int hg_num_levels(const hg_t* h, int32_t* out_levels) {
   if (!h || !out_levels) return HG_ERR_INVALID;
   *out_levels = (int32_t)h->levels.size();
+  return HG_OK;
+}
+
+int hg_level_is_graph(const hg_t* h, int32_t level, int32_t* out_graph) {
+  if (!h || !out_graph) return HG_ERR_INVALID;
+  if (!valid_level(h, level)) return HG_ERR_STATE;
+  *out_graph = h->levels[level]->graph ? 1 : 0;
   return HG_OK;
 }
 

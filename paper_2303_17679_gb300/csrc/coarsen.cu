@@ -97,6 +97,11 @@ struct RateArgs {
   const int32_t* inets;
   const int32_t* eoff;
   const int2* rinfo;  // {deduplicated cluster, weight or INT32_MAX} per pin position
+  // graph levels: visits come from the adjacency array, the cluster of a
+  // neighbour from rep and its weight and status from cst
+  bool graph;
+  const int2* adj;
+  const int32_t* rep;
   const unsigned long long* rterm;  // Q20 net term of every rated net, 0 otherwise
   const int32_t* c;
   const int2* cst;  // {cw, status}
@@ -240,7 +245,30 @@ __device__ __forceinline__ EachVisit<VT, F> each_visit(F f) {
   return EachVisit<VT, F>{f};
 }
 
-// Filters a batch of pin positions (-1 = no visit) and hands it to `add`:
+// {cluster, weight word} of a batch of visits (-1 = no visit): on
+// hypergraph levels q is a pin position and the record is rinfo[q]; on graph
+// levels q is the neighbour node, whose cluster is rep[q] (a net of two pins
+// needs no deduplication: u is a singleton, so rep[q] != u) and whose weight
+// word is the cluster's weight, or INT32_MAX for an unclustered node of this
+// sub-round.
+__device__ __forceinline__ void resolve_batch(const RateArgs& A, const int32_t (&q)[RATE_ILP],
+                                              int2 (&ri)[RATE_ILP]) {
+  if (!A.graph) {
+#pragma unroll
+    for (int k = 0; k < RATE_ILP; ++k) ri[k] = q[k] >= 0 ? A.rinfo[q[k]] : make_int2(-1, 0);
+    return;
+  }
+  int32_t C[RATE_ILP];
+#pragma unroll
+  for (int k = 0; k < RATE_ILP; ++k) C[k] = q[k] >= 0 ? A.rep[q[k]] : -1;
+#pragma unroll
+  for (int k = 0; k < RATE_ILP; ++k) {
+    const int2 cs = C[k] >= 0 ? A.cst[C[k]] : make_int2(0, 0);
+    ri[k] = make_int2(C[k], cs.y == A.s ? 0x7fffffff : cs.x);
+  }
+}
+
+// Filters a batch of visits (-1 = no visit) and hands it to `add`:
 // admissible C is not u, not an unclustered node of this sub-round (weight
 // word INT32_MAX), and fits c_max.
 template <typename VT, typename Add>
@@ -248,8 +276,7 @@ __device__ __forceinline__ void visit_filtered(const RateArgs& A, int32_t u, int
                                                const int32_t (&q)[RATE_ILP],
                                                const VT (&rr)[RATE_ILP], Add& add) {
   int2 ri[RATE_ILP];
-#pragma unroll
-  for (int k = 0; k < RATE_ILP; ++k) ri[k] = q[k] >= 0 ? A.rinfo[q[k]] : make_int2(-1, 0);
+  resolve_batch(A, q, ri);
   int32_t C[RATE_ILP];
   bool ok[RATE_ILP];
 #pragma unroll
@@ -258,6 +285,35 @@ __device__ __forceinline__ void visit_filtered(const RateArgs& A, int32_t u, int
     ok[k] = C[k] >= 0 && C[k] != u && (long long)ri[k].y + cu <= (long long)A.c_max;
   }
   add(C, rr, ok);
+}
+
+// Graph levels: the visits of incidences [lo, hi) of u are the other
+// endpoints of its edges, each with the edge's term w(e) * 2^20 (the Q20 term
+// of a two-pin net); chunk c of 32 * RATE_ILP incidences goes to warp c mod
+// TW of the team.  Returns the visits in warp 0 (0 in the other warps).
+template <typename VT, typename Visit>
+__device__ __forceinline__ int32_t graph_walk(const RateArgs& A, int32_t lo, int32_t hi, int wt,
+                                              int TW, Visit& visit_batch) {
+  constexpr int32_t CH = 32 * RATE_ILP;
+  const int lane = lane_id();
+  for (int32_t c0 = lo + CH * wt; c0 < hi; c0 += CH * TW) {
+    int32_t q[RATE_ILP];
+    VT rr[RATE_ILP];
+#pragma unroll
+    for (int k = 0; k < RATE_ILP; ++k) {
+      const int32_t j = c0 + 32 * k + lane;
+      if (j < hi) {
+        const int2 a = A.adj[j];
+        q[k] = a.x;
+        rr[k] = (VT)((unsigned long long)(uint32_t)a.y << 20);
+      } else {
+        q[k] = -1;
+        rr[k] = (VT)0;
+      }
+    }
+    visit_batch(q, rr);
+  }
+  return wt == 0 ? hi - lo : 0;
 }
 
 // Adds one group of (up to) 32 consecutive incident nets of u, starting at
@@ -356,6 +412,7 @@ __device__ __forceinline__ int32_t walk_group(const NetMeta<VT>& m, int wt, int 
 template <typename VT, typename Visit>
 __device__ __forceinline__ int32_t rate_group_raw(const RateArgs& A, int32_t g0, int32_t end,
                                                   int wt, int TW, int32_t& run, Visit& visit_batch) {
+  if (A.graph) return graph_walk<VT>(A, g0, min(g0 + 32, end), wt, TW, visit_batch);
   const int32_t e = g0 + lane_id() < end ? A.inets[g0 + lane_id()] : -1;
   return walk_group<VT>(net_meta<VT>(A, e), wt, TW, run, visit_batch);
 }
@@ -370,6 +427,12 @@ __device__ __forceinline__ int64_t rate_groups_raw(const RateArgs& A, int32_t fi
   const int lane = lane_id();
   int64_t visits = 0;
   if (first >= end) return 0;
+  if (A.graph) {
+    if (step == 32) return graph_walk<VT>(A, first, end, wt, TW, visit_batch);
+    for (int32_t g = first; g < end; g += step)
+      visits += graph_walk<VT>(A, g, min(g + 32, end), wt, TW, visit_batch);
+    return visits;
+  }
   int32_t g = first;
   NetMeta<VT> m = net_meta<VT>(A, g + lane < end ? A.inets[g + lane] : -1);
   int32_t e_next = g + step + lane < end ? A.inets[g + step + lane] : -1;
@@ -735,8 +798,7 @@ k_rate_part(RateArgs A, const int32_t* __restrict__ split, const int32_t* __rest
     int32_t* nused = &s_nused[it & 1];
     auto visit = [&](const int32_t(&q)[RATE_ILP], const VT(&rr)[RATE_ILP]) HG_INLINE {
       int2 ri[RATE_ILP];
-#pragma unroll
-      for (int j = 0; j < RATE_ILP; ++j) ri[j] = q[j] >= 0 ? A.rinfo[q[j]] : make_int2(-1, 0);
+      resolve_batch(A, q, ri);
 #pragma unroll
       for (int j = 0; j < RATE_ILP; ++j) {
         const int32_t Cj = ri[j].x;
@@ -892,8 +954,9 @@ __device__ __forceinline__ int rate_class(int64_t W, int32_t n, bool dense_block
   return 4;
 }
 
-// W(u) (pins of rated nets) of every node, and the largest bound on a node's
-// rating (sum of its net terms), which decides the value width.
+// W(u) (pins of rated nets, or rated incident edges on graph levels) of every
+// node, and the largest bound on a node's rating (sum of its net terms),
+// which decides the value width.
 // floor(w(e) * 2^20 / (|e| - 1)) for the rated nets (2 <= |e| <= T), else 0;
 // at least 1 for a rated net since |e| - 1 < 2^20.
 __global__ void k_net_terms(const int32_t* __restrict__ eoff, const int32_t* __restrict__ w,
@@ -910,7 +973,7 @@ __global__ void k_net_terms(const int32_t* __restrict__ eoff, const int32_t* __r
 // One warp per node, lanes over its incident nets.
 __global__ void k_node_work(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
                             const int32_t* __restrict__ eoff,
-                            const unsigned long long* __restrict__ rterm, int32_t n,
+                            const unsigned long long* __restrict__ rterm, int32_t n, bool graph,
                             int32_t* __restrict__ wof, unsigned long long* __restrict__ max_r) {
   unsigned long long lr = 0;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -921,7 +984,7 @@ __global__ void k_node_work(const int32_t* __restrict__ ioff, const int32_t* __r
       const int32_t e = inets[j];
       const unsigned long long r = rterm[e];
       if (r != 0) {
-        W += eoff[e + 1] - eoff[e];
+        W += graph ? 1 : eoff[e + 1] - eoff[e];  // a graph visits the other endpoint only
         R += r;
       }
     }
@@ -1551,7 +1614,7 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   clusters.alloc(&cx.alloc, 1);
   max_r.alloc(&cx.alloc, 1);
   stats.alloc(&cx.alloc, (size_t)ST_WORDS * NCLASS);
-  rinfo.alloc(&cx.alloc, (size_t)std::max<int64_t>(L.p, 1));
+  rinfo.alloc(&cx.alloc, L.graph ? 1 : (size_t)std::max<int64_t>(L.p, 1));
   HG_CUDA(cudaMemsetAsync(gw.p, 0, gw.bytes(), cx.stream));
   HG_CUDA(cudaMemsetAsync(gcnt.p, 0, gcnt.bytes(), cx.stream));
   HG_CUDA(cudaMemsetAsync(slot_fill.p, 0, slot_fill.bytes(), cx.stream));
@@ -1561,8 +1624,11 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   HG_CUDA(cudaMemsetAsync(max_r.p, 0, max_r.bytes(), cx.stream));
   HG_CUDA(cudaMemsetAsync(stats.p, 0, stats.bytes(), cx.stream));
   HG_CUDA(cudaMemcpyAsync(clusters.p, &n, sizeof(int32_t), cudaMemcpyHostToDevice, cx.stream));
+  // graph levels rate from the adjacency array: no pin records, no
+  // (net, cluster) map
+  const bool records = L.p > 0 && !L.graph;
   DBuf<int32_t> tiles;
-  if (L.p > 0) {
+  if (records) {
     tiles.alloc(&cx.alloc, (size_t)num_pin_tiles(L.p) + 1);
     build_tile_index(cx, L.eoff.p, L.m, L.p, tiles.p);
     k_rinfo_init<<<grid_for(num_pin_tiles(L.p), 1, cx.num_sms, 8), PIN_TILE_THREADS, 0,
@@ -1583,7 +1649,7 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
     check_launch("net_terms");
   }
   k_node_work<<<grid_for(n, 8, cx.num_sms, 16), 256, 0, cx.stream>>>(
-      L.ioff.p, L.inets.p, L.eoff.p, rterm.p, n, wof.p, max_r.p);
+      L.ioff.p, L.inets.p, L.eoff.p, rterm.p, n, L.graph, wof.p, max_r.p);
   check_launch("node_work");
   const unsigned long long hmax_r = (unsigned long long)read_i64(cx, (const int64_t*)max_r.p);
   // 32-bit rating words when no node's total rating can reach 2^31; block
@@ -1697,7 +1763,7 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   pm.key = nullptr;
   pm.pos = nullptr;
   pm.mask = 0;
-  if (L.p > 0 && S > 1) {
+  if (records && S > 1) {
     uint64_t cap = 1024;
     while (cap < 4 * (uint64_t)L.p && cap < (1ull << 32)) cap <<= 1;
     pm_key.alloc(&cx.alloc, cap);
@@ -1728,6 +1794,9 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   A.inets = L.inets.p;
   A.eoff = L.eoff.p;
   A.rinfo = rinfo.p;
+  A.graph = L.graph;
+  A.adj = L.adj.p;
+  A.rep = L.rep.p;
   A.rterm = rterm.p;
   A.c = L.c.p;
   A.cst = cst.p;
@@ -1749,7 +1818,7 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
     A.s = s;
     A.words = words.p + (size_t)s * CW_WORDS;
     int32_t* w_s = words.p + (size_t)s * CW_WORDS;
-    if (L.p > 0) {
+    if (records) {
       EventTimer tm(cx, &cc.ms_refresh);
       k_rinfo_refresh<<<grid_for(L.p / 2 + 1, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(
           rinfo.p, L.p, cst.p, s);
@@ -1785,7 +1854,7 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
       check_launch("finish");
       if (cx.launches) *cx.launches += 4;
     }
-    if (s + 1 < S && L.p > 0) {
+    if (s + 1 < S && records) {
       EventTimer tm(cx, &cc.ms_refresh);
       SubRanges R;
       for (int c = 0; c < NCLASS; ++c) {

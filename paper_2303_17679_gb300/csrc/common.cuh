@@ -256,6 +256,11 @@ struct Level {
   DBuf<int32_t> map;    // n    node -> node of the next level (after coarsening)
   DBuf<int32_t> rep;    // n    representative in the clustering that made the next level
   bool coarsened = false;
+  // Graph levels (every net has exactly two pins, Sec. 10): the one
+  // adjacency array adj[j] = {other endpoint, w(e)} of incidence j = (u, e),
+  // aligned with inets.  The coarse level of a graph level is a graph level.
+  bool graph = false;
+  DBuf<int2> adj;       // p (graph levels only)
 };
 
 // --------------------------------------------------------- primitives (prim.cu)
@@ -285,6 +290,10 @@ void iota_i32(const Ctx& cx, int32_t* p, int64_t n);
 
 // Builds ioff/inets of a level from eoff/pins (a1).
 void build_incidence(const Ctx& cx, Level& L);
+// True when the level has nets and every net has exactly two pins.
+bool level_is_graph(const Ctx& cx, const Level& L);
+// Sets L.graph and builds L.adj (after build_incidence).
+void build_graph_adjacency(const Ctx& cx, Level& L);
 
 // Device-side validation of a level given by device pointers: offsets
 // monotone, pins in range, no net empty, no repeated pin in a net, weights

@@ -471,6 +471,8 @@ void contract_level(const Ctx& cx, Level& L, const int32_t* cw, Level& out, int 
                           cudaMemcpyDeviceToDevice, cx.stream));
   if (cx.launches) *cx.launches += 2;
   build_incidence(cx, out);
+  // a graph's coarse nets have two pins again (one-pin nets are dropped)
+  if (L.graph && out.m > 0) build_graph_adjacency(cx, out);
   L.coarsened = true;
 }
 

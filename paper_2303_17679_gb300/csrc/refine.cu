@@ -97,6 +97,23 @@ __global__ void k_objective(const unsigned long long* __restrict__ lam,
   if (threadIdx.x == 0 && f) atomicAdd(out, (unsigned long long)f);
 }
 
+// Objective of a graph level: the weight of the cut edges (lambda(e) - 1 is
+// 1 for a cut edge and 0 otherwise).
+__global__ void k_objective_graph(const int32_t* __restrict__ eoff,
+                                  const int32_t* __restrict__ pins, const int32_t* __restrict__ w,
+                                  const int32_t* __restrict__ part, int32_t m,
+                                  unsigned long long* __restrict__ out) {
+  __shared__ int64_t red[32];
+  int64_t f = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t b = eoff[e];
+    if (part[pins[b]] != part[pins[b + 1]]) f += w[e];
+  }
+  f = block_sum(f, red);
+  if (threadIdx.x == 0 && f) atomicAdd(out, (unsigned long long)f);
+}
+
 // -------------------------------------------- sub-round node lists (a11)
 
 // Nodes of a pass are listed by key = sub-round * 2 + class, class 1 for
@@ -221,6 +238,45 @@ __device__ __forceinline__ GainPart gain_partial(const int32_t* __restrict__ ine
   return g;
 }
 
+// Graph levels (Sec. 10, "The Gain Table"): the gain of moving u to V_t is
+// w(u, V_t) - w(u, V_Pi(u)), the weight of u's edges into V_t minus that of
+// its edges into its own block, which equals the gain of Sec. 6 for nets of
+// two pins.  The lanes sum the edge weights per neighbour block: a warp
+// reduction per block for k <= 16, shared counters above.
+__device__ __forceinline__ GainPart gain_partial_graph(const int2* __restrict__ adj,
+                                                       const int32_t* __restrict__ part, int k,
+                                                       int32_t beg, int32_t end, int first,
+                                                       int stride, int32_t* s_cnt) {
+  const int lane = lane_id();
+  GainPart g{0, 0, 0, 0, 0};
+  for (int32_t c0 = beg + 32 * first; c0 < end; c0 += 32 * stride) {
+    const int32_t j = c0 + lane;
+    int32_t we = 0, tb = -1;
+    if (j < end) {
+      const int2 a = adj[j];
+      we = a.y;
+      tb = part[a.x];
+    }
+    if (k <= GAIN_REDUCE_K) {
+      for (int t = 0; t < k; ++t) {
+        const unsigned x = __reduce_add_sync(FULL, tb == t ? (unsigned)we : 0u);
+        if (lane == t) g.acc0 += x;
+      }
+    } else if (tb >= 0) {
+      atomicAdd(&s_cnt[tb], we);
+    }
+  }
+  return g;
+}
+
+// After gain_collect on a graph level: ben - wsum = -w(u, V_from), so that
+// gain_best computes w(u, V_t) - w(u, V_from).
+__device__ __forceinline__ void graph_gain_terms(GainPart& g, int from) {
+  const int lane = lane_id();
+  g.ben = 0;
+  g.wsum = lane == from ? g.acc0 : (lane + 32 == from ? g.acc1 : 0);
+}
+
 // Moves the warp's block counters plus its `full` sum into acc0 / acc1 and
 // clears the counters (k above GAIN_REDUCE_K; for smaller k the sums are in
 // acc0 already).
@@ -283,6 +339,8 @@ struct GainArgs {
   int32_t* dcount;
   int32_t* words;
   unsigned long long* work;
+  bool graph;       // graph level: gains from adj and part, no Phi / Lambda
+  const int2* adj;
 };
 
 __device__ __forceinline__ void gain_emit(const GainArgs& A, int32_t u, int from, long long g,
@@ -310,8 +368,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_lp_gain_warp(GainArgs A) {
     const int32_t u = A.list[i];
     const int from = A.part[u];
     const int32_t beg = A.ioff[u], end = A.ioff[u + 1];
-    GainPart g = gain_partial(A.inets, A.w, A.phi, A.lam, A.k, from, beg, end, 0, 1, cnt);
+    GainPart g = A.graph ? gain_partial_graph(A.adj, A.part, A.k, beg, end, 0, 1, cnt)
+                         : gain_partial(A.inets, A.w, A.phi, A.lam, A.k, from, beg, end, 0, 1, cnt);
     gain_collect(g, cnt, A.k);
+    if (A.graph) graph_gain_terms(g, from);
     long long bg;
     int bt;
     gain_best(g, A.k, from, bg, bt);
@@ -341,8 +401,11 @@ __global__ void __launch_bounds__(GAIN_BLOCK_WARPS * 32) k_lp_gain_block(GainArg
     const int32_t u = A.list[i];
     const int from = A.part[u];
     const int32_t beg = A.ioff[u], end = A.ioff[u + 1];
-    GainPart g = gain_partial(A.inets, A.w, A.phi, A.lam, A.k, from, beg, end, wv, WARPS, cnt);
+    GainPart g =
+        A.graph ? gain_partial_graph(A.adj, A.part, A.k, beg, end, wv, WARPS, cnt)
+                : gain_partial(A.inets, A.w, A.phi, A.lam, A.k, from, beg, end, wv, WARPS, cnt);
     gain_collect(g, cnt, A.k);
+    if (A.graph) graph_gain_terms(g, from);
     s_acc[wv][lane] = g.acc0;
     s_acc[wv][lane + 32] = g.acc1;
     const long long b = warp_sum(g.ben), ws = warp_sum(g.wsum);
@@ -510,7 +573,7 @@ k_lp_select(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
             int32_t* __restrict__ phi, unsigned long long* __restrict__ lam,
             unsigned long long* __restrict__ moved, int32_t* __restrict__ ap_u,
             int32_t* __restrict__ ap_from, int32_t* __restrict__ ap_to,
-            int32_t* __restrict__ ap_count) {
+            int32_t* __restrict__ ap_count, bool graph) {
   extern __shared__ __align__(16) unsigned long long sel_smem[];
   const int cap = sel_cap_for(k);
   unsigned long long* s_keys0 = sel_smem;
@@ -664,7 +727,21 @@ k_lp_select(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
     if (A[mid] <= B[r - 1 - mid]) lo = mid + 1; else hi = mid;
   }
   const int ia = lo, jb = r - lo;
-  {
+  if (graph) {
+    // graph level: a move only rewrites Pi[u] (no pin counts to update).
+    // No kernel of the sub-round reads Pi after the best moves, and the
+    // moves carry their source block, so the pair block writes it here.
+    unsigned long long incid = 0;
+    for (int i = threadIdx.x; i < ia + jb; i += blockDim.x) {
+      const bool fromA = i < ia;
+      const unsigned long long key = fromA ? ka[i] : kb[i - ia];
+      const int32_t u = (int32_t)(key & 0xffffffffu);
+      part[u] = fromA ? b : a;
+      incid += (unsigned long long)(ioff[u + 1] - ioff[u]);
+    }
+    incid = warp_sum(incid);
+    if (lane_id() == 0 && incid) atomicAdd(moved + 2, incid);
+  } else {
     // every selected move becomes ceil(deg/32) work items of at most 32
     // incident nets for k_lp_apply, which spreads them over the whole grid
     // (a block applying its own pair's moves serialises the nodes with
@@ -763,14 +840,19 @@ struct PinState {
   DBuf<int32_t> tiles;
 };
 
-void build_pin_state(const Ctx& cx, const Level& L, int k, const int32_t* part, PinState& st) {
-  st.phi.alloc(&cx.alloc, (size_t)L.m * k + 1);
-  st.lam.alloc(&cx.alloc, (size_t)L.m + 1);
+// Phi, Lambda (unless counts == false: graph levels in label propagation)
+// and the block weights of a partition.
+void build_pin_state(const Ctx& cx, const Level& L, int k, const int32_t* part, PinState& st,
+                     bool counts = true) {
   st.bw.alloc(&cx.alloc, (size_t)k);
-  HG_CUDA(cudaMemsetAsync(st.phi.p, 0, st.phi.bytes(), cx.stream));
-  HG_CUDA(cudaMemsetAsync(st.lam.p, 0, st.lam.bytes(), cx.stream));
   HG_CUDA(cudaMemsetAsync(st.bw.p, 0, st.bw.bytes(), cx.stream));
-  if (L.p > 0) {
+  if (counts) {
+    st.phi.alloc(&cx.alloc, (size_t)L.m * k + 1);
+    st.lam.alloc(&cx.alloc, (size_t)L.m + 1);
+    HG_CUDA(cudaMemsetAsync(st.phi.p, 0, st.phi.bytes(), cx.stream));
+    HG_CUDA(cudaMemsetAsync(st.lam.p, 0, st.lam.bytes(), cx.stream));
+  }
+  if (counts && L.p > 0) {
     st.tiles.alloc(&cx.alloc, (size_t)num_pin_tiles(L.p) + 1);
     build_tile_index(cx, L.eoff.p, L.m, L.p, st.tiles.p);
     k_pin_counts<<<grid_for(num_pin_tiles(L.p), 1, cx.num_sms, 8), PIN_TILE_THREADS, 0,
@@ -782,6 +864,19 @@ void build_pin_state(const Ctx& cx, const Level& L, int k, const int32_t* part, 
                                                                           st.bw.p);
   check_launch("block_weights");
   if (cx.launches) *cx.launches += 3;
+}
+
+int64_t objective_of_graph(const Ctx& cx, const Level& L, const int32_t* part) {
+  DBuf<unsigned long long> acc;
+  acc.alloc(&cx.alloc, 1);
+  HG_CUDA(cudaMemsetAsync(acc.p, 0, sizeof(unsigned long long), cx.stream));
+  if (L.m > 0) {
+    k_objective_graph<<<grid_for(L.m, 256, cx.num_sms, 4), 256, 0, cx.stream>>>(
+        L.eoff.p, L.pins.p, L.w.p, part, L.m, acc.p);
+    check_launch("objective_graph");
+    if (cx.launches) *cx.launches += 1;
+  }
+  return read_i64(cx, reinterpret_cast<const int64_t*>(acc.p));
 }
 
 int64_t objective_from_lambda(const Ctx& cx, const Level& L, const unsigned long long* lam) {
@@ -936,7 +1031,7 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   PinState st;
   {
     EventTimer tm(cx, &rc.ms_phi);
-    build_pin_state(cx, L, k, part, st);
+    build_pin_state(cx, L, k, part, st, !L.graph);
   }
   const int64_t per_block = (total_node_weight + k - 1) / k;
   const long long lmax = (long long)(per_block * (1000000 + (int64_t)eps_ppm) / 1000000);
@@ -959,7 +1054,8 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   // block-weight change of every sub-round of a pass (k per sub-round)
   dbw.alloc(&cx.alloc, (size_t)S * k);
   // work items of the application: one per 32 incident nets of a moved node
-  const size_t acap = ncap + (size_t)(L.p / 32) + 1;
+  // (graph levels: the selection rewrites Pi itself, no application launch)
+  const size_t acap = L.graph ? 1 : ncap + (size_t)(L.p / 32) + 1;
   ap_u.alloc(&cx.alloc, acap);
   ap_from.alloc(&cx.alloc, acap);
   ap_to.alloc(&cx.alloc, acap);
@@ -997,6 +1093,8 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   G.mv_to = mv_to.p;
   G.mv_g = mv_g.p;
   G.work = counters.p + 1;
+  G.graph = L.graph;
+  G.adj = L.adj.p;
 
   // One pass = the sub-round lists, then per sub-round best moves, pair
   // bucketing and selection, application.  Every launch has a fixed geometry
@@ -1021,7 +1119,7 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   // k <= SEL_GATHER_K: the pair blocks gather their own moves (k (k - 1) / 2
   // blocks each reading the move list), no bucket pass
   const bool gather = k <= SEL_GATHER_K;
-  const int per_pass_launches = 3 + (gather ? 4 : 5) * S;
+  const int per_pass_launches = 3 + (3 + (gather ? 0 : 1) + (L.graph ? 0 : 1)) * S;
   // side != nullptr: the two best-move kernels of a sub-round are captured
   // as parallel branches (they only meet in atomics on the move list), so
   // the few high-degree nodes of the block class overlap with the warp class
@@ -1095,16 +1193,18 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
         sel<<<g_sel, SEL_THREADS, sel_bytes, sm>>>(
             L.ioff.p, L.inets.p, bucket.p, doff.p, dc_s, mv_u.p, mv_to.p, mv_g.p, L.c.p, st.bw.p,
             dbw.p, s, lmax, k, gkeys.p, gpre.p, w_s, part, st.phi.p, st.lam.p, counters.p, ap_u.p,
-            ap_from.p, ap_to.p, w_s + SW_APPROVED);
+            ap_from.p, ap_to.p, w_s + SW_APPROVED, L.graph);
         check_launch("lp_select");
         mark(fj, sm, s, 2);
       }
       {
         EventTimer tm(cx, timed ? &rc.ms_apply : nullptr);
-        k_lp_apply<<<g_apply, WARPS * 32, 0, sm>>>(L.ioff.p, L.inets.p, k, ap_u.p, ap_from.p,
-                                                    ap_to.p, w_s + SW_APPROVED, part, st.phi.p,
-                                                    st.lam.p, counters.p);
-        check_launch("lp_apply");
+        if (!L.graph) {
+          k_lp_apply<<<g_apply, WARPS * 32, 0, sm>>>(L.ioff.p, L.inets.p, k, ap_u.p, ap_from.p,
+                                                      ap_to.p, w_s + SW_APPROVED, part, st.phi.p,
+                                                      st.lam.p, counters.p);
+          check_launch("lp_apply");
+        }
         mark(fj, sm, s, 3);
       }
     }
@@ -1166,7 +1266,7 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   rc.lp_passes += res.passes;
   {
     EventTimer tm(cx, &rc.ms_objective);
-    res.objective = objective_from_lambda(cx, L, st.lam.p);
+    res.objective = L.graph ? objective_of_graph(cx, L, part) : objective_from_lambda(cx, L, st.lam.p);
   }
   return res;
 }

@@ -1,6 +1,7 @@
 // Hypergraph structure on the device: the pin-tile index, the incident-net
 // lists I(u) (the second adjacency array of Sec. 4.2, "The Contraction
-// Algorithm"), and validation of caller-provided device arrays.
+// Algorithm"), the single adjacency array of graph levels (Sec. 10, "Graph
+// Data Structure"), and validation of caller-provided device arrays.
 #include "common.cuh"
 #include "pintile.cuh"
 
@@ -177,7 +178,65 @@ __global__ void k_max_net_size(const int32_t* __restrict__ eoff, int32_t m, int3
   if (lane_id() == 0 && mx) atomicMax(out, mx);
 }
 
+__global__ void k_net_size_range(const int32_t* __restrict__ eoff, int32_t m,
+                                 int32_t* __restrict__ out) {
+  int32_t lo = 0x7fffffff, hi = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t sz = eoff[e + 1] - eoff[e];
+    lo = min(lo, sz);
+    hi = max(hi, sz);
+  }
+  lo = warp_min(lo);
+  hi = warp_max(hi);
+  if (lane_id() == 0) {
+    atomicMin(&out[0], lo);
+    atomicMax(&out[1], hi);
+  }
+}
+
+// adj[j] = {the other pin of net inets[j], w(inets[j])} for every incidence
+// of a graph level (ipin[j] is the incidence's own pin position).
+__global__ void k_adjacency(const int32_t* __restrict__ eoff, const int32_t* __restrict__ pins,
+                            const int32_t* __restrict__ w, const int32_t* __restrict__ inets,
+                            const int32_t* __restrict__ ipin, int64_t p, int2* __restrict__ adj) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t e = inets[j];
+    const int32_t b = eoff[e];
+    const int32_t other = ipin[j] == b ? b + 1 : b;
+    adj[j] = make_int2(pins[other], w[e]);
+  }
+}
+
 }  // namespace
+
+bool level_is_graph(const Ctx& cx, const Level& L) {
+  if (L.m <= 0) return false;
+  DBuf<int32_t> range;
+  range.alloc(&cx.alloc, 2);
+  const int32_t init[2] = {0x7fffffff, 0};
+  HG_CUDA(cudaMemcpyAsync(range.p, init, sizeof(init), cudaMemcpyHostToDevice, cx.stream));
+  k_net_size_range<<<grid_for(L.m, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(L.eoff.p, L.m,
+                                                                            range.p);
+  check_launch("net_size_range");
+  if (cx.launches) *cx.launches += 1;
+  int32_t h[2];
+  HG_CUDA(cudaMemcpyAsync(h, range.p, sizeof(h), cudaMemcpyDeviceToHost, cx.stream));
+  HG_CUDA(cudaStreamSynchronize(cx.stream));
+  return h[0] == 2 && h[1] == 2;
+}
+
+void build_graph_adjacency(const Ctx& cx, Level& L) {
+  L.graph = true;
+  L.adj.alloc(&cx.alloc, (size_t)(L.p > 0 ? L.p : 1));
+  if (L.p > 0) {
+    k_adjacency<<<grid_for(L.p, 256, cx.num_sms, 16), 256, 0, cx.stream>>>(
+        L.eoff.p, L.pins.p, L.w.p, L.inets.p, L.ipin.p, L.p, L.adj.p);
+    check_launch("adjacency");
+    if (cx.launches) *cx.launches += 1;
+  }
+}
 
 void build_tile_index(const Ctx& cx, const int32_t* eoff, int32_t m, int64_t p, int32_t* tile_net) {
   const int64_t ntiles = num_pin_tiles(p);

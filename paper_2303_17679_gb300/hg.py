@@ -49,6 +49,7 @@ class hg_options(ctypes.Structure):
         ("rate_block_max_d", ctypes.c_int32),
         ("lp_block_min_deg", ctypes.c_int32),
         ("blocking_sync", ctypes.c_int32),
+        ("graph_path", ctypes.c_int32),
     ]
 
     TUNABLE = ("rate_warp_max_d", "rate_pair_max_d", "rate_quad_max_d", "rate_block_max_d",
@@ -148,6 +149,7 @@ def load(path: str | None = None):
             "hg_reset_stats": (ctypes.c_int, [H]),
             "hg_destroy": (ctypes.c_int, [H]),
             "hg_trim_memory": (ctypes.c_int, []),
+            "hg_level_is_graph": (ctypes.c_int, [H, i32, P(i32)]),
             "hg_calibrate_smem_atomics": (ctypes.c_int, [vp, P(ctypes.c_double),
                                                          P(ctypes.c_double)]),
             "hg_exec_create": (ctypes.c_int, [i32, i64, P(hg_options), P(H)]),
@@ -173,7 +175,7 @@ def exported_symbols():
             "hg_level_info", "hg_initial_partition", "hg_project", "hg_lp_refine",
             "hg_objective", "hg_pin_counts", "hg_recalculate_gains", "hg_gain_table", "hg_gain_table_move",
             "hg_objective_noalloc", "hg_partition", "hg_get_level", "hg_get_incidence",
-            "hg_truncate", "hg_enable_timing", "hg_get_stats", "hg_reset_stats", "hg_destroy", "hg_trim_memory", "hg_calibrate_smem_atomics",
+            "hg_truncate", "hg_enable_timing", "hg_get_stats", "hg_reset_stats", "hg_destroy", "hg_trim_memory", "hg_level_is_graph", "hg_calibrate_smem_atomics",
             "hg_exec_create", "hg_exec_submit", "hg_exec_wait", "hg_exec_pending",
             "hg_exec_now_ns", "hg_exec_destroy", "hg_strerror", "hg_version"]
 
@@ -267,6 +269,12 @@ def hg_num_levels(h) -> int:
     x = ctypes.c_int32()
     _check(load().hg_num_levels(h, ctypes.byref(x)), "hg_num_levels")
     return x.value
+
+
+def hg_level_is_graph(h, level) -> bool:
+    x = ctypes.c_int32()
+    _check(load().hg_level_is_graph(h, int(level), ctypes.byref(x)), "hg_level_is_graph")
+    return bool(x.value)
 
 
 def hg_level_info(h, level):

@@ -194,6 +194,20 @@ def zipf_1m(seed: int = 1, n: int = 1_000_000, m: int | None = None) -> Hypergra
     return zipf_preferential(seed, n, n if m is None else m, name=f"zipf_n{n}")
 
 
+def graph_preferential(seed: int, n: int, m: int, w_lo: int = 1, w_hi: int = 10,
+                       name="graph") -> Hypergraph:
+    """A graph as a hypergraph whose nets all have two pins: m edges with
+    preferential endpoints (heavy-tailed degrees; parallel edges possible),
+    node and edge weights uniform in [w_lo, w_hi]."""
+    sizes = np.full(m, 2, dtype=np.int32)
+    return make(seed, n, m, sizes, True, (w_lo, w_hi), (w_lo, w_hi), name)
+
+
+def graph_uniform(seed: int, n: int, m: int, name="graph_uniform") -> Hypergraph:
+    """m edges with uniform endpoints, unit weights."""
+    return random_uniform(seed, n, m, geom_p=1.0, cap=2, name=name)
+
+
 def large_net_stress(seed: int, n: int, m: int, big_every: int = 100, big_lo: int = 1000,
                      big_hi: int = 100_000, alpha: float = 4.0, force_first: int | None = None,
                      name="stress") -> Hypergraph:
