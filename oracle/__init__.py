@@ -66,7 +66,12 @@ def _L():
                                           i32, vp, vp, vp, vp, vp, vp]
             lib.o_coarsen.restype = i32
             lib.o_coarsen.argtypes = [i32, i32, vp, vp, vp, vp, i64, i32, i32, i32, i32, u64, i32,
-                                      vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+                                      vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+            lib.o_bipartite.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp]
+            lib.o_louvain_best_move.restype = i32
+            lib.o_louvain_best_move.argtypes = [i32, vp, vp, vp, vp, vp, vp, i32]
+            lib.o_louvain_aggregate.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+            lib.o_communities.argtypes = [i32, i32, vp, vp, vp, i32, u64, i32, i32, vp, vp]
             lib.o_contract.restype = i32
             lib.o_contract.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
             lib.o_project.argtypes = [i32, vp, vp, vp]
@@ -227,10 +232,14 @@ def lp_subround(hg, k: int, part, eps_ppm: int, S: int, seed: int, level: int, p
 # -------------------------------------------------------------- coarsening
 
 def coarsen(hg, W: int, k: int, S: int = 16, T: int = 1000, factor: int = 160, seed: int = 1,
-            level: int = 0):
+            level: int = 0, comm=None):
     """One clustering + contraction level.  Returns None when no level is
-    built (n <= factor * k), else a dict with the coarse Level and traces."""
+    built (n <= factor * k), else a dict with the coarse Level and traces.
+    comm: community of every node (candidates stay inside u's community);
+    the result then also holds the coarse nodes' communities."""
     off, pins, w, c = _arrs(hg)
+    cm = None if comm is None else _i32(comm)
+    ccomm = np.zeros(max(hg.n, 1), np.int32)
     n, m, p = hg.n, hg.m, int(off[-1])
     rep = np.zeros(max(n, 1), np.int32)
     target = np.zeros(max(n, 1), np.int32)
@@ -245,13 +254,65 @@ def coarsen(hg, W: int, k: int, S: int = 16, T: int = 1000, factor: int = 160, s
     rc = _L().o_coarsen(n, m, _p(off), _p(pins), _p(w), _p(c), W, k, S, T, factor, seed, level,
                         _p(rep), _p(target), _p(rated), _p(mp), ctypes.byref(on), ctypes.byref(om),
                         ctypes.byref(op), _p(coff), _p(cpins), _p(cw), _p(cc),
-                        ctypes.byref(stop_after))
+                        ctypes.byref(stop_after), _p(cm), _p(ccomm))
     if rc == 1:
         return None
     n2, m2, p2 = on.value, om.value, op.value
     lvl = Level(n2, m2, coff[: m2 + 1].copy(), cpins[:p2].copy(), cw[:m2].copy(), cc[:n2].copy())
-    return dict(level=lvl, rep=rep[:n].copy(), target=target[:n].copy(), rated_in=rated[:n].copy(),
-                map=mp[:n].copy(), stop_after=bool(stop_after.value))
+    out = dict(level=lvl, rep=rep[:n].copy(), target=target[:n].copy(), rated_in=rated[:n].copy(),
+               map=mp[:n].copy(), stop_after=bool(stop_after.value))
+    if comm is not None:
+        out["comm"] = ccomm[:n2].copy()
+    return out
+
+
+# ------------------------------------------------------------ communities
+
+def bipartite(hg):
+    """Bipartite graph of Sec. 4: (V, offsets int64 [V+1], adj int32, weights int64)."""
+    off, pins, w, _ = _arrs(hg)
+    V = hg.n + hg.m
+    p = int(off[-1])
+    boff = np.zeros(V + 1, np.int64)
+    badj = np.zeros(max(2 * p, 1), np.int32)
+    bw = np.zeros(max(2 * p, 1), np.int64)
+    _L().o_bipartite(hg.n, hg.m, _p(off), _p(pins), _p(w), _p(boff), _p(badj), _p(bw))
+    return V, boff, badj[: 2 * p], bw[: 2 * p]
+
+
+def louvain_best_move(V, off, adj, w, self_w, cl, vol, i) -> int:
+    """Target cluster of vertex i under the state (cl, vol), or -1."""
+    a = [np.ascontiguousarray(x, t) for x, t in ((off, np.int64), (adj, np.int32), (w, np.int64),
+                                                 (self_w, np.int64), (cl, np.int32), (vol, np.int64))]
+    return int(_L().o_louvain_best_move(V, *[_p(x) for x in a], i))
+
+
+def louvain_aggregate(V, off, adj, w, self_w, cl):
+    """(V2, off2, adj2, w2, self2, cid) of the aggregation of clustering cl."""
+    a = [np.ascontiguousarray(x, t) for x, t in ((off, np.int64), (adj, np.int32), (w, np.int64),
+                                                 (self_w, np.int64), (cl, np.int32))]
+    e = max(len(adj), 1)
+    V2 = ctypes.c_int32(0)
+    off2 = np.zeros(V + 1, np.int64)
+    adj2 = np.zeros(e, np.int32)
+    w2 = np.zeros(e, np.int64)
+    self2 = np.zeros(max(V, 1), np.int64)
+    cid = np.zeros(max(V, 1), np.int32)
+    _L().o_louvain_aggregate(V, *[_p(x) for x in a], ctypes.byref(V2), _p(off2), _p(adj2), _p(w2),
+                             _p(self2), _p(cid))
+    v2 = V2.value
+    q = int(off2[v2])
+    return v2, off2[: v2 + 1].copy(), adj2[:q].copy(), w2[:q].copy(), self2[:v2].copy(), cid[:V].copy()
+
+
+def communities(hg, S: int = 16, seed: int = 1, max_rounds: int = 5, max_levels: int = 32):
+    """(community of every node, Louvain levels aggregated, vertex moves)."""
+    off, pins, w, _ = _arrs(hg)
+    comm = np.zeros(max(hg.n, 1), np.int32)
+    stats = np.zeros(2, np.int64)
+    _L().o_communities(hg.n, hg.m, _p(off), _p(pins), _p(w), S, seed, max_rounds, max_levels,
+                       _p(comm), _p(stats))
+    return comm[: hg.n].copy(), int(stats[0]), int(stats[1])
 
 
 def contract(hg, rep):
@@ -299,23 +360,30 @@ class VCycle:
     objectives: list = field(default_factory=list) # objective after LP per level
     moves: list = field(default_factory=list)
     initial_objective: int = 0
+    communities: object = None                     # community of every node (or None)
 
 
 def multilevel(hg, k: int, eps_ppm: int = 30000, S: int = 16, T: int = 1000, factor: int = 160,
-               seed: int = 1, max_passes: int = 5, max_levels: int = 64) -> VCycle:
+               seed: int = 1, max_passes: int = 5, max_levels: int = 64,
+               communities_first: bool = False) -> VCycle:
     """Algorithm 1 restricted to the deterministic path: coarsen until a stop
     rule fires, seeded initial partition of the coarsest level, then label
     propagation on every level from the coarsest to the finest, projecting
-    between levels."""
+    between levels.  communities_first: detect communities (Sec. 4) before
+    coarsening and keep every contraction inside a community."""
     W = int(np.asarray(hg.node_w, dtype=np.int64).sum())
     vc = VCycle()
     vc.levels.append(hg)
+    comm = communities(hg, S, seed)[0] if communities_first else None
+    vc.communities = comm
     for lv in range(max_levels):
-        r = coarsen(vc.levels[-1], W, k, S, T, factor, seed, lv)
+        r = coarsen(vc.levels[-1], W, k, S, T, factor, seed, lv, comm)
         if r is None:
             break
         vc.maps.append(r["map"])
         vc.levels.append(r["level"])
+        if comm is not None:
+            comm = r["comm"]
         if r["stop_after"]:
             break
     L = len(vc.levels) - 1

@@ -34,7 +34,17 @@
 //    weight-prefix sequences (step into M_st while A[i] <= B[j]) and keep the
 //    last feasible state;
 //  * initial partition: nodes in order of (mix64(seed ^ 2^63 ^ u), u), each to
-//    the currently lightest block, ties to the smaller block id.
+//    the currently lightest block, ties to the smaller block id;
+//  * community detection (Sec. 4 "Community-Aware Coarsening", Sec. 11
+//    "Deterministic Louvain Method"): the bipartite graph of the hypergraph
+//    (a vertex per node, a vertex n + e per net, an edge {v, n + e} per pin)
+//    with edge weight floor(w(e) * 2^20 / |e|), an integer reading of the
+//    fractional w(e) / |e| model; modularity moves compared exactly in 128-bit
+//    integers; vertices in sub-rounds mix64(seed ^ 2^62 ^ level<<32 ^
+//    (round+1)<<48 ^ i) mod S; up to 5 rounds per Louvain level, ending after
+//    a round that moved fewer than 1 % of the vertices; a Louvain level
+//    without any move ends the detection (as do 32 levels); a candidate
+//    cluster of the coarsening rating must lie in u's community.
 //
 // Build: g++ -O2 -std=c++17 -shared -fPIC oracle.cpp -o liboracle.so
 #include <algorithm>
@@ -327,7 +337,7 @@ struct CoarsenResult {
 // function, contraction limit and c_max; Sec. 11 "Deterministic Clustering for
 // Coarsening"; Sec. 4.2 contraction and identical-net removal).
 CoarsenResult coarsen(const Hypergraph& h, int64_t W, int k, int S, int T, int factor, uint64_t seed,
-                      int level) {
+                      int level, const vector<int>* comm = nullptr) {
   CoarsenResult res;
   const int n = h.n;
   if ((int64_t)n <= (int64_t)factor * k) {
@@ -362,6 +372,9 @@ CoarsenResult coarsen(const Hypergraph& h, int64_t W, int k, int S, int T, int f
         for (int v : h.pins[e]) clusters_of_e.insert(rep[v]);
         for (int C : clusters_of_e) {
           if (C == u) continue;
+          // community-aware coarsening (Sec. 4): contractions stay inside a
+          // community (every member of C shares C's community)
+          if (comm && (*comm)[C] != (*comm)[u]) continue;
           if (!joined[C] && subround_clustering(seed, level, C, S) == s) continue;
           if (cw[C] + h.c[u] > c_max) continue;
           rating[C] += term;
@@ -417,6 +430,175 @@ CoarsenResult coarsen(const Hypergraph& h, int64_t W, int k, int S, int T, int f
   res.rated_in = rated_in;
   res.stop_after = 100 * (int64_t)n2 > 99 * (int64_t)n;
   return res;
+}
+
+// ------------------------------------------------------------ communities
+
+// A weighted undirected graph for the Louvain method: adjacency lists (no
+// self entries) and a self-loop weight per vertex.  The degree of vertex i is
+// k_i = sum_j A_ij + 2 self_i, and 2W = sum_i k_i.
+struct LGraph {
+  int V = 0;
+  vector<vector<std::pair<int, int64_t>>> adj;  // (neighbour, weight)
+  vector<int64_t> self;
+};
+
+int64_t lg_degree(const LGraph& g, int i) {
+  int64_t k = 2 * g.self[i];
+  for (auto& a : g.adj[i]) k += a.second;
+  return k;
+}
+
+// The bipartite graph of a hypergraph (Sec. 4, "Community-Aware Coarsening"):
+// vertex v for node v, vertex n + e for net e, an edge {v, n + e} for every
+// pin v of e with weight floor(w(e) * 2^20 / |e|).
+LGraph bipartite_graph(const Hypergraph& h) {
+  LGraph g;
+  g.V = h.n + h.m;
+  g.adj.assign(g.V, {});
+  g.self.assign(g.V, 0);
+  for (int e = 0; e < h.m; ++e) {
+    const int64_t we = ((int64_t)h.w[e] << 20) / (int64_t)h.pins[e].size();
+    for (int v : h.pins[e]) {
+      g.adj[v].push_back({h.n + e, we});
+      g.adj[h.n + e].push_back({v, we});
+    }
+  }
+  return g;
+}
+
+int subround_louvain(uint64_t seed, int level, int round, int i, int S) {
+  uint64_t key = seed ^ (1ULL << 62) ^ ((uint64_t)(uint32_t)level << 32) ^
+                 ((uint64_t)(uint32_t)(round + 1) << 48) ^ (uint64_t)(uint32_t)i;
+  return (int)(mix64(key) % (uint64_t)S);
+}
+
+// The best cluster for vertex i given the clustering cl and the cluster
+// volumes vol (Sec. 11, synchronous local moving): moving i from its cluster
+// A into C changes the modularity by (2 / (2W)^2) (s(C) - s(A)) with
+// s(C) = 2W k_{i,C} - k_i vol(C) for C != A and
+// s(A) = 2W k_{i,A} - k_i (vol(A) - k_i), k_{i,C} the weight of i's edges
+// into C.  Candidates are the clusters of i's neighbours; the largest s wins,
+// ties to the smaller cluster id; i moves only if s(best) > s(A).  Returns
+// the target, or -1 to stay.
+int louvain_best_move(const LGraph& g, const vector<int>& cl, const vector<int64_t>& vol,
+                      int64_t W2, int i) {
+  const int A = cl[i];
+  const int64_t ki = lg_degree(g, i);
+  std::map<int, int64_t> kic;  // k_{i,C} of every neighbouring cluster
+  for (auto& a : g.adj[i]) kic[cl[a.first]] += a.second;
+  using i128 = __int128;
+  const int64_t kia = kic.count(A) ? kic[A] : 0;
+  const i128 s_own = (i128)W2 * kia - (i128)ki * (vol[A] - ki);
+  int best = -1;
+  i128 best_s = 0;
+  for (auto& kv : kic) {  // ascending C: strict > keeps the smaller id on ties
+    if (kv.first == A) continue;
+    const i128 sc = (i128)W2 * kv.second - (i128)ki * vol[kv.first];
+    if (best < 0 || sc > best_s) {
+      best = kv.first;
+      best_s = sc;
+    }
+  }
+  if (best >= 0 && best_s > s_own) return best;
+  return -1;
+}
+
+// Aggregation (the Louvain method's coarsening of the graph): clusters become
+// vertices numbered by the rank of their cluster id; edges between clusters
+// are summed, edges inside a cluster add to its self-loop weight.
+LGraph louvain_aggregate(const LGraph& g, const vector<int>& cl, vector<int>& cid) {
+  cid.assign(g.V, -1);
+  vector<char> used(g.V, 0);
+  for (int i = 0; i < g.V; ++i) used[cl[i]] = 1;
+  int V2 = 0;
+  for (int c = 0; c < g.V; ++c)
+    if (used[c]) cid[c] = V2++;
+  LGraph h;
+  h.V = V2;
+  h.adj.assign(V2, {});
+  h.self.assign(V2, 0);
+  vector<std::map<int, int64_t>> acc(V2);
+  vector<int64_t> internal(V2, 0);  // inside a cluster, each edge seen from both ends
+  for (int i = 0; i < g.V; ++i) {
+    const int ci = cid[cl[i]];
+    h.self[ci] += g.self[i];
+    for (auto& a : g.adj[i]) {
+      const int cj = cid[cl[a.first]];
+      if (cj == ci) internal[ci] += a.second;
+      else acc[ci][cj] += a.second;
+    }
+  }
+  for (int c = 0; c < V2; ++c) {
+    h.self[c] += internal[c] / 2;
+    for (auto& kv : acc[c]) h.adj[c].push_back(kv);
+  }
+  return h;
+}
+
+struct LouvainStats {
+  int levels = 0;
+  int64_t moves = 0;
+};
+
+// Deterministic Louvain method on the bipartite graph (Sec. 4, Sec. 11):
+// per level, up to max_rounds rounds of S synchronous sub-rounds (every
+// vertex of a sub-round picks its move from the state at the sub-round's
+// start; all moves are applied, cluster volumes updated by integer sums), a
+// round moving fewer than 1 % of the vertices ends the level; then the
+// clusters are aggregated into the next level's vertices.  Returns the
+// community of every hypergraph node, numbered by the rank of the final
+// cluster ids.
+vector<int> communities(const Hypergraph& h, int S, uint64_t seed, int max_rounds, int max_levels,
+                        LouvainStats& st) {
+  LGraph g = bipartite_graph(h);
+  vector<int> vmap(h.n);  // hypergraph node -> vertex of the current level
+  for (int v = 0; v < h.n; ++v) vmap[v] = v;
+  int64_t W2 = 0;
+  for (int i = 0; i < g.V; ++i) W2 += lg_degree(g, i);
+  vector<int> cl;
+  for (int level = 0; level < max_levels; ++level) {
+    cl.assign(g.V, 0);
+    vector<int64_t> vol(g.V);
+    for (int i = 0; i < g.V; ++i) {
+      cl[i] = i;
+      vol[i] = lg_degree(g, i);
+    }
+    int64_t level_moves = 0;
+    for (int round = 0; round < max_rounds; ++round) {
+      int64_t moved = 0;
+      for (int s = 0; s < S; ++s) {
+        vector<std::pair<int, int>> moves;
+        for (int i = 0; i < g.V; ++i) {
+          if (subround_louvain(seed, level, round, i, S) != s) continue;
+          const int t = louvain_best_move(g, cl, vol, W2, i);
+          if (t >= 0) moves.push_back({i, t});
+        }
+        for (auto& mv : moves) {
+          const int64_t ki = lg_degree(g, mv.first);
+          vol[cl[mv.first]] -= ki;
+          vol[mv.second] += ki;
+          cl[mv.first] = mv.second;
+        }
+        moved += (int64_t)moves.size();
+      }
+      level_moves += moved;
+      if (100 * moved < (int64_t)g.V) break;
+    }
+    st.moves += level_moves;
+    if (level_moves == 0) break;
+    st.levels = level + 1;
+    vector<int> cid;
+    LGraph next = louvain_aggregate(g, cl, cid);
+    for (int v = 0; v < h.n; ++v) vmap[v] = cid[cl[vmap[v]]];
+    const bool shrank = next.V < g.V;
+    g = std::move(next);
+    cl.clear();
+    if (!shrank) break;
+  }
+  // every level either ended without a move or was aggregated, so the
+  // communities are the vertices of the last graph (numbered 0..V-1 by rank)
+  return vmap;
 }
 
 }  // namespace
@@ -607,14 +789,23 @@ int32_t o_lp_subround(int32_t n, int32_t m, const int32_t* off, const int32_t* p
 // coarse net CSR): rep, target (-2 not rated, -1 no candidate), rated_in
 // (sub-round, -1 if never rated), map (fine -> coarse), the coarse hypergraph
 // in canonical order, and *stop_after = 1 if the level shrank by < 1 %.
+// comm (n entries, may be NULL): community of every node; candidates outside
+// u's community are skipped, and ccomm (capacity n) receives the coarse
+// nodes' communities.
 int32_t o_coarsen(int32_t n, int32_t m, const int32_t* off, const int32_t* pins,
                   const int32_t* w, const int32_t* c, int64_t W, int32_t k, int32_t S, int32_t T,
                   int32_t factor, uint64_t seed, int32_t level, int32_t* rep, int32_t* target,
                   int32_t* rated_in, int32_t* map, int32_t* out_n, int32_t* out_m, int64_t* out_p,
-                  int32_t* coff, int32_t* cpins, int32_t* cw, int32_t* cc, int32_t* stop_after) {
+                  int32_t* coff, int32_t* cpins, int32_t* cw, int32_t* cc, int32_t* stop_after,
+                  const int32_t* comm, int32_t* ccomm) {
   Hypergraph h = load(n, m, off, pins, w, c);
-  CoarsenResult r = coarsen(h, W, k, S, T, factor, seed, level);
+  vector<int> cm;
+  if (comm) cm.assign(comm, comm + n);
+  CoarsenResult r = coarsen(h, W, k, S, T, factor, seed, level, comm ? &cm : nullptr);
   if (r.stop_before) return 1;
+  // coarse communities: every cluster lies inside one community
+  if (comm && ccomm)
+    for (int u = 0; u < n; ++u) ccomm[r.map[u]] = cm[u];
   std::copy(r.rep.begin(), r.rep.end(), rep);
   std::copy(r.target.begin(), r.target.end(), target);
   std::copy(r.rated_in.begin(), r.rated_in.end(), rated_in);
@@ -661,6 +852,90 @@ int32_t o_contract(int32_t n, int32_t m, const int32_t* off, const int32_t* pins
   *out_p = p;
   for (int v = 0; v < H2.n; ++v) cc[v] = H2.c[v];
   return 0;
+}
+
+// Bipartite graph of a hypergraph (Sec. 4): V = n + m vertices, CSR
+// adjacency (capacity 2p) with weights floor(w(e) * 2^20 / |e|).
+void o_bipartite(int32_t n, int32_t m, const int32_t* off, const int32_t* pins, const int32_t* w,
+                 int64_t* boff, int32_t* badj, int64_t* bw) {
+  Hypergraph h = load(n, m, off, pins, w, nullptr);
+  LGraph g = bipartite_graph(h);
+  int64_t q = 0;
+  boff[0] = 0;
+  for (int i = 0; i < g.V; ++i) {
+    for (auto& a : g.adj[i]) {
+      badj[q] = a.first;
+      bw[q] = a.second;
+      ++q;
+    }
+    boff[i + 1] = q;
+  }
+}
+
+namespace {
+LGraph lgraph_from(int32_t V, const int64_t* off, const int32_t* adj, const int64_t* w,
+                   const int64_t* self) {
+  LGraph g;
+  g.V = V;
+  g.adj.assign(V, {});
+  g.self.assign(V, 0);
+  for (int i = 0; i < V; ++i) {
+    g.self[i] = self ? self[i] : 0;
+    for (int64_t q = off[i]; q < off[i + 1]; ++q) g.adj[i].push_back({adj[q], w[q]});
+  }
+  return g;
+}
+}  // namespace
+
+// One Louvain move decision (see louvain_best_move) for vertex i of a graph
+// in CSR form with self-loop weights, clustering cl and volumes vol.
+int32_t o_louvain_best_move(int32_t V, const int64_t* off, const int32_t* adj, const int64_t* w,
+                            const int64_t* self, const int32_t* cl, const int64_t* vol, int32_t i) {
+  LGraph g = lgraph_from(V, off, adj, w, self);
+  vector<int> c(cl, cl + V);
+  vector<int64_t> vo(vol, vol + V);
+  int64_t W2 = 0;
+  for (int x = 0; x < V; ++x) W2 += lg_degree(g, x);
+  return louvain_best_move(g, c, vo, W2, i);
+}
+
+// Aggregation of a clustering (see louvain_aggregate).  Outputs: V2, the
+// coarse CSR (capacity: V + 1 offsets, the input's entries), self-loop
+// weights and cid (cluster id -> coarse vertex, -1 for unused ids).
+void o_louvain_aggregate(int32_t V, const int64_t* off, const int32_t* adj, const int64_t* w,
+                         const int64_t* self, const int32_t* cl, int32_t* out_V2, int64_t* off2,
+                         int32_t* adj2, int64_t* w2, int64_t* self2, int32_t* cid_out) {
+  LGraph g = lgraph_from(V, off, adj, w, self);
+  vector<int> c(cl, cl + V), cid;
+  LGraph h = louvain_aggregate(g, c, cid);
+  *out_V2 = h.V;
+  int64_t q = 0;
+  off2[0] = 0;
+  for (int i = 0; i < h.V; ++i) {
+    for (auto& a : h.adj[i]) {
+      adj2[q] = a.first;
+      w2[q] = a.second;
+      ++q;
+    }
+    off2[i + 1] = q;
+    self2[i] = h.self[i];
+  }
+  for (int x = 0; x < V; ++x) cid_out[x] = cid[x];
+}
+
+// Communities of the hypergraph's nodes (Sec. 4, Sec. 11; see communities).
+// stats: [0] Louvain levels aggregated, [1] vertex moves.
+void o_communities(int32_t n, int32_t m, const int32_t* off, const int32_t* pins, const int32_t* w,
+                   int32_t S, uint64_t seed, int32_t max_rounds, int32_t max_levels, int32_t* comm,
+                   int64_t* stats) {
+  Hypergraph h = load(n, m, off, pins, w, nullptr);
+  LouvainStats st;
+  vector<int> c = communities(h, S, seed, max_rounds, max_levels, st);
+  std::copy(c.begin(), c.end(), comm);
+  if (stats) {
+    stats[0] = st.levels;
+    stats[1] = st.moves;
+  }
 }
 
 // Projection Pi_fine[u] = Pi_coarse[map[u]] (Algorithm 1, uncoarsening).

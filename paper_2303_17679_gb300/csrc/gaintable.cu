@@ -17,6 +17,13 @@
 // lemma of Sec. 6.2 the final penalties of all nodes and the final benefits
 // of the unmoved nodes do not depend on it; the benefits of the moved nodes
 // are recomputed from the final pin counts afterwards.
+//
+// Graph levels (Sec. 10, "The Gain Table"): the table of a graph is
+// w(u, V_i), the weight of u's edges into V_i, one warp per node over its
+// adjacency list; the benefit and penalties follow from it:
+//   b(u) = w(I(u)) - w(u, V_Pi(u)),  p(u, V_Pi(u)) = 0,
+//   p(u, V_i) = w(I(u)) - w(u, V_i) for i != Pi(u)
+// (an edge has no pin in V_i exactly when neither endpoint is in V_i).
 #include "common.cuh"
 
 namespace hgk {
@@ -69,6 +76,42 @@ k_gt_build(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
     if (lane == 0) b[u] = bu;
     for (int i = lane; i < k; i += 32) {
       p[u * k + i] = wsum - (cnt[i] + full);
+      cnt[i] = 0;
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(GT_WARPS * 32)
+k_gt_build_graph(const int32_t* __restrict__ ioff, const int2* __restrict__ adj,
+                 const int32_t* __restrict__ part, int32_t n, int k, long long* __restrict__ b,
+                 long long* __restrict__ p, int32_t* status) {
+  __shared__ long long s_cnt[GT_WARPS][HG_MAX_K];
+  const int wv = warp_in_block(), lane = lane_id();
+  long long* cnt = s_cnt[wv];
+  for (int i = lane; i < HG_MAX_K; i += 32) cnt[i] = 0;
+  __syncwarp();
+  for (int64_t u = (int64_t)blockIdx.x * GT_WARPS + wv; u < n; u += (int64_t)gridDim.x * GT_WARPS) {
+    const int32_t pu = part[u];
+    if (pu < 0 || pu >= k) {  // bad input: reported, never indexed
+      if (lane == 0) dev_fail(status, DEV_BAD_INPUT);
+      continue;
+    }
+    long long wsum = 0;
+    for (int32_t j = ioff[u] + lane; j < ioff[u + 1]; j += 32) {
+      const int2 a = adj[j];
+      const int32_t pv = part[a.x];
+      wsum += a.y;
+      if (pv >= 0 && pv < k)
+        atomicAdd(reinterpret_cast<unsigned long long*>(&cnt[pv]), (unsigned long long)a.y);
+      else
+        dev_fail(status, DEV_BAD_INPUT);
+    }
+    wsum = warp_sum(wsum);
+    __syncwarp();
+    if (lane == 0) b[u] = wsum - cnt[pu];
+    for (int i = lane; i < k; i += 32) {
+      p[u * k + i] = i == pu ? 0 : wsum - cnt[i];
       cnt[i] = 0;
     }
     __syncwarp();
@@ -157,6 +200,15 @@ __global__ void k_gt_moved_benefit(const int32_t* __restrict__ nodes, int32_t l,
 void gain_table_build(const Ctx& cx, const Level& L, int k, const int32_t* part, int64_t* b,
                       int64_t* p) {
   validate_partition(cx, part, L.n, k);
+  if (L.graph) {
+    k_gt_build_graph<<<grid_for(L.n, GT_WARPS, cx.num_sms, 16), GT_WARPS * 32, 0, cx.stream>>>(
+        L.ioff.p, L.adj.p, part, L.n, k, reinterpret_cast<long long*>(b),
+        reinterpret_cast<long long*>(p), cx.d_status);
+    check_launch("gt_build_graph");
+    if (cx.launches) *cx.launches += 1;
+    check_status(cx);
+    return;
+  }
   DBuf<int32_t> phi;
   DBuf<unsigned long long> lam;
   device_pin_counts(cx, L, k, part, phi, lam);

@@ -107,3 +107,35 @@ def test_graph_lp_and_objective_from_a_random_partition(oracle_mod, k):
         assert obj == ref["objective"] and moves == ref["moves"]
     finally:
         hg.hg_destroy(h)
+
+
+@pytest.mark.parametrize("k", [2, 16, 64])
+def test_graph_gain_table_matches_oracle_and_moves(oracle_mod, k):
+    """The graph form of the gain table (from w(u, V_i)) equals the oracle's
+    table of Sec. 6.2; a concurrent move set then gives the new partition's
+    table (the moves run through the hypergraph update rules)."""
+    hgr = synth.graph_preferential(31, 15_000, 50_000, 1, 20)
+    rng = np.random.default_rng(k + 1)
+    part0 = rng.integers(0, k, size=hgr.n).astype(np.int32)
+    stream = torch.cuda.current_stream()
+    h = hg.hg_create(hgr.n, hgr.m, hgr.offsets, hgr.pins, hgr.net_w, hgr.node_w,
+                     hg.HG_MEM_HOST, None, stream)
+    try:
+        assert hg.hg_level_is_graph(h, 0)
+        d = torch.from_numpy(part0.copy()).cuda()
+        b = torch.zeros(hgr.n, dtype=torch.int64, device="cuda")
+        p = torch.zeros((hgr.n, k), dtype=torch.int64, device="cuda")
+        hg.hg_gain_table(h, 0, k, d, b, p)
+        rb, rp = oracle_mod.gain_table(hgr, k, part0)
+        assert np.array_equal(b.cpu().numpy(), rb) and np.array_equal(p.cpu().numpy(), rp)
+        nodes = rng.permutation(hgr.n)[: hgr.n // 5].astype(np.int32)
+        targets = ((part0[nodes] + 1 + rng.integers(0, k - 1, size=len(nodes))) % k).astype(np.int32)
+        hg.hg_gain_table_move(h, 0, k, d, torch.from_numpy(nodes).cuda(),
+                              torch.from_numpy(targets).cuda(), b, p)
+        part1 = part0.copy()
+        part1[nodes] = targets
+        assert np.array_equal(d.cpu().numpy(), part1)
+        rb, rp = oracle_mod.gain_table(hgr, k, part1)
+        assert np.array_equal(b.cpu().numpy(), rb) and np.array_equal(p.cpu().numpy(), rp)
+    finally:
+        hg.hg_destroy(h)
