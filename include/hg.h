@@ -112,6 +112,9 @@ typedef struct {
    * without pin counts.  Contraction keeps a graph a graph.  1 = always use
    * the hypergraph path.  Results are identical either way. */
   int32_t graph_path;
+  /* 1: hg_partition first detects communities (hg_detect_communities) and
+   * keeps every contraction inside a community.  0 (default): off. */
+  int32_t community_detection;
 } hg_options;
 
 /* Per-phase device time (milliseconds, from CUDA events) and work counters,
@@ -148,6 +151,10 @@ typedef struct {
   int64_t lp_moved_incidences; /* incident nets of the moved nodes */
   int64_t lp_passes;           /* label-propagation passes run */
   int64_t timing_failures;     /* kernel-timing event pairs that could not be read */
+  double ms_communities;       /* community detection (timing flag 1) */
+  int64_t louvain_levels;      /* Louvain levels aggregated */
+  int64_t louvain_rounds;      /* local-moving rounds */
+  int64_t louvain_moves;       /* vertex moves of the local moving */
 } hg_stats;
 
 /* Fills *opt with the defaults listed above (seed 1). */
@@ -314,8 +321,32 @@ int hg_objective_noalloc(int32_t n, int32_t m, int64_t p, const int32_t* net_off
                          const int32_t* node_weights, int32_t k, const int32_t* part,
                          void* cuda_stream, int64_t* out_objective, int64_t* out_block_weights);
 
+/* Community detection (Sec. 4, "Community-Aware Coarsening"; Sec. 11,
+ * "Deterministic Louvain Method") on level 0, before any coarsening; the
+ * communities then restrict every later clustering step: a node only joins
+ * a cluster of its own community, and coarse nodes inherit it.
+ * The hypergraph is turned into its bipartite graph (a vertex per node and
+ * per net, an edge {v, n + e} of weight floor(w(e) * 2^20 / |e|) per pin) and
+ * the Louvain method maximises its modularity: per level up to 5 rounds of S
+ * synchronous sub-rounds (vertex i in sub-round
+ * mix64(seed ^ 2^62 ^ level<<32 ^ (round+1)<<48 ^ i) mod S), every vertex of
+ * a sub-round moving to the neighbouring cluster with the largest modularity
+ * gain (exact 128-bit integer comparison, ties to the smaller id) when that
+ * beats staying; a round moving fewer than 1 % of the vertices ends a level,
+ * a level without moves ends the method; clusters are then aggregated into
+ * the next level's vertices (numbered by the rank of the cluster id).  The
+ * community of a node is its vertex in the last level.
+ *   out_communities  host, may be NULL: number of distinct communities
+ * HG_ERR_STATE once a level has been coarsened.  Synchronizes the stream. */
+int hg_detect_communities(hg_t* h, int32_t* out_communities);
+
+/* Copies the community of every node of a level (host, n_level int32).
+ * HG_ERR_STATE when no communities were detected. */
+int hg_get_communities(const hg_t* h, int32_t level, int32_t* comm);
+
 /* The whole deterministic multilevel path (Algorithm 1 without FM and
- * flows): coarsen until HG_STOP, initial partition of the coarsest level,
+ * flows): with hg_options.community_detection, communities first; then
+ * coarsen until HG_STOP, initial partition of the coarsest level,
  * label propagation on it, then project and refine level by level down to
  * level 0.  part: device, n_0 int32, written.  Levels already built are
  * reused; the handle keeps all levels afterwards. */

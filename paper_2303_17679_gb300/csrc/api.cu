@@ -184,7 +184,8 @@ int hg_create(int32_t n, int32_t m, const int32_t* net_offsets, const int32_t* p
       o.rate_pair_max_d > 1024 || o.rate_quad_max_d < 0 || o.rate_quad_max_d > 2048 ||
       o.rate_block_max_d < 0 || o.rate_block_max_d > 4096 || o.lp_block_min_deg < 0 ||
       o.lp_block_min_deg > (1 << 20) || o.blocking_sync < 0 || o.blocking_sync > 1 ||
-      o.graph_path < 0 || o.graph_path > 1)
+      o.graph_path < 0 || o.graph_path > 1 || o.community_detection < 0 ||
+      o.community_detection > 1)
     return HG_ERR_INVALID;
   int64_t W = 0;
   int64_t p = 0;
@@ -479,12 +480,51 @@ int hg_pin_counts(hg_t* h, int32_t level, int32_t k, const int32_t* part, int32_
   });
 }
 
+int hg_detect_communities(hg_t* h, int32_t* out_communities) {
+  if (!h) return HG_ERR_INVALID;
+  if (h->levels.size() != 1) return HG_ERR_STATE;  // before any coarsening
+  return guarded(h, [&]() -> int {
+    hgk::EventTimer tm(h->cx, &h->stats.ms_communities);
+    Level& L = *h->levels[0];
+    hgk::LouvainCounters lc;
+    DBuf<int32_t> comm;
+    const int32_t count =
+        hgk::detect_communities(h->cx, L, h->opt.subrounds, h->opt.seed, comm, lc);
+    L.comm = std::move(comm);
+    h->stats.louvain_levels += lc.levels;
+    h->stats.louvain_rounds += lc.rounds;
+    h->stats.louvain_moves += lc.moves;
+    h->launches += lc.launches;
+    if (out_communities) *out_communities = count;
+    sync_stats(h);
+    return HG_OK;
+  });
+}
+
+int hg_get_communities(const hg_t* hc, int32_t level, int32_t* comm) {
+  hg_t* h = const_cast<hg_t*>(hc);
+  if (!h || !comm) return HG_ERR_INVALID;
+  if (!valid_level(h, level)) return HG_ERR_STATE;
+  const Level& L = *h->levels[level];
+  if (!L.comm.p) return HG_ERR_STATE;
+  return guarded(h, [&]() -> int {
+    HG_CUDA(cudaMemcpyAsync(comm, L.comm.p, sizeof(int32_t) * (size_t)L.n, cudaMemcpyDeviceToHost,
+                            h->cx.stream));
+    HG_CUDA(cudaStreamSynchronize(h->cx.stream));
+    return HG_OK;
+  });
+}
+
 int hg_partition(hg_t* h, int32_t k, int32_t eps_ppm, int32_t max_passes, int32_t* part,
                  int64_t* out_objective) {
   if (!h || !part) return HG_ERR_INVALID;
   if (k < 2 || k > HG_MAX_K || eps_ppm < 0 || max_passes < 0) return HG_ERR_INVALID;
   if (h->sticky) return h->sticky;
   int rc;
+  if (h->opt.community_detection && h->levels.size() == 1 && !h->levels[0]->comm.p) {
+    rc = hg_detect_communities(h, nullptr);
+    if (rc != HG_OK) return rc;
+  }
   while ((rc = hg_coarsen_level(h, k, nullptr, nullptr, nullptr, nullptr)) == HG_OK) {
   }
   if (rc != HG_STOP) return rc;

@@ -102,6 +102,12 @@ struct RateArgs {
   bool graph;
   const int2* adj;
   const int32_t* rep;
+  // community-aware coarsening (Sec. 4): comm[v] per node, pcomm[q] =
+  // comm[pins[q]] per pin position (hypergraph levels); both NULL when off.
+  // A cluster's members share its community, so the pin's community is the
+  // community of the pin's cluster.
+  const int32_t* comm;
+  const int32_t* pcomm;
   const unsigned long long* rterm;  // Q20 net term of every rated net, 0 otherwise
   const int32_t* c;
   const int2* cst;  // {cw, status}
@@ -251,16 +257,23 @@ __device__ __forceinline__ EachVisit<VT, F> each_visit(F f) {
 // needs no deduplication: u is a singleton, so rep[q] != u) and whose weight
 // word is the cluster's weight, or INT32_MAX for an unclustered node of this
 // sub-round.
+// cmu >= 0: u's community; a visit in another community is dropped.
 __device__ __forceinline__ void resolve_batch(const RateArgs& A, const int32_t (&q)[RATE_ILP],
-                                              int2 (&ri)[RATE_ILP]) {
+                                              int2 (&ri)[RATE_ILP], int32_t cmu) {
   if (!A.graph) {
 #pragma unroll
     for (int k = 0; k < RATE_ILP; ++k) ri[k] = q[k] >= 0 ? A.rinfo[q[k]] : make_int2(-1, 0);
+    if (cmu >= 0) {
+#pragma unroll
+      for (int k = 0; k < RATE_ILP; ++k)
+        if (ri[k].x >= 0 && A.pcomm[q[k]] != cmu) ri[k].x = -1;
+    }
     return;
   }
   int32_t C[RATE_ILP];
 #pragma unroll
-  for (int k = 0; k < RATE_ILP; ++k) C[k] = q[k] >= 0 ? A.rep[q[k]] : -1;
+  for (int k = 0; k < RATE_ILP; ++k)
+    C[k] = q[k] >= 0 && (cmu < 0 || A.comm[q[k]] == cmu) ? A.rep[q[k]] : -1;
 #pragma unroll
   for (int k = 0; k < RATE_ILP; ++k) {
     const int2 cs = C[k] >= 0 ? A.cst[C[k]] : make_int2(0, 0);
@@ -276,7 +289,7 @@ __device__ __forceinline__ void visit_filtered(const RateArgs& A, int32_t u, int
                                                const int32_t (&q)[RATE_ILP],
                                                const VT (&rr)[RATE_ILP], Add& add) {
   int2 ri[RATE_ILP];
-  resolve_batch(A, q, ri);
+  resolve_batch(A, q, ri, A.comm ? A.comm[u] : -1);
   int32_t C[RATE_ILP];
   bool ok[RATE_ILP];
 #pragma unroll
@@ -796,9 +809,10 @@ k_rate_part(RateArgs A, const int32_t* __restrict__ split, const int32_t* __rest
     // other counter is cleared for the next part once every thread has read
     // this one
     int32_t* nused = &s_nused[it & 1];
+    const int32_t cmu = A.comm ? A.comm[u] : -1;
     auto visit = [&](const int32_t(&q)[RATE_ILP], const VT(&rr)[RATE_ILP]) HG_INLINE {
       int2 ri[RATE_ILP];
-      resolve_batch(A, q, ri);
+      resolve_batch(A, q, ri, cmu);
 #pragma unroll
       for (int j = 0; j < RATE_ILP; ++j) {
         const int32_t Cj = ri[j].x;
@@ -1409,6 +1423,14 @@ k_rinfo_init(const int32_t* __restrict__ eoff, const int32_t* __restrict__ pins,
   }
 }
 
+// pcomm[q] = comm[pins[q]] for every pin position.
+__global__ void k_pin_comm(const int32_t* __restrict__ pins, int64_t p,
+                           const int32_t* __restrict__ comm, int32_t* __restrict__ pcomm) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < p;
+       q += (int64_t)gridDim.x * blockDim.x)
+    pcomm[q] = comm[pins[q]];
+}
+
 // Weight words of every record before sub-round s: the cluster's weight, or
 // INT32_MAX for an unclustered node of sub-round s.  Two records per thread
 // and iteration (16-byte loads and stores).
@@ -1797,6 +1819,17 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   A.graph = L.graph;
   A.adj = L.adj.p;
   A.rep = L.rep.p;
+  A.comm = L.comm.p;
+  A.pcomm = nullptr;
+  DBuf<int32_t> pcomm;
+  if (L.comm.p && !L.graph && L.p > 0) {
+    pcomm.alloc(&cx.alloc, (size_t)L.p);
+    k_pin_comm<<<grid_for(L.p, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(L.pins.p, L.p, L.comm.p,
+                                                                         pcomm.p);
+    check_launch("pin_comm");
+    if (cx.launches) *cx.launches += 1;
+    A.pcomm = pcomm.p;
+  }
   A.rterm = rterm.p;
   A.c = L.c.p;
   A.cst = cst.p;

@@ -261,6 +261,9 @@ struct Level {
   // aligned with inets.  The coarse level of a graph level is a graph level.
   bool graph = false;
   DBuf<int2> adj;       // p (graph levels only)
+  // community of every node (Sec. 4, community-aware coarsening), when
+  // detected: contractions stay inside a community
+  DBuf<int32_t> comm;   // n (or empty)
 };
 
 // --------------------------------------------------------- primitives (prim.cu)
@@ -338,6 +341,18 @@ struct ContractCounters {
 // Contraction of L's clustering into a new level (a5-a8); fills L.map.
 void contract_level(const Ctx& cx, Level& L, const int32_t* cw, Level& out, int fingerprint_bits,
                     ContractCounters& kc);
+
+// ----------------------------------------------- communities (community.cu)
+
+struct LouvainCounters {
+  int64_t levels = 0, rounds = 0, moves = 0, launches = 0;
+};
+
+// Deterministic Louvain community detection on the bipartite graph of L
+// (Sec. 4, Sec. 11): comm receives the community of every node; returns the
+// number of distinct communities.
+int32_t detect_communities(const Ctx& cx, const Level& L, int S, uint64_t seed,
+                           DBuf<int32_t>& comm, LouvainCounters& lc);
 
 // ------------------------------------------------------- refinement (refine.cu)
 

@@ -330,6 +330,24 @@ __global__ void k_compact(const int32_t* __restrict__ keep, const int32_t* __res
   }
 }
 
+// Community of every coarse node: the community of its members (a cluster
+// never spans two communities).
+__global__ void k_coarse_comm(const int32_t* __restrict__ map, const int32_t* __restrict__ comm,
+                              int32_t n, int32_t* __restrict__ ccomm) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x)
+    ccomm[map[u]] = comm[u];
+}
+
+void coarse_communities(const Ctx& cx, const Level& L, Level& out) {
+  if (!L.comm.p) return;
+  out.comm.alloc(&cx.alloc, (size_t)std::max<int32_t>(out.n, 1));
+  k_coarse_comm<<<grid_for(L.n, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(L.map.p, L.comm.p, L.n,
+                                                                        out.comm.p);
+  check_launch("coarse_comm");
+  if (cx.launches) *cx.launches += 1;
+}
+
 }  // namespace
 
 void contract_level(const Ctx& cx, Level& L, const int32_t* cw, Level& out, int fingerprint_bits,
@@ -359,6 +377,7 @@ void contract_level(const Ctx& cx, Level& L, const int32_t* cw, Level& out, int 
     out.eoff.alloc(&cx.alloc, 1);
     HG_CUDA(cudaMemsetAsync(out.eoff.p, 0, sizeof(int32_t), cx.stream));
     build_incidence(cx, out);
+    coarse_communities(cx, L, out);
     L.coarsened = true;
     return;
   }
@@ -473,6 +492,7 @@ void contract_level(const Ctx& cx, Level& L, const int32_t* cw, Level& out, int 
   build_incidence(cx, out);
   // a graph's coarse nets have two pins again (one-pin nets are dropped)
   if (L.graph && out.m > 0) build_graph_adjacency(cx, out);
+  coarse_communities(cx, L, out);
   L.coarsened = true;
 }
 

@@ -50,6 +50,7 @@ class hg_options(ctypes.Structure):
         ("lp_block_min_deg", ctypes.c_int32),
         ("blocking_sync", ctypes.c_int32),
         ("graph_path", ctypes.c_int32),
+        ("community_detection", ctypes.c_int32),
     ]
 
     TUNABLE = ("rate_warp_max_d", "rate_pair_max_d", "rate_quad_max_d", "rate_block_max_d",
@@ -91,7 +92,9 @@ class hg_stats(ctypes.Structure):
         ("ms_rating_class", ctypes.c_double * 8), ("rating_visits_class", ctypes.c_int64 * 8),
         ("ms_lp_select_kernels", ctypes.c_double), ("ms_lp_apply_kernels", ctypes.c_double),
         ("lp_moved_incidences", ctypes.c_int64), ("lp_passes", ctypes.c_int64),
-        ("timing_failures", ctypes.c_int64)]
+        ("timing_failures", ctypes.c_int64), ("ms_communities", ctypes.c_double),
+        ("louvain_levels", ctypes.c_int64), ("louvain_rounds", ctypes.c_int64),
+        ("louvain_moves", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}
@@ -150,6 +153,8 @@ def load(path: str | None = None):
             "hg_destroy": (ctypes.c_int, [H]),
             "hg_trim_memory": (ctypes.c_int, []),
             "hg_level_is_graph": (ctypes.c_int, [H, i32, P(i32)]),
+            "hg_detect_communities": (ctypes.c_int, [H, P(i32)]),
+            "hg_get_communities": (ctypes.c_int, [H, i32, vp]),
             "hg_calibrate_smem_atomics": (ctypes.c_int, [vp, P(ctypes.c_double),
                                                          P(ctypes.c_double)]),
             "hg_exec_create": (ctypes.c_int, [i32, i64, P(hg_options), P(H)]),
@@ -175,7 +180,7 @@ def exported_symbols():
             "hg_level_info", "hg_initial_partition", "hg_project", "hg_lp_refine",
             "hg_objective", "hg_pin_counts", "hg_recalculate_gains", "hg_gain_table", "hg_gain_table_move",
             "hg_objective_noalloc", "hg_partition", "hg_get_level", "hg_get_incidence",
-            "hg_truncate", "hg_enable_timing", "hg_get_stats", "hg_reset_stats", "hg_destroy", "hg_trim_memory", "hg_level_is_graph", "hg_calibrate_smem_atomics",
+            "hg_truncate", "hg_enable_timing", "hg_get_stats", "hg_reset_stats", "hg_destroy", "hg_trim_memory", "hg_level_is_graph", "hg_detect_communities", "hg_get_communities", "hg_calibrate_smem_atomics",
             "hg_exec_create", "hg_exec_submit", "hg_exec_wait", "hg_exec_pending",
             "hg_exec_now_ns", "hg_exec_destroy", "hg_strerror", "hg_version"]
 
@@ -269,6 +274,20 @@ def hg_num_levels(h) -> int:
     x = ctypes.c_int32()
     _check(load().hg_num_levels(h, ctypes.byref(x)), "hg_num_levels")
     return x.value
+
+
+def hg_detect_communities(h) -> int:
+    """Detects communities on level 0 (before coarsening); returns their number."""
+    x = ctypes.c_int32()
+    _check(load().hg_detect_communities(h, ctypes.byref(x)), "hg_detect_communities")
+    return x.value
+
+
+def hg_get_communities(h, level):
+    n, _, _ = hg_level_info(h, level)
+    out = np.zeros(max(n, 1), np.int32)
+    _check(load().hg_get_communities(h, int(level), _ptr(out)), "hg_get_communities")
+    return out[:n]
 
 
 def hg_level_is_graph(h, level) -> bool:
