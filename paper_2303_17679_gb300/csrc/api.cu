@@ -47,6 +47,10 @@ int guarded(hg_t* h, F&& body) {
   }
 }
 
+// Host inputs with at most this many pins have their pins checked on the
+// host, larger ones on the device.
+constexpr int64_t HOST_PIN_CHECK_MAX = 1 << 16;
+
 bool valid_level(const hg_t* h, int32_t level) {
   return level >= 0 && level < (int32_t)h->levels.size();
 }
@@ -75,18 +79,21 @@ bool check_pins_range(int32_t n, const int32_t* off, const int32_t* pins, int32_
   return true;
 }
 
-// Host-side checks of a host CSR (hg_create contract).  The pin checks run
-// on up to 8 host threads over ranges of nets.
+// Host-side checks of a host CSR (hg_create contract): offsets and weights,
+// and the pins when `pins` is given (on up to 8 host threads over ranges of
+// nets; hg_create passes NULL and checks the pins on the device instead).
 int check_host_csr(int32_t n, int32_t m, const int32_t* off, const int32_t* pins, const int32_t* w,
                    const int32_t* c, int64_t* W) {
   if (off[0] != 0) return HG_ERR_INVALID;
   for (int32_t e = 0; e < m; ++e)
     if (off[e + 1] <= off[e]) return HG_ERR_INVALID;  // decreasing or empty net
-  const int64_t p = off[m];
+  const int64_t p = pins ? off[m] : 0;
   const int threads = (int)std::max<int64_t>(
       1, std::min<int64_t>({8, (int64_t)std::thread::hardware_concurrency(), p / (1 << 20) + 1}));
   std::vector<char> ok((size_t)threads, 1);
-  if (threads == 1) {
+  if (!pins) {
+    // pins checked elsewhere
+  } else if (threads == 1) {
     std::vector<int32_t> stamp;
     ok[0] = check_pins_range(n, off, pins, 0, m, stamp);
   } else {
@@ -193,7 +200,12 @@ int hg_create(int32_t n, int32_t m, const int32_t* net_offsets, const int32_t* p
     p = net_offsets[m];
     if (p > 0 && !pins) return HG_ERR_INVALID;
     if (p < 0 || p >= (1ll << 31)) return HG_ERR_INVALID;
-    const int rc = check_host_csr(n, m, net_offsets, pins, net_weights, node_weights, &W);
+    // offsets and weights here; the pins (ranges and repeats inside a net,
+    // O(p) host work per call) here too for small inputs, else on the device
+    // after the upload, which keeps concurrent callers' host threads free
+    const bool host_pins = p <= HOST_PIN_CHECK_MAX;
+    const int rc = check_host_csr(n, m, net_offsets, host_pins ? pins : nullptr, net_weights,
+                                  node_weights, &W);
     if (rc != HG_OK) return rc;
   }
   auto h = std::make_unique<hg_t>();
@@ -234,7 +246,10 @@ int hg_create(int32_t n, int32_t m, const int32_t* net_offsets, const int32_t* p
     upload(h->cx, L->pins, pins, (size_t)p, mem, 0);
     upload(h->cx, L->w, net_weights, (size_t)m, mem, 1);
     upload(h->cx, L->c, node_weights, (size_t)n, mem, 1);
-    if (mem == HG_MEM_DEVICE) {
+    if (mem == HG_MEM_HOST) {
+      if (p > HOST_PIN_CHECK_MAX && !hgk::validate_pins_device(h->cx, *L))
+        throw HgError(HG_ERR_INVALID, "pins failed validation");
+    } else {
       int64_t wn = 0, ww = 0;
       if (!hgk::validate_level_device(h->cx, *L, &wn, &ww))
         throw HgError(HG_ERR_INVALID, "device input failed validation");

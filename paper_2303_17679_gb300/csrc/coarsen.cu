@@ -1601,6 +1601,29 @@ void rate_subround(const Ctx& cx, RateArgs A, const std::vector<int32_t>& hoff, 
   }
 }
 
+// A private stream of the calling host thread on its current device, for
+// capturing a level's sub-round loop (the caller's stream may be the legacy
+// default stream, which cannot be captured).
+cudaStream_t level_capture_stream() {
+  struct Cache {
+    int device = -1;
+    cudaStream_t s = nullptr;
+    ~Cache() {
+      if (s) cudaStreamDestroy(s);
+    }
+  };
+  thread_local Cache cache;
+  int dev = 0;
+  HG_CUDA(cudaGetDevice(&dev));
+  if (cache.device != dev) {
+    if (cache.s) cudaStreamDestroy(cache.s);
+    cache.s = nullptr;
+    HG_CUDA(cudaStreamCreateWithFlags(&cache.s, cudaStreamNonBlocking));
+    cache.device = dev;
+  }
+  return cache.s;
+}
+
 }  // namespace
 
 void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCounters& cc,
@@ -1847,13 +1870,18 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
 
   std::vector<KernelTimer> rate_timers;
   for (int c = 0; c < NCLASS; ++c) rate_timers.emplace_back(cx);
+  // The S sub-rounds have no host interaction after the readbacks above, so
+  // without phase or kernel timing they are captured as one CUDA graph per
+  // level and launched once (lx = the context whose stream the launches go
+  // to; nothing is allocated inside the loop).
+  auto subrounds = [&](const Ctx& lx) {
   for (int s = 0; s < S; ++s) {
     A.s = s;
     A.words = words.p + (size_t)s * CW_WORDS;
     int32_t* w_s = words.p + (size_t)s * CW_WORDS;
     if (records) {
       EventTimer tm(cx, &cc.ms_refresh);
-      k_rinfo_refresh<<<grid_for(L.p / 2 + 1, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(
+      k_rinfo_refresh<<<grid_for(L.p / 2 + 1, 256, cx.num_sms, 8), 256, 0, lx.stream>>>(
           rinfo.p, L.p, cst.p, s);
       check_launch("rinfo_refresh");
       if (cx.launches) *cx.launches += 1;
@@ -1862,28 +1890,28 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
       EventTimer tm(cx, &cc.ms_rating);
       const int64_t before = cc.rating_launches;
       if (narrow)
-        rate_subround<uint32_t>(cx, A, hoff, list.p, S, s, dense_block, sp, rate_timers.data(),
+        rate_subround<uint32_t>(lx, A, hoff, list.p, S, s, dense_block, sp, rate_timers.data(),
                                 stats.p, cc);
       else
-        rate_subround<unsigned long long>(cx, A, hoff, list.p, S, s, dense_block, sp,
+        rate_subround<unsigned long long>(lx, A, hoff, list.p, S, s, dense_block, sp,
                                           rate_timers.data(), stats.p, cc);
       if (cx.launches) *cx.launches += cc.rating_launches - before;
     }
     {
       EventTimer tm(cx, &cc.ms_approve);
       const int g = grid_for((n + S - 1) / S, 256, cx.num_sms, 4);
-      k_approve<<<g, 256, 0, cx.stream>>>(mv.p, w_s, target.p, cst.p, gw.p, gcnt.p, P.c_max,
+      k_approve<<<g, 256, 0, lx.stream>>>(mv.p, w_s, target.p, cst.p, gw.p, gcnt.p, P.c_max,
                                           L.rep.p, slot_of.p, slot_c.p, slot_off.p,
                                           w_s + CW_SLOTS, w_s + CW_CURSOR);
       check_launch("approve");
-      k_contest_scatter<<<g, 256, 0, cx.stream>>>(mv.p, w_s, target.p, cst.p, gw.p, P.c_max,
+      k_contest_scatter<<<g, 256, 0, lx.stream>>>(mv.p, w_s, target.p, cst.p, gw.p, P.c_max,
                                                   slot_of.p, slot_off.p, slot_fill.p, glist.p);
       check_launch("contest_scatter");
-      k_contest_group<<<cx.num_sms, GROUP_THREADS, 0, cx.stream>>>(
+      k_contest_group<<<cx.num_sms, GROUP_THREADS, 0, lx.stream>>>(
           w_s, slot_c.p, slot_off.p, slot_fill.p, slot_of.p, glist.p, gcnt.p, L.c.p, P.c_max,
           cst.p, L.rep.p, clusters.p);
       check_launch("contest_group");
-      k_finish<<<g, 256, 0, cx.stream>>>(touched.p, w_s, P.c_max, cst.p, gw.p, gcnt.p, clusters.p);
+      k_finish<<<g, 256, 0, lx.stream>>>(touched.p, w_s, P.c_max, cst.p, gw.p, gcnt.p, clusters.p);
       check_launch("finish");
       if (cx.launches) *cx.launches += 4;
     }
@@ -1895,18 +1923,44 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
         R.hi[c] = hoff[c * S + s + 1];
       }
       const int g = cx.num_sms * 8;
-      k_posmap_pass<true><<<g, 256, 0, cx.stream>>>(list.p, lpre.p, R, L.rep.p, L.ioff.p,
+      k_posmap_pass<true><<<g, 256, 0, lx.stream>>>(list.p, lpre.p, R, L.rep.p, L.ioff.p,
                                                     L.inets.p, L.ipin.p, L.eoff.p, P.T, pm,
                                                     jslot.p, reinterpret_cast<int32_t*>(rinfo.p),
                                                     cx.d_status);
       check_launch("posmap_join");
-      k_posmap_pass<false><<<g, 256, 0, cx.stream>>>(list.p, lpre.p, R, L.rep.p, L.ioff.p,
+      k_posmap_pass<false><<<g, 256, 0, lx.stream>>>(list.p, lpre.p, R, L.rep.p, L.ioff.p,
                                                      L.inets.p, L.ipin.p, L.eoff.p, P.T, pm,
                                                      jslot.p, reinterpret_cast<int32_t*>(rinfo.p),
                                                     cx.d_status);
       check_launch("posmap_fix");
       if (cx.launches) *cx.launches += 2;
     }
+  }
+  };
+  if (!cx.timing && !cx.kernel_timing) {
+    set_rate_attrs<uint32_t>();
+    set_rate_attrs<unsigned long long>();
+    Ctx lx = cx;
+    lx.stream = level_capture_stream();
+    cudaGraph_t graph = nullptr;
+    HG_CUDA(cudaStreamBeginCapture(lx.stream, cudaStreamCaptureModeThreadLocal));
+    try {
+      subrounds(lx);
+    } catch (...) {
+      cudaStreamEndCapture(lx.stream, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    HG_CUDA(cudaStreamEndCapture(lx.stream, &graph));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    HG_CUDA(ie);
+    const cudaError_t le = cudaGraphLaunch(exec, cx.stream);
+    cudaGraphExecDestroy(exec);  // freed once the launch completes
+    HG_CUDA(le);
+  } else {
+    subrounds(cx);
   }
   for (int c = 0; c < NCLASS; ++c) {
     const double ms = rate_timers[c].flush();

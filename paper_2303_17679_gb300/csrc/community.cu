@@ -469,37 +469,63 @@ __global__ void k_lv_agg_insert(const int32_t* __restrict__ members, const long 
   }
 }
 
-// Distinct neighbours of every coarse vertex (a warp per table).
+// The coarse vertex owning table slot s: the largest c with toff[c] <= s.
+__device__ __forceinline__ int32_t table_owner(const long long* toff, int32_t V2, long long s) {
+  int32_t a = 0, b = V2 - 1;
+  while (a < b) {
+    const int32_t mid = (a + b + 1) >> 1;
+    if (toff[mid] <= s) a = mid;
+    else b = mid - 1;
+  }
+  return a;
+}
+
+// Distinct neighbours of every coarse vertex: one thread per table slot over
+// all tables (a hub's table is spread over the grid), lanes of a warp that
+// count for the same coarse vertex share one atomic.
 __global__ void k_lv_agg_count(const long long* __restrict__ toff, int32_t V2,
                                const int32_t* __restrict__ tkey, int32_t* __restrict__ deg2) {
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < V2; c += nw) {
-    int32_t d = 0;
-    for (long long s = toff[c] + lane_id(); s < toff[c + 1]; s += 32) d += tkey[s] != LV_EMPTY;
-    d = warp_sum(d);
-    if (lane_id() == 0) deg2[c] = d;
+  const long long total = toff[V2];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long b = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < total;
+       b += stride) {
+    const long long s = b + lane_id();
+    const bool used = s < total && tkey[s] != LV_EMPTY;
+    const int32_t c = used ? table_owner(toff, V2, s) : -1;
+    warp_claim_slot(deg2, c, __ballot_sync(FULL, used));
   }
 }
 
-// Writes the coarse edge lists (order inside a list unspecified) and the
-// coarse self-loop weights: own self loops plus half the internal weight
-// (every internal edge was seen from both of its ends).
+// Writes the coarse edge lists (order inside a list unspecified), again one
+// thread per table slot; positions come from a per-vertex cursor claimed
+// once per warp and coarse vertex.
 __global__ void k_lv_agg_write(const long long* __restrict__ toff, int32_t V2,
                                const int32_t* __restrict__ tkey, const long long* __restrict__ tval,
                                const long long* __restrict__ off2, int32_t* __restrict__ adj2,
-                               long long* __restrict__ aw2, const long long* __restrict__ internal,
-                               long long* __restrict__ self2, int32_t* __restrict__ fill) {
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < V2; c += nw) {
-    for (long long s = toff[c] + lane_id(); s < toff[c + 1]; s += 32) {
-      const int32_t key = tkey[s];
-      if (key == LV_EMPTY) continue;
-      const long long pos = off2[c] + atomicAdd(&fill[c], 1);
+                               long long* __restrict__ aw2, int32_t* __restrict__ fill) {
+  const long long total = toff[V2];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long b = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < total;
+       b += stride) {
+    const long long s = b + lane_id();
+    const int32_t key = s < total ? tkey[s] : LV_EMPTY;
+    const bool used = key != LV_EMPTY;
+    const int32_t c = used ? table_owner(toff, V2, s) : -1;
+    const int32_t slot = warp_claim_slot(fill, c, __ballot_sync(FULL, used));
+    if (used) {
+      const long long pos = off2[c] + slot;
       adj2[pos] = key;
       aw2[pos] = tval[s];
     }
-    if (lane_id() == 0) self2[c] += internal[c] / 2;
   }
+}
+
+// Coarse self-loop weights: own self loops plus half the internal weight
+// (every internal edge was seen from both of its ends).
+__global__ void k_lv_self2(int32_t V2, const long long* __restrict__ internal,
+                           long long* __restrict__ self2) {
+  for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < V2; c += gridDim.x * blockDim.x)
+    self2[c] += internal[c] / 2;
 }
 
 __global__ void k_lv_vmap(int32_t* __restrict__ vmap, int32_t n, const int32_t* __restrict__ cv) {
@@ -606,7 +632,9 @@ void lv_aggregate(const Ctx& cx, const LvGraph& g, const int32_t* cl, LvGraph& o
   deg2.alloc(&cx.alloc, (size_t)V2 + 1);
   fill2.alloc(&cx.alloc, (size_t)V2 + 1);
   HG_CUDA(cudaMemsetAsync(fill2.p, 0, fill2.bytes(), cx.stream));
-  k_lv_agg_count<<<gC, 256, 0, cx.stream>>>(toff.p, V2, tkey.p, deg2.p);
+  HG_CUDA(cudaMemsetAsync(deg2.p, 0, deg2.bytes(), cx.stream));
+  const int gT = grid_for(tslots, 256, cx.num_sms, 8);
+  k_lv_agg_count<<<gT, 256, 0, cx.stream>>>(toff.p, V2, tkey.p, deg2.p);
   check_launch("lv_agg_count");
   out.V = V2;
   out.off.alloc(&cx.alloc, (size_t)V2 + 1);
@@ -615,10 +643,12 @@ void lv_aggregate(const Ctx& cx, const LvGraph& g, const int32_t* cl, LvGraph& o
   out.E = read_i64(cx, reinterpret_cast<const int64_t*>(out.off.p) + V2);
   out.adj.alloc(&cx.alloc, (size_t)std::max<int64_t>(out.E, 1));
   out.aw.alloc(&cx.alloc, (size_t)std::max<int64_t>(out.E, 1));
-  k_lv_agg_write<<<gC, 256, 0, cx.stream>>>(toff.p, V2, tkey.p, tval.p, out.off.p, out.adj.p,
-                                          out.aw.p, internal.p, out.self.p, fill2.p);
+  k_lv_agg_write<<<gT, 256, 0, cx.stream>>>(toff.p, V2, tkey.p, tval.p, out.off.p, out.adj.p,
+                                          out.aw.p, fill2.p);
   check_launch("lv_agg_write");
-  if (cx.launches) *cx.launches += 13;
+  k_lv_self2<<<grid_for(V2, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(V2, internal.p, out.self.p);
+  check_launch("lv_self2");
+  if (cx.launches) *cx.launches += 14;
 }
 
 // One Louvain level on g (clusters start as singletons).  Returns the moves.

@@ -272,6 +272,62 @@ void build_incidence(const Ctx& cx, Level& L) {
   if (cx.launches) *cx.launches += 1;
 }
 
+namespace {
+
+// No node twice in a net (offsets and pin ranges already valid).
+bool distinct_pins(const Ctx& cx, const Level& L) {
+  if (L.m <= 0) return true;
+  DBuf<int32_t> mx;
+  mx.alloc(&cx.alloc, 1);
+  HG_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(int32_t), cx.stream));
+  k_max_net_size<<<grid_for(L.m, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(L.eoff.p, L.m, mx.p);
+  check_launch("max_net_size");
+  k_distinct_small<<<grid_for(L.m, DISTINCT_WARPS, cx.num_sms, 16), DISTINCT_WARPS * 32, 0,
+                     cx.stream>>>(L.eoff.p, L.pins.p, L.m, cx.d_status);
+  check_launch("distinct_small");
+  const int32_t biggest = read_i32(cx, mx.p);
+  if (biggest > DISTINCT_SMALL) {
+    uint32_t cap = 1;
+    while (cap < 2u * (uint32_t)biggest) cap <<= 1;
+    const int blocks = cx.num_sms;
+    DBuf<int32_t> scratch;
+    scratch.alloc(&cx.alloc, (size_t)blocks * cap);
+    HG_CUDA(cudaMemsetAsync(scratch.p, 0xff, scratch.bytes(), cx.stream));
+    k_distinct_big<<<blocks, 256, 0, cx.stream>>>(L.eoff.p, L.pins.p, L.m, scratch.p, cap,
+                                                  cx.d_status);
+    check_launch("distinct_big");
+  }
+  int32_t st = 0;
+  wait_stream(cx);
+  HG_CUDA(cudaMemcpyAsync(&st, cx.d_status, sizeof(st), cudaMemcpyDeviceToHost, cx.stream));
+  HG_CUDA(cudaStreamSynchronize(cx.stream));
+  if (st != DEV_OK) {
+    int32_t zero = 0;
+    HG_CUDA(cudaMemcpy(cx.d_status, &zero, sizeof(zero), cudaMemcpyHostToDevice));
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+bool validate_pins_device(const Ctx& cx, const Level& L) {
+  if (L.p > 0) {
+    k_validate_pins<<<grid_for(L.p, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(L.pins.p, L.p, L.n,
+                                                                             cx.d_status);
+    check_launch("validate_pins");
+    int32_t st = 0;
+    HG_CUDA(cudaMemcpyAsync(&st, cx.d_status, sizeof(st), cudaMemcpyDeviceToHost, cx.stream));
+    HG_CUDA(cudaStreamSynchronize(cx.stream));
+    if (st != DEV_OK) {
+      int32_t zero = 0;
+      HG_CUDA(cudaMemcpy(cx.d_status, &zero, sizeof(zero), cudaMemcpyHostToDevice));
+      return false;
+    }
+  }
+  return distinct_pins(cx, L);
+}
+
 bool validate_level_device(const Ctx& cx, const Level& L, int64_t* total_node_w,
                            int64_t* total_net_w) {
   DBuf<unsigned long long> sums;
@@ -301,36 +357,7 @@ bool validate_level_device(const Ctx& cx, const Level& L, int64_t* total_node_w,
     return false;
   }
   // offsets and pins are sound: no node twice in a net
-  if (L.m > 0) {
-    DBuf<int32_t> mx;
-    mx.alloc(&cx.alloc, 1);
-    HG_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(int32_t), cx.stream));
-    k_max_net_size<<<grid_for(L.m, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(L.eoff.p, L.m, mx.p);
-    check_launch("max_net_size");
-    k_distinct_small<<<grid_for(L.m, DISTINCT_WARPS, cx.num_sms, 16), DISTINCT_WARPS * 32, 0,
-                       cx.stream>>>(L.eoff.p, L.pins.p, L.m, cx.d_status);
-    check_launch("distinct_small");
-    const int32_t biggest = read_i32(cx, mx.p);
-    if (biggest > DISTINCT_SMALL) {
-      uint32_t cap = 1;
-      while (cap < 2u * (uint32_t)biggest) cap <<= 1;
-      const int blocks = cx.num_sms;
-      DBuf<int32_t> scratch;
-      scratch.alloc(&cx.alloc, (size_t)blocks * cap);
-      HG_CUDA(cudaMemsetAsync(scratch.p, 0xff, scratch.bytes(), cx.stream));
-      k_distinct_big<<<blocks, 256, 0, cx.stream>>>(L.eoff.p, L.pins.p, L.m, scratch.p, cap,
-                                                    cx.d_status);
-      check_launch("distinct_big");
-    }
-    wait_stream(cx);
-    HG_CUDA(cudaMemcpyAsync(&st, cx.d_status, sizeof(st), cudaMemcpyDeviceToHost, cx.stream));
-    HG_CUDA(cudaStreamSynchronize(cx.stream));
-    if (st != DEV_OK) {
-      int32_t zero = 0;
-      HG_CUDA(cudaMemcpy(cx.d_status, &zero, sizeof(zero), cudaMemcpyHostToDevice));
-      return false;
-    }
-  }
+  if (!distinct_pins(cx, L)) return false;
   *total_node_w = (int64_t)h[0];
   *total_net_w = (int64_t)h[1];
   return true;

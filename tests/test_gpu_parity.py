@@ -458,3 +458,36 @@ def test_device_input_with_repeated_pins_rejected():
                 with pytest.raises(hg.HgError) as ei:
                     hg.hg_create(n, 2, *args, hg.HG_MEM_DEVICE, make_opt(), stream)
                 assert ei.value.status == hg.HG_ERR_INVALID
+
+
+@pytest.mark.parametrize("fault", ["out_of_range", "repeat_small", "repeat_big", "none"])
+def test_large_host_input_pins_checked_on_the_device(fault):
+    """Host inputs above 65,536 pins have their pins checked on the device:
+    a pin out of range or a node repeated inside a net (small or large net)
+    is rejected with HG_ERR_INVALID and the next create succeeds."""
+    hgr = synth.random_uniform(61, 30_000, 40_000)
+    assert hgr.p > 1 << 16
+    off = np.concatenate([hgr.offsets, [hgr.p + 2000]]).astype(np.int32)
+    big = np.arange(0, 4000, 2, dtype=np.int32)  # a 2000-pin net
+    pins = np.concatenate([hgr.pins, big]).astype(np.int32)
+    if fault == "out_of_range":
+        pins[hgr.p // 2] = hgr.n
+    elif fault == "repeat_small":
+        e = 7
+        b = hgr.offsets[e]
+        pins[b + 1] = pins[b]
+    elif fault == "repeat_big":
+        pins[-1] = pins[-1000]
+    w = np.concatenate([hgr.net_w, [1]]).astype(np.int32)
+    stream = torch.cuda.current_stream()
+    if fault == "none":
+        h = hg.hg_create(hgr.n, hgr.m + 1, off, pins, w, hgr.node_w, hg.HG_MEM_HOST, make_opt(),
+                         stream)
+        hg.hg_destroy(h)
+        return
+    with pytest.raises(hg.HgError) as ei:
+        hg.hg_create(hgr.n, hgr.m + 1, off, pins, w, hgr.node_w, hg.HG_MEM_HOST, make_opt(), stream)
+    assert ei.value.status == hg.HG_ERR_INVALID
+    h = hg.hg_create(hgr.n, hgr.m, hgr.offsets, hgr.pins, hgr.net_w, hgr.node_w, hg.HG_MEM_HOST,
+                     make_opt(), stream)
+    hg.hg_destroy(h)
