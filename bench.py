@@ -833,6 +833,40 @@ def run_ours(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_profile(args):
+    """For profilers: `warmup` untimed V-cycle steps then one more step of the
+    named workload (the same calls as a timed step), no output."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2303_17679_gb300 import build as libbuild
+    from paper_2303_17679_gb300 import hg
+
+    libbuild.build()
+    hg.load()
+    stream = torch.cuda.current_stream()
+    opt = hg.hg_default_options()
+    opt.seed = SEED
+    if args.profile == "zipf1m":
+        hgr, k = synth.zipf_1m(SEED), K_BLOCKS
+        load_mapping(hg, opt)
+    elif args.profile == "largenet4m":
+        hgr, k = synth.large_net_4m(SEED), 64
+    else:
+        hgr, k = synth.graph_preferential(SEED, 1_000_000, 4_000_000), K_BLOCKS
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).cuda()
+    d = (t(hgr.offsets), t(hgr.pins), t(hgr.net_w), t(hgr.node_w))
+    part = torch.empty(hgr.n, dtype=torch.int32, device="cuda")
+    for _ in range(args.warmup + 1):
+        h = hg.hg_create(hgr.n, hgr.m, *d, hg.HG_MEM_DEVICE, opt, stream)
+        try:
+            hg.hg_partition(h, k, EPS_PPM, PASSES, part)
+        finally:
+            hg.hg_destroy(h)
+    torch.cuda.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -847,7 +881,12 @@ def main():
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the n=m=1e4 and 4e6-node large-net sub-objects")
     ap.add_argument("--slots", type=int, default=16, help="executor slots for batch and serve")
+    ap.add_argument("--profile", choices=["zipf1m", "largenet4m", "graph1m"], default=None,
+                    help="run warm-up steps and one step of a workload for a profiler, no output")
     args = ap.parse_args()
+    if args.profile:
+        run_profile(args)
+        return
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)

@@ -114,6 +114,79 @@ __global__ void k_objective_graph(const int32_t* __restrict__ eoff,
   if (threadIdx.x == 0 && f) atomicAdd(out, (unsigned long long)f);
 }
 
+// ------------------------------------------------ packed net records (a11)
+
+// Label propagation reads, for every incidence (u, e), w(e), Lambda(e) and
+// whether Phi(e, Pi[u]) = 1.  They live in one record per net, so the gain
+// gathers one 32-byte sector per incidence instead of three:
+//   k <= 32: 16 bytes {w(e), ones(e), Lambda(e), 0} (one int4);
+//   k >  32: 32 bytes {w(e), 0, ones(e) as 64 bits}, {Lambda(e) as 64 bits, 0, 0},
+// with ones(e) = {i : Phi(e, i) = 1}.  Phi stays the authority: the
+// application changes a pin count with an atomic that returns the old
+// count, and flips the record's bits for the transitions it caused
+// (0 <-> 1 toggles Lambda and ones, 1 <-> 2 toggles ones); the flips commute,
+// so the records equal their definition whatever the order of the moves.
+struct NetRec {
+  int32_t w;
+  unsigned long long ones, lam;
+};
+
+__device__ __forceinline__ NetRec load_rec(const int4* __restrict__ rec, int64_t e, bool wide) {
+  if (!wide) {
+    const int4 r = rec[e];
+    return NetRec{r.x, (unsigned long long)(uint32_t)r.y, (unsigned long long)(uint32_t)r.z};
+  }
+  const int4 a = rec[2 * e], b = rec[2 * e + 1];
+  return NetRec{a.x, (unsigned long long)(uint32_t)a.z | ((unsigned long long)(uint32_t)a.w << 32),
+                (unsigned long long)(uint32_t)b.x | ((unsigned long long)(uint32_t)b.y << 32)};
+}
+
+// Applies the bit flips of one pin-count change to net e's record.
+__device__ __forceinline__ void flip_rec(int4* rec, int64_t e, bool wide, unsigned long long ones_x,
+                                         unsigned long long lam_x) {
+  if (!wide) {
+    if (ones_x) atomicXor(reinterpret_cast<unsigned*>(&rec[e].y), (unsigned)ones_x);
+    if (lam_x) atomicXor(reinterpret_cast<unsigned*>(&rec[e].z), (unsigned)lam_x);
+  } else {
+    if (ones_x) atomicXor(reinterpret_cast<unsigned long long*>(&rec[2 * e].z), ones_x);
+    if (lam_x) atomicXor(reinterpret_cast<unsigned long long*>(&rec[2 * e + 1].x), lam_x);
+  }
+}
+
+// Records from Phi, Lambda and w (one thread per net).
+__global__ void k_net_records(const int32_t* __restrict__ phi, const unsigned long long* __restrict__ lam,
+                              const int32_t* __restrict__ w, int32_t m, int k, bool wide,
+                              int4* __restrict__ rec) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long ones = 0;
+    for (int i = 0; i < k; ++i)
+      if (phi[e * k + i] == 1) ones |= 1ull << i;
+    const unsigned long long l = lam[e];
+    if (!wide) {
+      rec[e] = make_int4(w[e], (int32_t)(uint32_t)ones, (int32_t)(uint32_t)l, 0);
+    } else {
+      rec[2 * e] = make_int4(w[e], 0, (int32_t)(uint32_t)ones, (int32_t)(uint32_t)(ones >> 32));
+      rec[2 * e + 1] = make_int4((int32_t)(uint32_t)l, (int32_t)(uint32_t)(l >> 32), 0, 0);
+    }
+  }
+}
+
+// Objective from the records' Lambda.
+__global__ void k_objective_rec(const int4* __restrict__ rec, int32_t m, bool wide,
+                                unsigned long long* __restrict__ out) {
+  __shared__ int64_t red[32];
+  int64_t f = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const NetRec r = load_rec(rec, e, wide);
+    const int l = __popcll(r.lam);
+    if (l > 1) f += (int64_t)(l - 1) * r.w;
+  }
+  f = block_sum(f, red);
+  if (threadIdx.x == 0 && f) atomicAdd(out, (unsigned long long)f);
+}
+
 // -------------------------------------------- sub-round node lists (a11)
 
 // Nodes of a pass are listed by key = sub-round * 2 + class, class 1 for
@@ -196,9 +269,7 @@ struct GainPart {
 constexpr int GAIN_REDUCE_K = 16;
 
 __device__ __forceinline__ GainPart gain_partial(const int32_t* __restrict__ inets,
-                                                 const int32_t* __restrict__ w,
-                                                 const int32_t* __restrict__ phi,
-                                                 const unsigned long long* __restrict__ lam, int k,
+                                                 const int4* __restrict__ rec, bool wide, int k,
                                                  int from, int32_t beg, int32_t end, int first,
                                                  int stride, int32_t* s_cnt) {
   const int lane = lane_id();
@@ -209,10 +280,10 @@ __device__ __forceinline__ GainPart gain_partial(const int32_t* __restrict__ ine
     int32_t we = 0;
     unsigned long long le = 0;
     if (j < end) {
-      const int32_t e = inets[j];
-      we = w[e];
-      le = lam[e];
-      if (phi[(int64_t)e * k + from] == 1) g.ben += we;
+      const NetRec r = load_rec(rec, inets[j], wide);
+      we = r.w;
+      le = r.lam;
+      if ((r.ones >> from) & 1ull) g.ben += we;  // u is the only pin of its block in e
       g.wsum += we;
     }
     if (k <= GAIN_REDUCE_K) {
@@ -325,9 +396,8 @@ __device__ __forceinline__ void gain_best(const GainPart& g, int k, int from, lo
 struct GainArgs {
   const int32_t* ioff;
   const int32_t* inets;
-  const int32_t* w;
-  const int32_t* phi;
-  const unsigned long long* lam;
+  const int4* rec;  // packed net records (hypergraph levels)
+  bool wide;        // k > 32: 32-byte records
   const int32_t* part;
   int k;
   const int32_t* list;
@@ -369,7 +439,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_lp_gain_warp(GainArgs A) {
     const int from = A.part[u];
     const int32_t beg = A.ioff[u], end = A.ioff[u + 1];
     GainPart g = A.graph ? gain_partial_graph(A.adj, A.part, A.k, beg, end, 0, 1, cnt)
-                         : gain_partial(A.inets, A.w, A.phi, A.lam, A.k, from, beg, end, 0, 1, cnt);
+                         : gain_partial(A.inets, A.rec, A.wide, A.k, from, beg, end, 0, 1, cnt);
     gain_collect(g, cnt, A.k);
     if (A.graph) graph_gain_terms(g, from);
     long long bg;
@@ -403,7 +473,7 @@ __global__ void __launch_bounds__(GAIN_BLOCK_WARPS * 32) k_lp_gain_block(GainArg
     const int32_t beg = A.ioff[u], end = A.ioff[u + 1];
     GainPart g =
         A.graph ? gain_partial_graph(A.adj, A.part, A.k, beg, end, wv, WARPS, cnt)
-                : gain_partial(A.inets, A.w, A.phi, A.lam, A.k, from, beg, end, wv, WARPS, cnt);
+                : gain_partial(A.inets, A.rec, A.wide, A.k, from, beg, end, wv, WARPS, cnt);
     gain_collect(g, cnt, A.k);
     if (A.graph) graph_gain_terms(g, from);
     s_acc[wv][lane] = g.acc0;
@@ -570,7 +640,6 @@ k_lp_select(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
             long long* __restrict__ dbw, int s, long long lmax, int k,
             unsigned long long* __restrict__ gkeys, long long* __restrict__ gpre,
             const int32_t* __restrict__ words, int32_t* __restrict__ part,
-            int32_t* __restrict__ phi, unsigned long long* __restrict__ lam,
             unsigned long long* __restrict__ moved, int32_t* __restrict__ ap_u,
             int32_t* __restrict__ ap_from, int32_t* __restrict__ ap_to,
             int32_t* __restrict__ ap_count, bool graph) {
@@ -775,15 +844,17 @@ k_lp_select(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
 // One warp per work item (u, s, t, chunk): for the <= 32 nets e of the
 // chunk: Phi(e, s) -= 1, Phi(e, t) += 1, clearing bit s of Lambda(e) when
 // Phi(e, s) reaches 0 and setting bit t when Phi(e, t) leaves 0 (Algorithm
-// 3's updates; the atomic xor flips commute, so the final masks equal
-// {i : Phi(e, i) > 0} whatever the order of the moves).  The chunk-0 item
-// also sets Pi[u] = t.  The block weights were moved by the selection.
+// 3's updates), and toggling the ones(e) bits of counts that reach or leave
+// 1, all in net e's record; the atomic xor flips commute, so the final masks
+// equal {i : Phi(e, i) > 0} and {i : Phi(e, i) = 1} whatever the order of the
+// moves.  The chunk-0 item also sets Pi[u] = t.  The block weights were
+// moved by the selection.
 __global__ void __launch_bounds__(WARPS * 32)
 k_lp_apply(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets, int k,
            const int32_t* __restrict__ ap_u, const int32_t* __restrict__ ap_from,
            const int32_t* __restrict__ ap_to, const int32_t* __restrict__ ap_count,
-           int32_t* __restrict__ part, int32_t* __restrict__ phi,
-           unsigned long long* __restrict__ lam, unsigned long long* __restrict__ moved) {
+           int32_t* __restrict__ part, int32_t* __restrict__ phi, int4* __restrict__ rec,
+           bool wide, unsigned long long* __restrict__ moved) {
   const int32_t na = *ap_count;
   const int lane = lane_id();
   unsigned long long incid = 0;
@@ -796,8 +867,23 @@ k_lp_apply(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets, 
     if (lane == 0 && j1 > j0) incid += (unsigned long long)(j1 - j0);
     if (j < j1) {
       const int32_t e = inets[j];
-      if (atomicSub(&phi[(int64_t)e * k + s], 1) == 1) atomicXor(&lam[e], 1ull << s);
-      if (atomicAdd(&phi[(int64_t)e * k + t], 1) == 0) atomicXor(&lam[e], 1ull << t);
+      const int32_t os = atomicSub(&phi[(int64_t)e * k + s], 1);  // s: os -> os - 1
+      const int32_t ot = atomicAdd(&phi[(int64_t)e * k + t], 1);  // t: ot -> ot + 1
+      const unsigned long long bs = 1ull << s, bt = 1ull << t;
+      unsigned long long ones_x = 0, lam_x = 0;
+      if (os == 1) {
+        ones_x ^= bs;
+        lam_x ^= bs;
+      } else if (os == 2) {
+        ones_x ^= bs;
+      }
+      if (ot == 0) {
+        ones_x ^= bt;
+        lam_x ^= bt;
+      } else if (ot == 1) {
+        ones_x ^= bt;
+      }
+      flip_rec(rec, e, wide, ones_x, lam_x);
     }
     if (ch == 0 && lane == 0) part[u] = t;
   }
@@ -874,6 +960,19 @@ int64_t objective_of_graph(const Ctx& cx, const Level& L, const int32_t* part) {
     k_objective_graph<<<grid_for(L.m, 256, cx.num_sms, 4), 256, 0, cx.stream>>>(
         L.eoff.p, L.pins.p, L.w.p, part, L.m, acc.p);
     check_launch("objective_graph");
+    if (cx.launches) *cx.launches += 1;
+  }
+  return read_i64(cx, reinterpret_cast<const int64_t*>(acc.p));
+}
+
+int64_t objective_from_records(const Ctx& cx, const Level& L, const int4* rec, bool wide) {
+  DBuf<unsigned long long> acc;
+  acc.alloc(&cx.alloc, 1);
+  HG_CUDA(cudaMemsetAsync(acc.p, 0, sizeof(unsigned long long), cx.stream));
+  if (L.m > 0) {
+    k_objective_rec<<<grid_for(L.m, 256, cx.num_sms, 4), 256, 0, cx.stream>>>(rec, L.m, wide,
+                                                                              acc.p);
+    check_launch("objective_rec");
     if (cx.launches) *cx.launches += 1;
   }
   return read_i64(cx, reinterpret_cast<const int64_t*>(acc.p));
@@ -1033,6 +1132,20 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
     EventTimer tm(cx, &rc.ms_phi);
     build_pin_state(cx, L, k, part, st, !L.graph);
   }
+  // packed net records (hypergraph levels); Lambda is then kept in them only
+  const bool wide = k > 32;
+  DBuf<int4> rec;
+  if (!L.graph) {
+    EventTimer tm(cx, &rc.ms_phi);
+    rec.alloc(&cx.alloc, (size_t)std::max<int32_t>(L.m, 1) * (wide ? 2 : 1));
+    if (L.m > 0) {
+      k_net_records<<<grid_for(L.m, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(
+          st.phi.p, st.lam.p, L.w.p, L.m, k, wide, rec.p);
+      check_launch("net_records");
+      if (cx.launches) *cx.launches += 1;
+    }
+    st.lam.release();
+  }
   const int64_t per_block = (total_node_weight + k - 1) / k;
   const long long lmax = (long long)(per_block * (1000000 + (int64_t)eps_ppm) / 1000000);
   const int kk = k * k;
@@ -1082,9 +1195,8 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   GainArgs G;
   G.ioff = L.ioff.p;
   G.inets = L.inets.p;
-  G.w = L.w.p;
-  G.phi = st.phi.p;
-  G.lam = st.lam.p;
+  G.rec = rec.p;
+  G.wide = wide;
   G.part = part;
   G.k = k;
   G.list = list.p;
@@ -1192,7 +1304,7 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
         auto sel = gather ? k_lp_select<true> : k_lp_select<false>;
         sel<<<g_sel, SEL_THREADS, sel_bytes, sm>>>(
             L.ioff.p, L.inets.p, bucket.p, doff.p, dc_s, mv_u.p, mv_to.p, mv_g.p, L.c.p, st.bw.p,
-            dbw.p, s, lmax, k, gkeys.p, gpre.p, w_s, part, st.phi.p, st.lam.p, counters.p, ap_u.p,
+            dbw.p, s, lmax, k, gkeys.p, gpre.p, w_s, part, counters.p, ap_u.p,
             ap_from.p, ap_to.p, w_s + SW_APPROVED, L.graph);
         check_launch("lp_select");
         mark(fj, sm, s, 2);
@@ -1202,7 +1314,7 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
         if (!L.graph) {
           k_lp_apply<<<g_apply, WARPS * 32, 0, sm>>>(L.ioff.p, L.inets.p, k, ap_u.p, ap_from.p,
                                                       ap_to.p, w_s + SW_APPROVED, part, st.phi.p,
-                                                      st.lam.p, counters.p);
+                                                      rec.p, wide, counters.p);
           check_launch("lp_apply");
         }
         mark(fj, sm, s, 3);
@@ -1266,7 +1378,7 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   rc.lp_passes += res.passes;
   {
     EventTimer tm(cx, &rc.ms_objective);
-    res.objective = L.graph ? objective_of_graph(cx, L, part) : objective_from_lambda(cx, L, st.lam.p);
+    res.objective = L.graph ? objective_of_graph(cx, L, part) : objective_from_records(cx, L, rec.p, wide);
   }
   return res;
 }

@@ -7,6 +7,7 @@ nothing here touches the CUDA library.  Run once on a CPU host:
     python tests/golden/make_fullsize.py zipf1m      # n = m = 1e6 Zipf(2.2), k = 8
     python tests/golden/make_fullsize.py largenet4m  # n = 4e6, m = 2e6 large nets, k = 64
     python tests/golden/make_fullsize.py batch       # a subset of the 512-instance batch
+    python tests/golden/make_fullsize.py serve       # a sample of the Poisson serving stream
 
 Each run writes one JSON file next to this script.  For a V-cycle it holds,
 per level, the sizes and SHA-256 digests of the level's canonical CSR
@@ -106,9 +107,40 @@ def run_batch():
             "instances": recs}
 
 
+# serve: the first 48 requests of the 200 req/s stream with at most 400,000
+# pins (the oracle then needs seconds, not minutes, per request)
+def serve_sample():
+    import synth
+    arr = synth.poisson_arrivals(SEED, rate=200.0, duration=60.0)
+    return [i for i, a in enumerate(arr) if a[2] <= 400_000][:48]
+
+
+def _serve_one(i):
+    import oracle
+    import synth
+    t_arr, req_seed, pins, k = synth.poisson_arrivals(SEED, rate=200.0, duration=60.0)[i]
+    hgr = synth.poisson_request(req_seed, pins)
+    vc = oracle.multilevel(hgr, k, EPS, max_passes=PASSES)
+    return {"index": i, "arrival_s": t_arr, "n": int(hgr.n), "p": int(hgr.p), "k": k,
+            "levels": len(vc.levels), "objective": int(vc.objectives[0]),
+            "part": digest(vc.parts[0])}
+
+
+def run_serve():
+    pick = serve_sample()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(max(1, min(len(pick), os.cpu_count() or 1))) as pool:
+        recs = pool.map(_serve_one, pick)
+    return {"workload": "synth.poisson_arrivals(1, 200/s, 60 s): requests of 1e4..2e6 pins "
+                        "(log-uniform), Zipf(2.2) sizes, k in {2, 8, 32}; the first 48 with at "
+                        "most 400,000 pins", "eps_ppm": EPS, "max_passes": PASSES, "seed": SEED,
+            "requests": recs}
+
+
 TARGETS = {"zipf1m": ("fullsize_zipf1m_k8.json", run_zipf1m),
            "largenet4m": ("fullsize_largenet4m_k64.json", run_largenet4m),
-           "batch": ("batch_subset.json", run_batch)}
+           "batch": ("batch_subset.json", run_batch),
+           "serve": ("serve_sample.json", run_serve)}
 
 
 def main():

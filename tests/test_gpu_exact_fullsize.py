@@ -222,3 +222,45 @@ def test_duplicated_big_nets_merge_exactly(oracle_mod, fp_bits):
             assert np.array_equal(got[key], getattr(ref["level"], key)), key
     finally:
         hg.hg_destroy(h)
+
+
+def test_served_stream_matches_oracle_digests():
+    """48 requests of the 200 req/s serving stream (those of at most 400,000
+    pins among its first ones), submitted at their Poisson arrival gaps to
+    an executor of 16 slots so that they overlap on the device: every served
+    partition and objective equals the oracle's."""
+    import time
+    want = load_golden("serve_sample.json")
+    arrivals = synth.poisson_arrivals(want["seed"], rate=200.0, duration=60.0)
+    reqs = [(r, synth.poisson_request(arrivals[r["index"]][1], arrivals[r["index"]][2]))
+            for r in want["requests"]]
+    ex = hg.Executor(slots=16)
+    got = {}
+    try:
+        t0 = time.perf_counter()
+        base = reqs[0][0]["arrival_s"]
+        for rec, hgr in reqs:
+            assert (hgr.n, hgr.p, arrivals[rec["index"]][3]) == (rec["n"], rec["p"], rec["k"])
+            delay = rec["arrival_s"] - base - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            ex.submit(hgr, rec["k"], want["eps_ppm"], want["max_passes"], tag=rec["index"])
+            for r in ex.wait(timeout_ms=0):
+                got[r["tag"]] = r
+        while len(got) < len(reqs):
+            for r in ex.wait():
+                got[r["tag"]] = r
+    finally:
+        ex.close()
+    overlapped = 0
+    res = list(got.values())
+    for r in res:
+        overlapped += sum(1 for x in res if x is not r and x["t_start_ns"] < r["t_end_ns"]
+                          and r["t_start_ns"] < x["t_end_ns"])
+    assert overlapped > 0
+    for rec, _ in reqs:
+        r = got[rec["index"]]
+        assert r["status"] == hg.HG_OK
+        assert r["levels"] == rec["levels"], rec["index"]
+        assert r["objective"] == rec["objective"], rec["index"]
+        assert digest(r["part"]) == rec["part"], rec["index"]
