@@ -80,8 +80,7 @@ constexpr int32_t SPLIT_DENSE_MAX = 65536;
 constexpr int SPLIT_WARPS = 8;
 constexpr int PART_THREADS = 1024;
 constexpr int PART_TEAMS = 1;
-constexpr uint32_t PART_SLOTS = 16384;   // shared hash slots of a part block
-constexpr int32_t PART_D = 9830;         // distinct candidates per part (60 % of the slots)
+// part blocks: see PartCfg (table slots and distinct candidates per part)
 constexpr int32_t PART_MAX = 8;          // more parts: the node uses a global hash table
 constexpr int ARGMAX_THREADS = 256;
 constexpr int32_t EMPTY_KEY = -1;
@@ -211,6 +210,44 @@ struct WideHash {
   }
 };
 
+// 32-bit ratings in a table of any size (not a power of two): the first slot
+// is the high half of hash * slots, probing wraps at the end.  Used by the
+// part blocks, whose table takes the whole shared-memory budget.
+struct ModHash {
+  uint32_t* val;
+  int32_t* key;
+  uint32_t slots;
+  static constexpr size_t BYTES_PER_SLOT = 8;
+  __device__ __forceinline__ void init(uint32_t i) {
+    key[i] = EMPTY_KEY;
+    val[i] = 0;
+  }
+  __device__ __forceinline__ int32_t add(int32_t C, uint32_t r) {
+    uint32_t h = (uint32_t)(((uint64_t)slot_hash(C) * slots) >> 32);
+    for (uint32_t probe = 0; probe < slots; ++probe) {
+      int32_t k = key[h];
+      bool fresh = false;
+      if (k == EMPTY_KEY) {
+        const int32_t old = atomicCAS(&key[h], EMPTY_KEY, C);
+        fresh = old == EMPTY_KEY;
+        k = fresh ? C : old;
+      }
+      if (k == C) {
+        atomicAdd(&val[h], r);
+        return fresh ? (int32_t)h : ADD_EXISTING;
+      }
+      h = h + 1 == slots ? 0 : h + 1;
+    }
+    return ADD_FULL;
+  }
+  __device__ __forceinline__ void take(uint32_t i, int32_t& C, uint32_t& v) {
+    C = key[i];
+    v = val[i];
+    key[i] = EMPTY_KEY;
+    val[i] = 0;
+  }
+};
+
 template <typename VT> struct HashOf;
 template <> struct HashOf<uint32_t> { using type = PackedHash; };
 template <> struct HashOf<unsigned long long> { using type = WideHash; };
@@ -221,6 +258,11 @@ template <>
 __device__ __forceinline__ PackedHash make_hash<PackedHash>(unsigned char* base, uint32_t slots) {
   uint32_t* val = reinterpret_cast<uint32_t*>(base);
   return PackedHash{val, reinterpret_cast<int32_t*>(val + slots), slots - 1};
+}
+template <>
+__device__ __forceinline__ ModHash make_hash<ModHash>(unsigned char* base, uint32_t slots) {
+  uint32_t* val = reinterpret_cast<uint32_t*>(base);
+  return ModHash{val, reinterpret_cast<int32_t*>(val + slots), slots};
 }
 template <>
 __device__ __forceinline__ WideHash make_hash<WideHash>(unsigned char* base, uint32_t slots) {
@@ -759,19 +801,32 @@ k_rate_split_acc(RateArgs A, const int32_t* __restrict__ split, const int32_t* _
 // table: the candidates are partitioned over P blocks by a hash of the
 // cluster id (part_of).  Every block walks all of the node's visits (the pin
 // clusters are read P times, from L2 at the levels where this happens) and
-// accumulates the candidates of its part in a PART_SLOTS-slot shared table;
-// P = ceil(min(W, n) / PART_D) keeps every table at most 60 % full, so no
+// accumulates the candidates of its part in a shared table (PartCfg);
+// P = ceil(min(W, n) / PartCfg::D) keeps every table at most 60 % full, so no
 // insertion can fail.  A node of one part publishes its argmax directly;
 // otherwise each part leaves its best (rating, cluster) for the per-node
 // combine in k_rate_split_argmax.  All warps of the block walk the node's
 // groups of 32 nets, sharing the chunks in turn.
-// Capacity of a part block's list of inserted slots (32-bit ratings: every
-// slot; 64-bit: what fits beside the table, else the whole table is scanned).
-template <typename VT> struct PartUsed { static constexpr uint32_t CAP = 2048; };
-template <> struct PartUsed<uint32_t> { static constexpr uint32_t CAP = PART_SLOTS; };
+// Table of a part block: SLOTS shared slots holding at most D distinct
+// candidates per part (60 % load), and a list of the inserted slots of
+// capacity CAP (more insertions: the whole table is scanned).  32-bit
+// ratings take the whole shared-memory budget (22,528 slots, so fewer nodes
+// need more than one part and every part re-reads the node's visits);
+// 64-bit ratings 16,384 slots.
+template <typename VT> struct PartCfg {
+  using Hash = WideHash;
+  static constexpr uint32_t SLOTS = 16384, CAP = 2048;
+  static constexpr int32_t D = 9830;
+};
+template <> struct PartCfg<uint32_t> {
+  using Hash = ModHash;
+  static constexpr uint32_t SLOTS = 22528, CAP = 10240;
+  static constexpr int32_t D = 13516;
+};
 template <typename VT>
 constexpr size_t part_bytes() {
-  return (size_t)PART_SLOTS * HashOf<VT>::type::BYTES_PER_SLOT + (size_t)PartUsed<VT>::CAP * 4;
+  return (size_t)PartCfg<VT>::SLOTS * PartCfg<VT>::Hash::BYTES_PER_SLOT +
+         (size_t)PartCfg<VT>::CAP * 4;
 }
 
 __device__ __forceinline__ int32_t part_of(int32_t C, int32_t P) {
@@ -783,9 +838,10 @@ __global__ void __launch_bounds__(PART_THREADS)
 k_rate_part(RateArgs A, const int32_t* __restrict__ split, const int32_t* __restrict__ part_node,
             const int32_t* __restrict__ part_off, int32_t part_lo, int32_t part_hi,
             VT* __restrict__ res_v, int32_t* __restrict__ res_c) {
-  using H = typename HashOf<VT>::type;
+  using H = typename PartCfg<VT>::Hash;
+  constexpr uint32_t PART_SLOTS = PartCfg<VT>::SLOTS;
   constexpr int NW = PART_THREADS / 32, TW = NW / PART_TEAMS;
-  constexpr uint32_t CAP = PartUsed<VT>::CAP;
+  constexpr uint32_t CAP = PartCfg<VT>::CAP;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ VT s_rv[NW];
   __shared__ int32_t s_rc[NW];
@@ -1053,19 +1109,20 @@ __global__ void k_node_scatter(const int32_t* __restrict__ key_of, int32_t n, in
 //   direct-indexed global table (n entries) when n <= min(2 W(u), 65536), so
 //   the table costs no more than the accumulation: groups of 32 nets over
 //   the grid (items);
-//   else P = ceil(D / PART_D) shared-memory parts when P <= PART_MAX (no
+//   else P = ceil(D / part_d) shared-memory parts when P <= PART_MAX (no
 //   global table);
 //   else a global hash table of a power of two >= 2 D + 2 slots, with items.
 __global__ void k_split_sizes(const int32_t* __restrict__ split, int32_t nsplit,
                               const int32_t* __restrict__ ioff, const int32_t* __restrict__ wof,
-                              int32_t n, int32_t* __restrict__ items, int32_t* __restrict__ parts,
-                              int32_t* __restrict__ cap, int8_t* __restrict__ dense) {
+                              int32_t n, int32_t part_d, int32_t* __restrict__ items,
+                              int32_t* __restrict__ parts, int32_t* __restrict__ cap,
+                              int8_t* __restrict__ dense) {
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nsplit; i += gridDim.x * blockDim.x) {
     const int32_t u = split[i];
     const int32_t deg = ioff[u + 1] - ioff[u];
     const bool d = n <= SPLIT_DENSE_MAX && (int64_t)n <= 2 * (int64_t)wof[u];
     const int32_t D = min(wof[u], n);
-    const int32_t P = d ? 0 : (D + PART_D - 1) / PART_D;
+    const int32_t P = d ? 0 : (D + part_d - 1) / part_d;
     const bool part = !d && P <= PART_MAX;
     items[i] = part ? 0 : (deg + 31) / 32;
     parts[i] = part ? P : 0;
@@ -1748,8 +1805,9 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
     sp.tnused.alloc(&cx.alloc, (size_t)nsplit + 1);
     HG_CUDA(cudaMemsetAsync(sp.tnused.p, 0, sp.tnused.bytes(), cx.stream));
     const int gs = grid_for(nsplit, 256, cx.num_sms, 4);
-    k_split_sizes<<<gs, 256, 0, cx.stream>>>(sp.split, nsplit, L.ioff.p, wof.p, n, items.p,
-                                             parts.p, cap32.p, sp.tab_dense.p);
+    k_split_sizes<<<gs, 256, 0, cx.stream>>>(
+        sp.split, nsplit, L.ioff.p, wof.p, n, narrow ? PartCfg<uint32_t>::D : PartCfg<unsigned long long>::D,
+        items.p, parts.p, cap32.p, sp.tab_dense.p);
     check_launch("split_sizes");
     scan_exclusive_i32(cx, items.p, sp.item_off.p, nsplit, sp.item_off.p + nsplit);
     scan_exclusive_i32(cx, parts.p, sp.part_off.p, nsplit, sp.part_off.p + nsplit);
