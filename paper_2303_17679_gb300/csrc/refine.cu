@@ -309,6 +309,83 @@ __device__ __forceinline__ GainPart gain_partial(const int32_t* __restrict__ ine
   return g;
 }
 
+// gain_partial for nodes of many incident nets (the block class) and k <= 16:
+// every lane takes four consecutive incidences of a 128-incidence chunk with
+// one 16-byte load of their net ids, so four record gathers are in flight per
+// lane, and the warp reduces each block's sum once per 128 incidences.  (For
+// k > 16 the per-lane shared-counter loops of four nets serialise; there the
+// one-incidence form is faster.)
+// Chunks start at beg rounded down to a multiple of 4 (the 16-byte loads stay
+// aligned); positions outside [beg, end) count nothing.
+constexpr int GAIN_VEC = 4;
+
+__device__ __forceinline__ GainPart gain_partial_vec(const int32_t* __restrict__ inets,
+                                                     const int4* __restrict__ rec, bool wide,
+                                                     int k, int from, int32_t beg, int32_t end,
+                                                     int first, int stride, int32_t* s_cnt) {
+  const int lane = lane_id();
+  const unsigned long long kmask = k == 64 ? ~0ull : ((1ull << k) - 1ull);
+  GainPart g{0, 0, 0, 0, 0};
+  constexpr int32_t CH = 32 * GAIN_VEC;
+  const int32_t a0 = beg & ~(GAIN_VEC - 1);
+  for (int32_t c0 = a0 + CH * first; c0 < end; c0 += CH * stride) {
+    const int32_t j0 = c0 + GAIN_VEC * lane;
+    int32_t e[GAIN_VEC];
+    if (j0 >= beg && j0 + GAIN_VEC <= end) {
+      const int4 v = *reinterpret_cast<const int4*>(inets + j0);
+      e[0] = v.x;
+      e[1] = v.y;
+      e[2] = v.z;
+      e[3] = v.w;
+    } else {
+#pragma unroll
+      for (int x = 0; x < GAIN_VEC; ++x) {
+        const int32_t j = j0 + x;
+        e[x] = j >= beg && j < end ? inets[j] : -1;
+      }
+    }
+    int32_t we[GAIN_VEC];
+    unsigned long long le[GAIN_VEC];
+#pragma unroll
+    for (int x = 0; x < GAIN_VEC; ++x) {
+      we[x] = 0;
+      le[x] = 0;
+      if (e[x] >= 0) {
+        const NetRec r = load_rec(rec, e[x], wide);
+        we[x] = r.w;
+        le[x] = r.lam;
+        if ((r.ones >> from) & 1ull) g.ben += r.w;
+        g.wsum += r.w;
+      }
+    }
+    if (k <= GAIN_REDUCE_K) {
+      for (int t = 0; t < k; ++t) {
+        unsigned mine = 0;
+#pragma unroll
+        for (int x = 0; x < GAIN_VEC; ++x) mine += ((le[x] >> t) & 1ull) ? (unsigned)we[x] : 0u;
+        const unsigned sum = __reduce_add_sync(FULL, mine);
+        if (lane == t) g.acc0 += sum;
+      }
+    } else {
+#pragma unroll
+      for (int x = 0; x < GAIN_VEC; ++x) {
+        unsigned long long l = le[x];
+        int32_t delta = we[x];
+        if (2 * __popcll(l) > k) {
+          g.full += we[x];
+          l = ~l & kmask;
+          delta = -we[x];
+        }
+        while (l) {
+          atomicAdd(&s_cnt[__ffsll((long long)l) - 1], delta);
+          l &= l - 1;
+        }
+      }
+    }
+  }
+  return g;
+}
+
 // Graph levels (Sec. 10, "The Gain Table"): the gain of moving u to V_t is
 // w(u, V_t) - w(u, V_Pi(u)), the weight of u's edges into V_t minus that of
 // its edges into its own block, which equals the gain of Sec. 6 for nets of
@@ -473,7 +550,9 @@ __global__ void __launch_bounds__(GAIN_BLOCK_WARPS * 32) k_lp_gain_block(GainArg
     const int32_t beg = A.ioff[u], end = A.ioff[u + 1];
     GainPart g =
         A.graph ? gain_partial_graph(A.adj, A.part, A.k, beg, end, wv, WARPS, cnt)
-                : gain_partial(A.inets, A.rec, A.wide, A.k, from, beg, end, wv, WARPS, cnt);
+        : A.k <= GAIN_REDUCE_K
+            ? gain_partial_vec(A.inets, A.rec, A.wide, A.k, from, beg, end, wv, WARPS, cnt)
+            : gain_partial(A.inets, A.rec, A.wide, A.k, from, beg, end, wv, WARPS, cnt);
     gain_collect(g, cnt, A.k);
     if (A.graph) graph_gain_terms(g, from);
     s_acc[wv][lane] = g.acc0;
