@@ -143,24 +143,31 @@ def sum_over_ranks(world, x: float) -> float:
 
 # ------------------------------------------------------------ CPU oracle
 
-ORACLE_SAMPLE_N = int(os.environ.get("BENCH_ORACLE_N", "200000"))
+# Bounded samples of the workload for the CPU oracle: the baseline leg of the
+# GPU line (one run, about 10-30 s of single-threaded work on the GPU machine's
+# host) and every step of the reference arm (a few seconds, so that its
+# warm-up and timed steps end within a few minutes).
+ORACLE_SAMPLE_N = int(os.environ.get("BENCH_ORACLE_N", "60000"))
+REFERENCE_STEP_N = int(os.environ.get("BENCH_REFERENCE_N", "20000"))
 
 
-def oracle_sample():
+def oracle_sample(n=None):
     """Times the CPU oracle (as it stands, one core) on a bounded sample of
-    the same workload shape: the Zipf(2.2) hypergraph scaled to n = m = 200,000 (about ten
-    seconds of single-threaded work)."""
+    the same workload shape: the Zipf(2.2) hypergraph scaled to n = m nodes
+    and nets (full V-cycle, k = 8)."""
     import oracle
     import synth
-    hgr = synth.zipf_1m(SEED, n=ORACLE_SAMPLE_N)
+    n = ORACLE_SAMPLE_N if n is None else n
+    hgr = synth.zipf_1m(SEED, n=n)
     t0 = time.perf_counter()
     vc = oracle.multilevel(hgr, K_BLOCKS, EPS_PPM, S=16, T=1000, factor=160, seed=SEED,
                            max_passes=PASSES)
     dt = time.perf_counter() - t0
     pins = sum(int(l.p) for l in vc.levels)
     return dict(value=pins / dt, seconds=dt, pins=pins, levels=len(vc.levels),
-                sample=f"Zipf(2.2) hypergraph scaled to n=m={ORACLE_SAMPLE_N:,} ({hgr.p} pins, "
-                       f"{len(vc.levels)} levels), full V-cycle, one process, single-threaded oracle")
+                sample=f"Zipf(2.2) hypergraph scaled to n=m={n:,} ({hgr.p} pins, "
+                       f"{len(vc.levels)} levels, {pins} level-pins), full V-cycle, one process, "
+                       "single-threaded oracle")
 
 
 def run_reference(args, world, rank):
@@ -169,7 +176,7 @@ def run_reference(args, world, rank):
     vals = []
     info = None
     for i in range(args.warmup + args.steps):
-        r = oracle_sample()
+        r = oracle_sample(REFERENCE_STEP_N)
         if i >= args.warmup:
             vals.append(r["value"])
             info = r
