@@ -24,6 +24,13 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# The executor's slots each run on their own stream; the CUDA runtime maps
+# streams onto CUDA_DEVICE_MAX_CONNECTIONS hardware queues (8 by default), and
+# streams sharing a queue serialise each other's dependent launches.  32
+# queues (the maximum) let 16-32 slots overlap; read when the process creates
+# its CUDA context, so it is set before anything touches CUDA.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 METRIC = "pins/s per coarsen+LP level on 1 GB300, batched vs plain; serve p50/p99 ms"
 K_BLOCKS, EPS_PPM, PASSES, SEED = 8, 30000, 5, 1
 WORKLOAD = ("hypergraph n=m=1,000,000: Zipf(2.2) net sizes in [2,1024], preferential pins, "

@@ -366,7 +366,11 @@ int hg_partition(hg_t* h, int32_t k, int32_t eps_ppm, int32_t max_passes, int32_
  * and the estimated device bytes of the running jobs plus the next one fit
  * mem_budget_bytes (0: 80 % of the device memory free at creation); a job
  * whose estimate exceeds the whole budget starts once nothing else runs.
- * The kernels of jobs on different slots overlap on the device.
+ * The kernels of jobs on different slots overlap on the device.  The CUDA
+ * runtime maps streams onto CUDA_DEVICE_MAX_CONNECTIONS hardware queues (8
+ * by default), and streams that share a queue serialise each other's
+ * dependent launches: set it to 32 (or at least the slot count) in the
+ * environment before the process creates its CUDA context.
  * ------------------------------------------------------------------ */
 typedef struct hg_exec_t hg_exec_t;
 

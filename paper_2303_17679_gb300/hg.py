@@ -479,7 +479,11 @@ def hg_exec_destroy(ex):
 
 
 class Executor:
-    """Keeps each job's host arrays alive until its result has been returned."""
+    """Keeps each job's host arrays alive until its result has been returned.
+
+    Slots overlap on the device only as far as the CUDA runtime gives their
+    streams separate hardware queues: set CUDA_DEVICE_MAX_CONNECTIONS=32 in
+    the environment before the process creates its CUDA context."""
 
     def __init__(self, slots, mem_budget_bytes=0, opt: hg_options | None = None):
         self.ex = hg_exec_create(slots, mem_budget_bytes, opt)
