@@ -44,8 +44,11 @@ L2_FLUSH_BYTES = 512 << 20
 # captures are summarised under profiles/.
 TRAFFIC = {
     "rating": {"source": "paper_2303_17679_gb300/csrc/coarsen.cu",
-               "source_sha256": "661e7a550beff5fa19897901ad138f0c1d14c9b1a200e2dd34612f435e255885",
-               "bytes_per_launch": 23338360},
+               "source_sha256": "5e90d7a223e1e0c725d1f22ee192af4de239b149100b095f28479b9e7977e0bf",
+               "bytes_per_launch": 23318916},
+    "lp_gain": {"source": "paper_2303_17679_gb300/csrc/refine.cu",
+                "source_sha256": "889f7dbadaa126ba6a275a766798746cda9eef2c9e6d2869382a40ca0ad7bfdd",
+                "bytes_per_launch": 7013833},
 }
 
 
@@ -499,7 +502,8 @@ def family_rooflines(agg, steps, bm, peak):
     fam = {}
     spec = [("rating", "k_rate_* (heavy-edge rating, a3)", "ms_rating_kernels", bm["rating"],
              agg["rating_launches"]),
-            ("lp_gain", "k_lp_gain_* (LP best moves, a11; both branches of a sub-round)",
+            ("lp_gain", "k_lp_gain_* (LP best moves, a11; both branches of a sub-round, "
+                        "so a 'launch' here is one sub-round of two kernels)",
              "ms_lp_gain_kernels", bm["lp_gain"], agg["lp_gain_launches"] // 2),
             ("lp_select", "k_lp_select / k_lp_bucket (a12)", "ms_lp_select_kernels", None, None),
             ("lp_apply", "k_lp_apply (a13)", "ms_lp_apply_kernels", bm["lp_apply"],
@@ -753,6 +757,9 @@ def run_ours(args, world, rank, local):
     ms_step = statistics.mean(step_ms)
     ni = iagg["instrumented_steps"]
     fam = family_rooflines(iagg, ni, bm, peak)
+    for key, tref in TRAFFIC.items():
+        fresh = tref["source_sha256"] == _source_sha256(tref["source"])
+        fam[key]["dram_bytes_per_launch_ncu"] = tref["bytes_per_launch"] if fresh else None
     dom = max(("rating", "lp_gain"), key=lambda f: fam[f]["ms_per_step"])
     d = fam[dom]
     traffic = None
