@@ -91,6 +91,14 @@ enum { CW_MOVES = 0, CW_TOUCHED = 1, CW_SLOTS = 2, CW_CURSOR = 3, CW_WORDS = 8 }
 // work counters
 enum { ST_PINS = 0, ST_INCID = 1, ST_NODES = 2, ST_WORDS = 4 };
 
+// Per incidence (aligned with inets): the first pin position of its net,
+// the net's size when it is rated (2 <= |e| <= T), else 0, and its Q20 term
+// (0 when not rated).
+struct __align__(16) IncMeta {
+  int32_t start, eff;
+  unsigned long long r;
+};
+
 struct RateArgs {
   const int32_t* ioff;
   const int32_t* inets;
@@ -108,6 +116,13 @@ struct RateArgs {
   const int32_t* comm;
   const int32_t* pcomm;
   const unsigned long long* rterm;  // Q20 net term of every rated net, 0 otherwise
+  // hypergraph levels: the metadata of the net of every incidence (aligned
+  // with inets), so a walk reads one record per incident net
+  const IncMeta* imeta;
+  // {u, ioff[u], ioff[u + 1], c(u)} of every listed node: lnode is aligned
+  // with list (this class and sub-round), lsplit with the split nodes
+  const int4* lnode;
+  const int4* lsplit;
   const int32_t* c;
   const int2* cst;  // {cw, status}
   int s, T;
@@ -389,16 +404,16 @@ struct NetMeta {
   VT r;
 };
 
+// The metadata of incidence j (-1: none): the first pin position of its net,
+// the net's size if it is rated (else 0) and its Q20 term.
 template <typename VT>
-__device__ __forceinline__ NetMeta<VT> net_meta(const RateArgs& A, int32_t e) {
+__device__ __forceinline__ NetMeta<VT> inc_meta(const RateArgs& A, int32_t j) {
   NetMeta<VT> m{0, 0, (VT)0};
-  if (e >= 0) {
-    const unsigned long long r = A.rterm[e];
-    m.start = A.eoff[e];
-    if (r != 0) {
-      m.eff = A.eoff[e + 1] - m.start;
-      m.r = (VT)r;
-    }
+  if (j >= 0) {
+    const IncMeta x = A.imeta[j];
+    m.start = x.start;
+    m.eff = x.eff;
+    m.r = (VT)x.r;
   }
   return m;
 }
@@ -468,13 +483,13 @@ template <typename VT, typename Visit>
 __device__ __forceinline__ int32_t rate_group_raw(const RateArgs& A, int32_t g0, int32_t end,
                                                   int wt, int TW, int32_t& run, Visit& visit_batch) {
   if (A.graph) return graph_walk<VT>(A, g0, min(g0 + 32, end), wt, TW, visit_batch);
-  const int32_t e = g0 + lane_id() < end ? A.inets[g0 + lane_id()] : -1;
-  return walk_group<VT>(net_meta<VT>(A, e), wt, TW, run, visit_batch);
+  const int32_t j = g0 + lane_id();
+  return walk_group<VT>(inc_meta<VT>(A, j < end ? j : -1), wt, TW, run, visit_batch);
 }
 
 // The groups g0 = first, first + step, ... (< end) of I(u), walked as by
-// rate_group_raw with the loads of the next group's net metadata and of the
-// net ids of the group after it issued before the current group is walked.
+// rate_group_raw with the load of the next group's net metadata issued
+// before the current group is walked.
 template <typename VT, typename Visit>
 __device__ __forceinline__ int64_t rate_groups_raw(const RateArgs& A, int32_t first, int32_t end,
                                                    int32_t step, int wt, int TW, int32_t& run,
@@ -489,12 +504,10 @@ __device__ __forceinline__ int64_t rate_groups_raw(const RateArgs& A, int32_t fi
     return visits;
   }
   int32_t g = first;
-  NetMeta<VT> m = net_meta<VT>(A, g + lane < end ? A.inets[g + lane] : -1);
-  int32_t e_next = g + step + lane < end ? A.inets[g + step + lane] : -1;
+  NetMeta<VT> m = inc_meta<VT>(A, g + lane < end ? g + lane : -1);
   while (g < end) {
     const int32_t gn = g + step;
-    const NetMeta<VT> mn = net_meta<VT>(A, e_next);
-    e_next = gn + step + lane < end ? A.inets[gn + step + lane] : -1;
+    const NetMeta<VT> mn = inc_meta<VT>(A, gn + lane < end ? gn + lane : -1);
     visits += walk_group<VT>(m, wt, TW, run, visit_batch);
     m = mn;
     g = gn;
@@ -594,9 +607,9 @@ __global__ void __launch_bounds__(TW * 32 * TEAMS, 1024 / (TW * 32 * TEAMS)) k_r
   int64_t visits = 0, incid = 0, nodes = 0;
   int it = 0;
   for (int32_t i = blockIdx.x * TEAMS + team; i < A.count; i += gridDim.x * TEAMS) {
-    const int32_t u = A.list[i];
+    const int4 nd = A.lnode[i];
+    const int32_t u = nd.x, beg = nd.y, end = nd.z, cu = nd.w;
     if (A.cst[u].y < 0) continue;  // joined a cluster in an earlier sub-round
-    const int32_t cu = A.c[u], beg = A.ioff[u], end = A.ioff[u + 1];
     // the used-slot counter of this node; the other one is cleared for the
     // next node once every thread has read this one
     int32_t* nused = &s_nused[team][it & 1];
@@ -667,9 +680,9 @@ __global__ void __launch_bounds__(256, 4) k_rate_dense(RateArgs A) {
   int64_t visits = 0, incid = 0, nodes = 0;
   int it = 0;
   for (int32_t i = blockIdx.x; i < A.count; i += gridDim.x) {
-    const int32_t u = A.list[i];
+    const int4 nd = A.lnode[i];
+    const int32_t u = nd.x, beg = nd.y, end = nd.z, cu = nd.w;
     if (A.cst[u].y < 0) continue;
-    const int32_t cu = A.c[u], beg = A.ioff[u], end = A.ioff[u + 1];
     // touched-id counter of this node; the other one is cleared for the next
     // node once every thread has read this one
     int32_t* nused = &s_nused[it & 1];
@@ -733,9 +746,9 @@ k_rate_split_acc(RateArgs A, const int32_t* __restrict__ split, const int32_t* _
   for (int32_t t = item_lo + blockIdx.x * SPLIT_WARPS + warp_in_block(); t < item_hi;
        t += gridDim.x * SPLIT_WARPS) {
     const int32_t i = item_node[t];
-    const int32_t u = split[i];
+    const int4 nd = A.lsplit[i];
+    const int32_t u = nd.x, beg = nd.y, end = nd.z, cu = nd.w;
     if (A.cst[u].y < 0) continue;
-    const int32_t cu = A.c[u], beg = A.ioff[u], end = A.ioff[u + 1];
     const int32_t g0 = beg + 32 * (t - item_off[i]);
     const int64_t base = tab_off[i] - tab_base;
     VT* val = tval + base;
@@ -857,10 +870,10 @@ k_rate_part(RateArgs A, const int32_t* __restrict__ split, const int32_t* __rest
   int it = 0;
   for (int32_t t = part_lo + blockIdx.x; t < part_hi; t += gridDim.x) {
     const int32_t i = part_node[t];
-    const int32_t u = split[i];
+    const int4 nd = A.lsplit[i];
+    const int32_t u = nd.x, beg = nd.y, end = nd.z, cu = nd.w;
     if (A.cst[u].y < 0) continue;  // joined a cluster in an earlier sub-round
     const int32_t P = part_off[i + 1] - part_off[i], k = t - part_off[i];
-    const int32_t cu = A.c[u], beg = A.ioff[u], end = A.ioff[u + 1];
     // slots inserted for this part (listed while they fit the list); the
     // other counter is cleared for the next part once every thread has read
     // this one
@@ -1037,6 +1050,32 @@ __global__ void k_net_terms(const int32_t* __restrict__ eoff, const int32_t* __r
     rterm[e] = (sz >= 2 && sz <= T)
                    ? (((unsigned long long)w[e]) << 20) / (unsigned long long)(sz - 1)
                    : 0ull;
+  }
+}
+
+// IncMeta of every incidence of a hypergraph level.
+__global__ void k_inc_meta(const int32_t* __restrict__ inets, const int32_t* __restrict__ eoff,
+                           const unsigned long long* __restrict__ rterm, int64_t p,
+                           IncMeta* __restrict__ imeta) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t e = inets[j];
+    const unsigned long long r = rterm[e];
+    IncMeta x;
+    x.start = eoff[e];
+    x.eff = r != 0 ? eoff[e + 1] - x.start : 0;
+    x.r = r;
+    imeta[j] = x;
+  }
+}
+
+// {u, ioff[u], ioff[u + 1], c(u)} of every listed node.
+__global__ void k_list_nodes(const int32_t* __restrict__ list, int32_t cnt,
+                             const int32_t* __restrict__ ioff, const int32_t* __restrict__ c,
+                             int4* __restrict__ lnode) {
+  for (int32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < cnt; x += gridDim.x * blockDim.x) {
+    const int32_t u = list[x];
+    lnode[x] = make_int4(u, ioff[u], ioff[u + 1], c[u]);
   }
 }
 
@@ -1594,12 +1633,14 @@ void launch_team(const Ctx& cx, const RateArgs& A, uint32_t slots) {
 
 template <typename VT>
 void rate_subround(const Ctx& cx, RateArgs A, const std::vector<int32_t>& hoff, const int32_t* list,
-                   int S, int s, bool dense_block, SplitPlan& sp, KernelTimer* timers,
+                   const int4* lnode, int S, int s, bool dense_block, SplitPlan& sp,
+                   KernelTimer* timers,
                    unsigned long long* stats_base, CoarsenCounters& cc) {
   set_rate_attrs<VT>();
   for (int cls = 0; cls < SPLIT_CLASS; ++cls) {
     A.count = hoff[cls * S + s + 1] - hoff[cls * S + s];
     A.list = list + hoff[cls * S + s];
+    A.lnode = lnode + hoff[cls * S + s];
     if (A.count == 0) continue;
     A.stats = stats_base + (size_t)cls * ST_WORDS;
     KernelTimer& timer = timers[cls];
@@ -1775,6 +1816,24 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   check_status(cx);
   std::vector<int32_t> hoff(nkeys + 1, 0);
   for (int i = 0; i < nkeys; ++i) hoff[i + 1] = hoff[i] + hcount[i];
+  // per listed node {u, ioff[u], ioff[u + 1], c(u)}, and on hypergraph
+  // levels the net metadata of every incidence, for the rating walks
+  DBuf<int4> lnode;
+  lnode.alloc(&cx.alloc, (size_t)std::max<int32_t>(hoff[nkeys], 1));
+  if (hoff[nkeys] > 0) {
+    k_list_nodes<<<grid_for(hoff[nkeys], 256, cx.num_sms, 8), 256, 0, cx.stream>>>(
+        list.p, hoff[nkeys], L.ioff.p, L.c.p, lnode.p);
+    check_launch("list_nodes");
+    if (cx.launches) *cx.launches += 1;
+  }
+  DBuf<IncMeta> imeta;
+  if (!L.graph && L.p > 0) {
+    imeta.alloc(&cx.alloc, (size_t)L.p);
+    k_inc_meta<<<grid_for(L.p, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(L.inets.p, L.eoff.p,
+                                                                         rterm.p, L.p, imeta.p);
+    check_launch("inc_meta");
+    if (cx.launches) *cx.launches += 1;
+  }
 
   // ---- split plan: items, table offsets and footprint per sub-round
   SplitPlan sp;
@@ -1912,6 +1971,8 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
     A.pcomm = pcomm.p;
   }
   A.rterm = rterm.p;
+  A.imeta = imeta.p;
+  A.lsplit = lnode.p + split_base;
   A.c = L.c.p;
   A.cst = cst.p;
   A.T = P.T;
@@ -1948,10 +2009,10 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
       EventTimer tm(cx, &cc.ms_rating);
       const int64_t before = cc.rating_launches;
       if (narrow)
-        rate_subround<uint32_t>(lx, A, hoff, list.p, S, s, dense_block, sp, rate_timers.data(),
-                                stats.p, cc);
+        rate_subround<uint32_t>(lx, A, hoff, list.p, lnode.p, S, s, dense_block, sp,
+                                rate_timers.data(), stats.p, cc);
       else
-        rate_subround<unsigned long long>(lx, A, hoff, list.p, S, s, dense_block, sp,
+        rate_subround<unsigned long long>(lx, A, hoff, list.p, lnode.p, S, s, dense_block, sp,
                                           rate_timers.data(), stats.p, cc);
       if (cx.launches) *cx.launches += cc.rating_launches - before;
     }
