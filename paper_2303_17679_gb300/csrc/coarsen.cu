@@ -1435,12 +1435,29 @@ k_posmap_init(const int32_t* __restrict__ eoff, const int32_t* __restrict__ pins
 // The incidences of the listed nodes of one sub-round, one thread each: the
 // nodes of sub-round s sit in one range of the class-ordered node list per
 // class, and lpre is the exclusive prefix sum of the degrees along that list,
-// so the incidence ranks of each range are contiguous and a binary search in
-// lpre finds the node of a rank.  Nodes that did not join a cluster in the
-// sub-round (rep[u] == u) are skipped.
+// so the incidence ranks of each range are contiguous.  The ranks are cut
+// into tiles of POS_TILE; tile_node[T] is the listed node holding rank
+// T * POS_TILE, and since every listed node has an incident net, the tile's
+// ranks belong to that node and the POS_TILE after it at most: a block stages
+// their prefix sums in shared memory and each thread finds its node there.
+// Nodes that did not join a cluster in the sub-round (rep[u] == u) are
+// skipped.
+constexpr int POS_TILE = 256;
+
 struct SubRanges {
   int32_t lo[NCLASS], hi[NCLASS];
 };
+
+// tile_node[T] for every tile T of the ranks of the whole list.
+__global__ void k_tile_node(const int32_t* __restrict__ lpre, int32_t nlisted,
+                            int32_t* __restrict__ tile_node) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nlisted;
+       i += gridDim.x * blockDim.x) {
+    const int32_t t0 = (lpre[i] + POS_TILE - 1) / POS_TILE;
+    const int32_t t1 = (lpre[i + 1] + POS_TILE - 1) / POS_TILE;
+    for (int32_t t = t0; t < t1; ++t) tile_node[t] = i;
+  }
+}
 
 // Pass 1 (JOIN): for a rated incidence (u, e) of a node that joined C, insert
 // (e, C), lower its first position to q and clear the position it displaced;
@@ -1448,54 +1465,65 @@ struct SubRanges {
 // Pass 2: cluster word of q = C where q is now C's first position in the
 // net, else -1.  `rx` is the cluster word of the rinfo records (stride 2).
 template <bool JOIN>
-__global__ void __launch_bounds__(256)
-k_posmap_pass(const int32_t* __restrict__ list, const int32_t* __restrict__ lpre, SubRanges R,
-              const int32_t* __restrict__ rep, const int32_t* __restrict__ ioff,
-              const int32_t* __restrict__ inets, const int32_t* __restrict__ ipin,
-              const int32_t* __restrict__ eoff, int T, PosMap M, uint32_t* __restrict__ jslot,
-              int32_t* __restrict__ rx, int32_t* status) {
-  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+__global__ void __launch_bounds__(POS_TILE)
+k_posmap_pass(const int4* __restrict__ lnode, const int32_t* __restrict__ lpre,
+              const int32_t* __restrict__ tile_node, int32_t nlisted, SubRanges R,
+              const int32_t* __restrict__ rep, const int32_t* __restrict__ inets,
+              const int32_t* __restrict__ ipin, const int32_t* __restrict__ eoff, int T, PosMap M,
+              uint32_t* __restrict__ jslot, int32_t* __restrict__ rx, int32_t* status) {
+  __shared__ int32_t s_pre[POS_TILE + 1];
 #pragma unroll 1
   for (int c = 0; c < NCLASS; ++c) {
     const int32_t lo = R.lo[c], hi = R.hi[c];
     if (lo >= hi) continue;
-    const int32_t base = lpre[lo];
-    const int32_t cnt = lpre[hi] - base;
-    for (int64_t t = gt; t < cnt; t += gs) {
-      const int32_t x = base + (int32_t)t;
-      int32_t a = lo, b = hi - 1;  // largest i in [lo, hi) with lpre[i] <= x
-      while (a < b) {
-        const int32_t mid = (a + b + 1) >> 1;
-        if (lpre[mid] <= x) a = mid;
-        else b = mid - 1;
-      }
-      const int32_t u = list[a];
-      const int32_t C = rep[u];
-      if (C == u) continue;
-      const int32_t j = ioff[u] + (x - lpre[a]);
-      if (JOIN) {
-        const int32_t e = inets[j];
-        const int32_t sz = eoff[e + 1] - eoff[e];
-        uint32_t slot = ~0u;
-        if (sz >= 2 && sz <= T) {
-          const int32_t q = ipin[j];
-          const int64_t sl = posmap_slot(M, e, C);
-          if (sl < 0) {
-            dev_fail(status, DEV_HASH_FULL);
-          } else {
-            slot = (uint32_t)sl;
-            const int32_t old = atomicMin(&M.pos[sl], q);
-            if (old != 0x7fffffff && q < old) rx[2 * (int64_t)old] = -1;  // the displaced first position
+    const int32_t r0 = lpre[lo], r1 = lpre[hi];
+    const int32_t t_end = (r1 + POS_TILE - 1) / POS_TILE;
+    for (int32_t tile = r0 / POS_TILE + blockIdx.x; tile < t_end; tile += gridDim.x) {
+      const int32_t a0 = tile_node[tile];
+      const int32_t nn = min(POS_TILE + 1, nlisted - a0 + 1);
+      for (int i = threadIdx.x; i < nn; i += blockDim.x) s_pre[i] = lpre[a0 + i];
+      __syncthreads();
+      const int32_t x = tile * POS_TILE + (int32_t)threadIdx.x;
+      if (x >= r0 && x < r1) {
+        int32_t a = 0, b = nn - 2;  // largest i with s_pre[i] <= x
+        while (a < b) {
+          const int32_t mid = (a + b + 1) >> 1;
+          if (s_pre[mid] <= x) a = mid;
+          else b = mid - 1;
+        }
+        const int4 nd = lnode[a0 + a];
+        const int32_t u = nd.x;
+        const int32_t C = rep[u];
+        const int32_t j = nd.y + (x - s_pre[a]);
+        if (j >= nd.z) {
+          dev_fail(status, DEV_CAPACITY);  // the tile outran its staged nodes
+        } else if (C == u) {
+          // not joined
+        } else if (JOIN) {
+          const int32_t e = inets[j];
+          const int32_t sz = eoff[e + 1] - eoff[e];
+          uint32_t slot = ~0u;
+          if (sz >= 2 && sz <= T) {
+            const int32_t q = ipin[j];
+            const int64_t sl = posmap_slot(M, e, C);
+            if (sl < 0) {
+              dev_fail(status, DEV_HASH_FULL);
+            } else {
+              slot = (uint32_t)sl;
+              const int32_t old = atomicMin(&M.pos[sl], q);
+              if (old != 0x7fffffff && q < old) rx[2 * (int64_t)old] = -1;  // the displaced first position
+            }
+          }
+          jslot[j] = slot;
+        } else {
+          const uint32_t sl = jslot[j];
+          if (sl != ~0u) {
+            const int32_t q = ipin[j];
+            rx[2 * (int64_t)q] = M.pos[sl] == q ? C : -1;
           }
         }
-        jslot[j] = slot;
-      } else {
-        const uint32_t sl = jslot[j];
-        if (sl == ~0u) continue;
-        const int32_t q = ipin[j];
-        rx[2 * (int64_t)q] = M.pos[sl] == q ? C : -1;
       }
+      __syncthreads();
     }
   }
 }
@@ -1528,32 +1556,49 @@ __global__ void k_pin_comm(const int32_t* __restrict__ pins, int64_t p,
 }
 
 // Weight words of every record before sub-round s: the cluster's weight, or
-// INT32_MAX for an unclustered node of sub-round s.  Two records per thread
-// and iteration (16-byte loads and stores).
+// INT32_MAX for an unclustered node of sub-round s.  A thread takes
+// REFRESH_ILP pairs of records per iteration (16-byte loads, all issued before
+// the cluster gathers) and stores only the weight words that change.
+constexpr int REFRESH_ILP = 4;
+
+__device__ __forceinline__ int32_t refresh_word(const int2* __restrict__ cst, int32_t C, int s,
+                                                int32_t old) {
+  if (C < 0) return old;
+  const int2 cs = cst[C];
+  return cs.y == s ? 0x7fffffff : cs.x;
+}
+
 __global__ void k_rinfo_refresh(int2* __restrict__ rinfo, int64_t p, const int2* __restrict__ cst,
                                 int s) {
   const int64_t pairs = p >> 1;
-  int4* r4 = reinterpret_cast<int4*>(rinfo);
+  const int4* r4 = reinterpret_cast<const int4*>(rinfo);
+  int32_t* words = reinterpret_cast<int32_t*>(rinfo);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < pairs; i += stride) {
-    int4 r = r4[i];
-    if (r.x >= 0) {
-      const int2 cs = cst[r.x];
-      r.y = cs.y == s ? 0x7fffffff : cs.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < pairs;
+       i0 += REFRESH_ILP * stride) {
+    int4 r[REFRESH_ILP];
+#pragma unroll
+    for (int k = 0; k < REFRESH_ILP; ++k) {
+      const int64_t i = i0 + k * stride;
+      r[k] = i < pairs ? r4[i] : make_int4(-1, 0, -1, 0);
     }
-    if (r.z >= 0) {
-      const int2 cs = cst[r.z];
-      r.w = cs.y == s ? 0x7fffffff : cs.x;
+    int32_t y[REFRESH_ILP], w[REFRESH_ILP];
+#pragma unroll
+    for (int k = 0; k < REFRESH_ILP; ++k) {
+      y[k] = refresh_word(cst, r[k].x, s, r[k].y);
+      w[k] = refresh_word(cst, r[k].z, s, r[k].w);
     }
-    r4[i] = r;
+#pragma unroll
+    for (int k = 0; k < REFRESH_ILP; ++k) {
+      const int64_t i = i0 + k * stride;
+      if (y[k] != r[k].y) words[4 * i + 1] = y[k];
+      if (w[k] != r[k].w) words[4 * i + 3] = w[k];
+    }
   }
   if ((p & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-    int2 r = rinfo[p - 1];
-    if (r.x >= 0) {
-      const int2 cs = cst[r.x];
-      r.y = cs.y == s ? 0x7fffffff : cs.x;
-    }
-    rinfo[p - 1] = r;
+    const int2 r = rinfo[p - 1];
+    const int32_t y = refresh_word(cst, r.x, s, r.y);
+    if (y != r.y) rinfo[p - 1].y = y;
   }
 }
 
@@ -1919,7 +1964,7 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
   // the start plus one per joining incidence, so 2p keys; capacity >= 4p
   // (at most 2^32, which still exceeds 2p since p < 2^31).
   DBuf<unsigned long long> pm_key;
-  DBuf<int32_t> pm_pos, lpre;
+  DBuf<int32_t> pm_pos, lpre, tile_node;
   DBuf<uint32_t> jslot;
   PosMap pm;
   pm.key = nullptr;
@@ -1945,10 +1990,16 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
       check_launch("list_degree");
     }
     scan_exclusive_i32(cx, lpre.p, lpre.p, nlisted, lpre.p + nlisted);
+    tile_node.alloc(&cx.alloc, (size_t)(L.p / POS_TILE + 2));
+    if (nlisted > 0) {
+      k_tile_node<<<grid_for(nlisted, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(lpre.p, nlisted,
+                                                                               tile_node.p);
+      check_launch("tile_node");
+    }
     k_posmap_init<<<grid_for(num_pin_tiles(L.p), 1, cx.num_sms, 8), PIN_TILE_THREADS, 0,
                     cx.stream>>>(L.eoff.p, L.pins.p, tiles.p, L.m, L.p, P.T, pm, cx.d_status);
     check_launch("posmap_init");
-    if (cx.launches) *cx.launches += 1 + (nlisted > 0);
+    if (cx.launches) *cx.launches += 1 + 2 * (nlisted > 0);
   }
 
   RateArgs A;
@@ -2042,15 +2093,13 @@ void cluster_level(const Ctx& cx, Level& L, const CoarsenParams& P, CoarsenCount
         R.hi[c] = hoff[c * S + s + 1];
       }
       const int g = cx.num_sms * 8;
-      k_posmap_pass<true><<<g, 256, 0, lx.stream>>>(list.p, lpre.p, R, L.rep.p, L.ioff.p,
-                                                    L.inets.p, L.ipin.p, L.eoff.p, P.T, pm,
-                                                    jslot.p, reinterpret_cast<int32_t*>(rinfo.p),
-                                                    cx.d_status);
+      k_posmap_pass<true><<<g, POS_TILE, 0, lx.stream>>>(
+          lnode.p, lpre.p, tile_node.p, hoff[nkeys], R, L.rep.p, L.inets.p, L.ipin.p, L.eoff.p,
+          P.T, pm, jslot.p, reinterpret_cast<int32_t*>(rinfo.p), cx.d_status);
       check_launch("posmap_join");
-      k_posmap_pass<false><<<g, 256, 0, lx.stream>>>(list.p, lpre.p, R, L.rep.p, L.ioff.p,
-                                                     L.inets.p, L.ipin.p, L.eoff.p, P.T, pm,
-                                                     jslot.p, reinterpret_cast<int32_t*>(rinfo.p),
-                                                    cx.d_status);
+      k_posmap_pass<false><<<g, POS_TILE, 0, lx.stream>>>(
+          lnode.p, lpre.p, tile_node.p, hoff[nkeys], R, L.rep.p, L.inets.p, L.ipin.p, L.eoff.p,
+          P.T, pm, jslot.p, reinterpret_cast<int32_t*>(rinfo.p), cx.d_status);
       check_launch("posmap_fix");
       if (cx.launches) *cx.launches += 2;
     }
