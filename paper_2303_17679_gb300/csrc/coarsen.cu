@@ -287,25 +287,30 @@ __device__ __forceinline__ WideHash make_hash<WideHash>(unsigned char* base, uin
 
 // ------------------------------------------------------- the rating walk
 
-// Visits per lane kept in flight: the two dependent gathers of a visit (its
-// deduplicated cluster, then that cluster's weight and status) are issued for
-// RATE_ILP visits before any of them is used.
-constexpr int RATE_ILP = 4;
+// Visits per lane kept in flight (ILP, a template parameter of the walks):
+// the record loads of ILP visits are issued before any of them is used.  The
+// team kernels, whose time goes to the per-node steps, walk two at a time;
+// the direct-indexed blocks, part blocks and split items, which walk the
+// long visit lists of heavy nodes, four.
+constexpr int TEAM_ILP = 2;
+constexpr int DENSE_ILP = 4;
+constexpr int PART_ILP = 4;
+constexpr int SPLIT_ILP = 4;
 
 // Adapts a per-visit adder f(C, r) to the batch interface of rate_group.
-template <typename VT, typename F>
+template <typename VT, int ILP, typename F>
 struct EachVisit {
   F f;
-  __device__ __forceinline__ void operator()(const int32_t (&C)[RATE_ILP], const VT (&rr)[RATE_ILP],
-                                             const bool (&ok)[RATE_ILP]) const {
+  __device__ __forceinline__ void operator()(const int32_t (&C)[ILP], const VT (&rr)[ILP],
+                                             const bool (&ok)[ILP]) const {
 #pragma unroll
-    for (int k = 0; k < RATE_ILP; ++k)
+    for (int k = 0; k < ILP; ++k)
       if (ok[k]) f(C[k], rr[k]);
   }
 };
-template <typename VT, typename F>
-__device__ __forceinline__ EachVisit<VT, F> each_visit(F f) {
-  return EachVisit<VT, F>{f};
+template <typename VT, int ILP, typename F>
+__device__ __forceinline__ EachVisit<VT, ILP, F> each_visit(F f) {
+  return EachVisit<VT, ILP, F>{f};
 }
 
 // {cluster, weight word} of a batch of visits (-1 = no visit): on
@@ -315,24 +320,25 @@ __device__ __forceinline__ EachVisit<VT, F> each_visit(F f) {
 // word is the cluster's weight, or INT32_MAX for an unclustered node of this
 // sub-round.
 // cmu >= 0: u's community; a visit in another community is dropped.
-__device__ __forceinline__ void resolve_batch(const RateArgs& A, const int32_t (&q)[RATE_ILP],
-                                              int2 (&ri)[RATE_ILP], int32_t cmu) {
+template <int ILP>
+__device__ __forceinline__ void resolve_batch(const RateArgs& A, const int32_t (&q)[ILP],
+                                              int2 (&ri)[ILP], int32_t cmu) {
   if (!A.graph) {
 #pragma unroll
-    for (int k = 0; k < RATE_ILP; ++k) ri[k] = q[k] >= 0 ? A.rinfo[q[k]] : make_int2(-1, 0);
+    for (int k = 0; k < ILP; ++k) ri[k] = q[k] >= 0 ? A.rinfo[q[k]] : make_int2(-1, 0);
     if (cmu >= 0) {
 #pragma unroll
-      for (int k = 0; k < RATE_ILP; ++k)
+      for (int k = 0; k < ILP; ++k)
         if (ri[k].x >= 0 && A.pcomm[q[k]] != cmu) ri[k].x = -1;
     }
     return;
   }
-  int32_t C[RATE_ILP];
+  int32_t C[ILP];
 #pragma unroll
-  for (int k = 0; k < RATE_ILP; ++k)
+  for (int k = 0; k < ILP; ++k)
     C[k] = q[k] >= 0 && (cmu < 0 || A.comm[q[k]] == cmu) ? A.rep[q[k]] : -1;
 #pragma unroll
-  for (int k = 0; k < RATE_ILP; ++k) {
+  for (int k = 0; k < ILP; ++k) {
     const int2 cs = C[k] >= 0 ? A.cst[C[k]] : make_int2(0, 0);
     ri[k] = make_int2(C[k], cs.y == A.s ? 0x7fffffff : cs.x);
   }
@@ -341,16 +347,16 @@ __device__ __forceinline__ void resolve_batch(const RateArgs& A, const int32_t (
 // Filters a batch of visits (-1 = no visit) and hands it to `add`:
 // admissible C is not u, not an unclustered node of this sub-round (weight
 // word INT32_MAX), and fits c_max.
-template <typename VT, typename Add>
+template <typename VT, int ILP, typename Add>
 __device__ __forceinline__ void visit_filtered(const RateArgs& A, int32_t u, int32_t cu,
-                                               const int32_t (&q)[RATE_ILP],
-                                               const VT (&rr)[RATE_ILP], Add& add) {
-  int2 ri[RATE_ILP];
+                                               const int32_t (&q)[ILP],
+                                               const VT (&rr)[ILP], Add& add) {
+  int2 ri[ILP];
   resolve_batch(A, q, ri, A.comm ? A.comm[u] : -1);
-  int32_t C[RATE_ILP];
-  bool ok[RATE_ILP];
+  int32_t C[ILP];
+  bool ok[ILP];
 #pragma unroll
-  for (int k = 0; k < RATE_ILP; ++k) {
+  for (int k = 0; k < ILP; ++k) {
     C[k] = ri[k].x;
     ok[k] = C[k] >= 0 && C[k] != u && (long long)ri[k].y + cu <= (long long)A.c_max;
   }
@@ -359,18 +365,18 @@ __device__ __forceinline__ void visit_filtered(const RateArgs& A, int32_t u, int
 
 // Graph levels: the visits of incidences [lo, hi) of u are the other
 // endpoints of its edges, each with the edge's term w(e) * 2^20 (the Q20 term
-// of a two-pin net); chunk c of 32 * RATE_ILP incidences goes to warp c mod
+// of a two-pin net); chunk c of 32 * ILP incidences goes to warp c mod
 // TW of the team.  Returns the visits in warp 0 (0 in the other warps).
-template <typename VT, typename Visit>
+template <typename VT, int ILP, typename Visit>
 __device__ __forceinline__ int32_t graph_walk(const RateArgs& A, int32_t lo, int32_t hi, int wt,
                                               int TW, Visit& visit_batch) {
-  constexpr int32_t CH = 32 * RATE_ILP;
+  constexpr int32_t CH = 32 * ILP;
   const int lane = lane_id();
   for (int32_t c0 = lo + CH * wt; c0 < hi; c0 += CH * TW) {
-    int32_t q[RATE_ILP];
-    VT rr[RATE_ILP];
+    int32_t q[ILP];
+    VT rr[ILP];
 #pragma unroll
-    for (int k = 0; k < RATE_ILP; ++k) {
+    for (int k = 0; k < ILP; ++k) {
       const int32_t j = c0 + 32 * k + lane;
       if (j < hi) {
         const int2 a = A.adj[j];
@@ -390,7 +396,7 @@ __device__ __forceinline__ int32_t graph_walk(const RateArgs& A, int32_t lo, int
 // position g0 of I(u), through `add`.  Nets of at least 32 rated pins are
 // walked one at a time with the lanes over their pins; the smaller nets of
 // the group are walked together over their flattened pins.  A team of TW
-// warps shares the group: the chunks of 32 * RATE_ILP visits are numbered on
+// warps shares the group: the chunks of 32 * ILP visits are numbered on
 // from `run` (the chunks the team has walked before, for this node) and warp
 // wt takes those whose number is wt modulo TW, so the team stays balanced
 // across groups; `run` is advanced past the group's chunks.  Returns the
@@ -418,10 +424,10 @@ __device__ __forceinline__ NetMeta<VT> inc_meta(const RateArgs& A, int32_t j) {
   return m;
 }
 
-template <typename VT, typename Visit>
+template <typename VT, int ILP, typename Visit>
 __device__ __forceinline__ int32_t walk_group(const NetMeta<VT>& m, int wt, int TW, int32_t& run,
                                               Visit& visit_batch) {
-  constexpr int32_t CH = 32 * RATE_ILP;
+  constexpr int32_t CH = 32 * ILP;
   const int lane = lane_id();
   const int32_t start = m.start, eff = m.eff;
   const VT r = m.r;
@@ -437,10 +443,10 @@ __device__ __forceinline__ int32_t walk_group(const NetMeta<VT>& m, int wt, int 
     const int32_t first = ((wt - run) % TW + TW) % TW;  // this warp's first chunk of the net
     run += (sz + CH - 1) / CH;
     for (int32_t q0 = CH * first; q0 < sz; q0 += CH * TW) {
-      int32_t q[RATE_ILP];
-      VT rr[RATE_ILP];
+      int32_t q[ILP];
+      VT rr[ILP];
 #pragma unroll
-      for (int k = 0; k < RATE_ILP; ++k) {
+      for (int k = 0; k < ILP; ++k) {
         const int32_t qq = q0 + 32 * k + lane;
         q[k] = qq < sz ? st + qq : -1;
         rr[k] = rj;
@@ -456,10 +462,10 @@ __device__ __forceinline__ int32_t walk_group(const NetMeta<VT>& m, int wt, int 
   const int32_t first = ((wt - run) % TW + TW) % TW;
   run += (Z + CH - 1) / CH;
   for (int32_t f0 = CH * first; f0 < Z; f0 += CH * TW) {
-    int32_t q[RATE_ILP];
-    VT rr[RATE_ILP];
+    int32_t q[ILP];
+    VT rr[ILP];
 #pragma unroll
-    for (int k = 0; k < RATE_ILP; ++k) {
+    for (int k = 0; k < ILP; ++k) {
       const int32_t f = f0 + 32 * k + lane;
       int j = 0;
 #pragma unroll
@@ -479,18 +485,18 @@ __device__ __forceinline__ int32_t walk_group(const NetMeta<VT>& m, int wt, int 
   return wt == 0 ? visits + Z : 0;
 }
 
-template <typename VT, typename Visit>
+template <typename VT, int ILP, typename Visit>
 __device__ __forceinline__ int32_t rate_group_raw(const RateArgs& A, int32_t g0, int32_t end,
                                                   int wt, int TW, int32_t& run, Visit& visit_batch) {
-  if (A.graph) return graph_walk<VT>(A, g0, min(g0 + 32, end), wt, TW, visit_batch);
+  if (A.graph) return graph_walk<VT, ILP>(A, g0, min(g0 + 32, end), wt, TW, visit_batch);
   const int32_t j = g0 + lane_id();
-  return walk_group<VT>(inc_meta<VT>(A, j < end ? j : -1), wt, TW, run, visit_batch);
+  return walk_group<VT, ILP>(inc_meta<VT>(A, j < end ? j : -1), wt, TW, run, visit_batch);
 }
 
 // The groups g0 = first, first + step, ... (< end) of I(u), walked as by
 // rate_group_raw with the load of the next group's net metadata issued
 // before the current group is walked.
-template <typename VT, typename Visit>
+template <typename VT, int ILP, typename Visit>
 __device__ __forceinline__ int64_t rate_groups_raw(const RateArgs& A, int32_t first, int32_t end,
                                                    int32_t step, int wt, int TW, int32_t& run,
                                                    Visit& visit_batch) {
@@ -498,9 +504,9 @@ __device__ __forceinline__ int64_t rate_groups_raw(const RateArgs& A, int32_t fi
   int64_t visits = 0;
   if (first >= end) return 0;
   if (A.graph) {
-    if (step == 32) return graph_walk<VT>(A, first, end, wt, TW, visit_batch);
+    if (step == 32) return graph_walk<VT, ILP>(A, first, end, wt, TW, visit_batch);
     for (int32_t g = first; g < end; g += step)
-      visits += graph_walk<VT>(A, g, min(g + 32, end), wt, TW, visit_batch);
+      visits += graph_walk<VT, ILP>(A, g, min(g + 32, end), wt, TW, visit_batch);
     return visits;
   }
   int32_t g = first;
@@ -508,7 +514,7 @@ __device__ __forceinline__ int64_t rate_groups_raw(const RateArgs& A, int32_t fi
   while (g < end) {
     const int32_t gn = g + step;
     const NetMeta<VT> mn = inc_meta<VT>(A, gn + lane < end ? gn + lane : -1);
-    visits += walk_group<VT>(m, wt, TW, run, visit_batch);
+    visits += walk_group<VT, ILP>(m, wt, TW, run, visit_batch);
     m = mn;
     g = gn;
   }
@@ -517,23 +523,23 @@ __device__ __forceinline__ int64_t rate_groups_raw(const RateArgs& A, int32_t fi
 
 // rate_group_raw / rate_groups_raw with the admissibility filter of
 // visit_filtered in front of `add`.
-template <typename VT, typename Add>
+template <typename VT, int ILP, typename Add>
 __device__ __forceinline__ int32_t rate_group(const RateArgs& A, int32_t u, int32_t cu, int32_t g0,
                                               int32_t end, int wt, int TW, int32_t& run, Add add) {
-  auto visit = [&](const int32_t(&q)[RATE_ILP], const VT(&rr)[RATE_ILP]) HG_INLINE {
-    visit_filtered<VT>(A, u, cu, q, rr, add);
+  auto visit = [&](const int32_t(&q)[ILP], const VT(&rr)[ILP]) HG_INLINE {
+    visit_filtered<VT, ILP>(A, u, cu, q, rr, add);
   };
-  return rate_group_raw<VT>(A, g0, end, wt, TW, run, visit);
+  return rate_group_raw<VT, ILP>(A, g0, end, wt, TW, run, visit);
 }
 
-template <typename VT, typename Add>
+template <typename VT, int ILP, typename Add>
 __device__ __forceinline__ int64_t rate_groups(const RateArgs& A, int32_t u, int32_t cu,
                                                int32_t first, int32_t end, int32_t step, int wt,
                                                int TW, int32_t& run, Add add) {
-  auto visit = [&](const int32_t(&q)[RATE_ILP], const VT(&rr)[RATE_ILP]) HG_INLINE {
-    visit_filtered<VT>(A, u, cu, q, rr, add);
+  auto visit = [&](const int32_t(&q)[ILP], const VT(&rr)[ILP]) HG_INLINE {
+    visit_filtered<VT, ILP>(A, u, cu, q, rr, add);
   };
-  return rate_groups_raw<VT>(A, first, end, step, wt, TW, run, visit);
+  return rate_groups_raw<VT, ILP>(A, first, end, step, wt, TW, run, visit);
 }
 
 template <typename VT>
@@ -614,8 +620,8 @@ __global__ void __launch_bounds__(TW * 32 * TEAMS, 1024 / (TW * 32 * TEAMS)) k_r
     // next node once every thread has read this one
     int32_t* nused = &s_nused[team][it & 1];
     int32_t run = 0;
-    visits += rate_groups<VT>(A, u, cu, beg, end, 32, wt, TW, run,
-                              each_visit<VT>([&](int32_t C, VT r) HG_INLINE {
+    visits += rate_groups<VT, TEAM_ILP>(A, u, cu, beg, end, 32, wt, TW, run,
+                                        each_visit<VT, TEAM_ILP>([&](int32_t C, VT r) HG_INLINE {
                                 const int32_t sl = tab.add(C, r);
                                 if (sl >= 0) used[atomicAdd(nused, 1)] = sl;
                                 else if (sl == ADD_FULL) dev_fail(A.status_word, DEV_HASH_FULL);
@@ -687,8 +693,8 @@ __global__ void __launch_bounds__(256, 4) k_rate_dense(RateArgs A) {
     // node once every thread has read this one
     int32_t* nused = &s_nused[it & 1];
     int32_t run = 0;
-    visits += rate_groups<VT>(A, u, cu, beg, end, 32, wv, nw, run,
-                              each_visit<VT>([&](int32_t C, VT r) HG_INLINE {
+    visits += rate_groups<VT, DENSE_ILP>(A, u, cu, beg, end, 32, wv, nw, run,
+                                         each_visit<VT, DENSE_ILP>([&](int32_t C, VT r) HG_INLINE {
                                 // every term is >= 1, so a zero before the add
                                 // marks the first touch
                                 if (atomicAdd(&val[C], r) == (VT)0)
@@ -758,25 +764,26 @@ k_rate_split_acc(RateArgs A, const int32_t* __restrict__ split, const int32_t* _
     if (tab_dense[i]) {
       // direct-indexed: a reduction without a returned value; the argmax
       // scans the whole table, which is no larger than twice the visits
-      visits += rate_group<VT>(A, u, cu, g0, end, 0, 1, run, each_visit<VT>([&](int32_t C, VT r) HG_INLINE {
+      visits += rate_group<VT, SPLIT_ILP>(A, u, cu, g0, end, 0, 1, run,
+                                          each_visit<VT, SPLIT_ILP>([&](int32_t C, VT r) HG_INLINE {
         atomicAdd(&val[C], r);
       }));
     } else {
       int32_t* key = tkey + base;
       const uint32_t mask = (uint32_t)tab_cap[i] - 1;
-      visits += rate_group<VT>(
+      visits += rate_group<VT, SPLIT_ILP>(
           A, u, cu, g0, end, 0, 1, run,
-          [&](const int32_t(&C)[RATE_ILP], const VT(&rr)[RATE_ILP], const bool(&ok)[RATE_ILP]) HG_INLINE {
+          [&](const int32_t(&C)[SPLIT_ILP], const VT(&rr)[SPLIT_ILP], const bool(&ok)[SPLIT_ILP]) HG_INLINE {
             // the first slot of every visit of the batch is loaded at once
-            uint32_t h[RATE_ILP];
-            int32_t k0[RATE_ILP];
+            uint32_t h[SPLIT_ILP];
+            int32_t k0[SPLIT_ILP];
 #pragma unroll
-            for (int k = 0; k < RATE_ILP; ++k) {
+            for (int k = 0; k < SPLIT_ILP; ++k) {
               h[k] = slot_hash(C[k]) & mask;
               k0[k] = ok[k] ? key[h[k]] : C[k];
             }
 #pragma unroll
-            for (int k = 0; k < RATE_ILP; ++k) {
+            for (int k = 0; k < SPLIT_ILP; ++k) {
               if (!ok[k]) continue;
               uint32_t hh = h[k];
               int32_t kk = k0[k];
@@ -879,11 +886,11 @@ k_rate_part(RateArgs A, const int32_t* __restrict__ split, const int32_t* __rest
     // this one
     int32_t* nused = &s_nused[it & 1];
     const int32_t cmu = A.comm ? A.comm[u] : -1;
-    auto visit = [&](const int32_t(&q)[RATE_ILP], const VT(&rr)[RATE_ILP]) HG_INLINE {
-      int2 ri[RATE_ILP];
+    auto visit = [&](const int32_t(&q)[PART_ILP], const VT(&rr)[PART_ILP]) HG_INLINE {
+      int2 ri[PART_ILP];
       resolve_batch(A, q, ri, cmu);
 #pragma unroll
-      for (int j = 0; j < RATE_ILP; ++j) {
+      for (int j = 0; j < PART_ILP; ++j) {
         const int32_t Cj = ri[j].x;
         if (Cj < 0 || Cj == u || (P != 1 && part_of(Cj, P) != k) ||
             (long long)ri[j].y + cu > (long long)A.c_max)
@@ -898,7 +905,7 @@ k_rate_part(RateArgs A, const int32_t* __restrict__ split, const int32_t* __rest
       }
     };
     int32_t run = 0;
-    const int64_t v = rate_groups_raw<VT>(A, beg + 32 * team, end, 32 * PART_TEAMS, wt, TW, run,
+    const int64_t v = rate_groups_raw<VT, PART_ILP>(A, beg + 32 * team, end, 32 * PART_TEAMS, wt, TW, run,
                                           visit);
     if (k == 0) visits += v;
     __syncthreads();
