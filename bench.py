@@ -44,8 +44,8 @@ L2_FLUSH_BYTES = 512 << 20
 # captures are summarised under profiles/.
 TRAFFIC = {
     "rating": {"source": "paper_2303_17679_gb300/csrc/coarsen.cu",
-               "source_sha256": "5e90d7a223e1e0c725d1f22ee192af4de239b149100b095f28479b9e7977e0bf",
-               "bytes_per_launch": 23318916},
+               "source_sha256": "7aa0826d3707ff1b7de6a75e42c0af837a3b31e0f1b57fcec49264f3f59f18e4",
+               "bytes_per_launch": 21248456},
     "lp_gain": {"source": "paper_2303_17679_gb300/csrc/refine.cu",
                 "source_sha256": "889f7dbadaa126ba6a275a766798746cda9eef2c9e6d2869382a40ca0ad7bfdd",
                 "bytes_per_launch": 7013833},
