@@ -650,53 +650,70 @@ __device__ __forceinline__ unsigned long long sel_key(long long g, int32_t u) {
   return ((unsigned long long)(0x7fffffffLL - g) << 32) | (unsigned)u;
 }
 
-// Bitonic sort of P (a power of two) keys in buf (shared or global) by the block.
-__device__ void block_bitonic_sort(unsigned long long* buf, int P) {
+// The weight prefixes of both directions of a pair from one block-wide scan
+// over the concatenation of their sorted moves: A[x] = weight of the first x
+// moves a->b (x = 0..na), B[x] likewise for b->a.
+__device__ void block_weight_prefix2(const unsigned long long* ka, int na,
+                                     const unsigned long long* kb, int nb,
+                                     const int32_t* __restrict__ c, long long* A, long long* B,
+                                     long long* s_red) {
+  __shared__ long long s_tot_a;
+  if (threadIdx.x == 0) {
+    s_red[32] = 0;
+    s_tot_a = 0;
+    A[0] = 0;
+    B[0] = 0;
+  }
+  __syncthreads();
+  const int cnt = na + nb;
+  for (int base = 0; base < cnt; base += blockDim.x) {
+    const int x = base + threadIdx.x;
+    long long v = 0;
+    if (x < na) v = (long long)c[(int32_t)(ka[x] & 0xffffffffu)];
+    else if (x < cnt) v = (long long)c[(int32_t)(kb[x - na] & 0xffffffffu)];
+    long long y = warp_inclusive_scan(v);
+    if (lane_id() == 31) s_red[warp_in_block()] = y;
+    __syncthreads();
+    if (warp_in_block() == 0) {
+      long long z = lane_id() < (int)(blockDim.x >> 5) ? s_red[lane_id()] : 0;
+      z = warp_inclusive_scan(z);
+      if (lane_id() < (int)(blockDim.x >> 5)) s_red[lane_id()] = z;
+    }
+    __syncthreads();
+    const long long carry = s_red[32];
+    const long long incl = carry + (warp_in_block() ? s_red[warp_in_block() - 1] : 0) + y;
+    if (x < na) A[x + 1] = incl;
+    if (x == na - 1) s_tot_a = incl;
+    __syncthreads();
+    if (x >= na && x < cnt) B[x - na + 1] = incl - s_tot_a;
+    if (threadIdx.x == blockDim.x - 1) s_red[32] = incl;
+    __syncthreads();
+  }
+}
+
+// Bitonic sorts of the two directions of a pair (Pa and Pb powers of two) by
+// the block, stage by stage together: one barrier per stage for both.
+__device__ void block_bitonic_sort2(unsigned long long* a, int Pa, unsigned long long* b, int Pb) {
+  const int P = Pa > Pb ? Pa : Pb;
   for (int kk = 2; kk <= P; kk <<= 1) {
     for (int j = kk >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+      for (int x = threadIdx.x; x < Pa + Pb; x += blockDim.x) {
+        unsigned long long* buf = x < Pa ? a : b;
+        const int i = x < Pa ? x : x - Pa;
+        const int n = x < Pa ? Pa : Pb;
+        if (kk > n) continue;
         const int ixj = i ^ j;
         if (ixj > i) {
-          const unsigned long long a = buf[i], b = buf[ixj];
+          const unsigned long long u = buf[i], v = buf[ixj];
           const bool up = (i & kk) == 0;
-          if ((a > b) == up) {
-            buf[i] = b;
-            buf[ixj] = a;
+          if ((u > v) == up) {
+            buf[i] = v;
+            buf[ixj] = u;
           }
         }
       }
       __syncthreads();
     }
-  }
-}
-
-// pre[x] = weight of the first x sorted moves, x = 0..cnt (block-wide scan).
-__device__ void block_weight_prefix(const unsigned long long* keys, int cnt,
-                                    const int32_t* __restrict__ c, long long* pre,
-                                    long long* s_red) {
-  if (threadIdx.x == 0) {
-    s_red[32] = 0;
-    pre[0] = 0;
-  }
-  __syncthreads();
-  for (int base = 0; base < cnt; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    const long long v = i < cnt ? (long long)c[(int32_t)(keys[i] & 0xffffffffu)] : 0;
-    long long x = warp_inclusive_scan(v);
-    if (lane_id() == 31) s_red[warp_in_block()] = x;
-    __syncthreads();
-    if (warp_in_block() == 0) {
-      long long y = lane_id() < (int)(blockDim.x >> 5) ? s_red[lane_id()] : 0;
-      y = warp_inclusive_scan(y);
-      if (lane_id() < (int)(blockDim.x >> 5)) s_red[lane_id()] = y;
-    }
-    __syncthreads();
-    const long long carry = s_red[32];
-    const long long before = warp_in_block() ? s_red[warp_in_block() - 1] : 0;
-    if (i < cnt) pre[i + 1] = carry + before + x;
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) s_red[32] = carry + before + x;
-    __syncthreads();
   }
 }
 
@@ -834,10 +851,8 @@ k_lp_select(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
     }
   }
   __syncthreads();
-  block_bitonic_sort(ka, Pa);
-  block_bitonic_sort(kb, Pb);
-  block_weight_prefix(ka, na, c, A, s_red);
-  block_weight_prefix(kb, nb, c, B, s_red);
+  block_bitonic_sort2(ka, Pa, kb, Pb);
+  block_weight_prefix2(ka, na, kb, nb, c, A, B, s_red);
 
   // block weights at the start of sub-round s: the pass's starting weights
   // plus the changes applied in its earlier sub-rounds (pair blocks of this
