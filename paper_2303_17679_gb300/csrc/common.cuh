@@ -126,6 +126,25 @@ __device__ __forceinline__ T warp_sum(T x) {
   return x;
 }
 
+// Adds every thread's v[i] to the global counter dst[i] with one atomic per
+// block and counter (a counter hit by an atomic from every warp of a large
+// grid serialises those atomics in one L2 slice).  All threads of the block
+// must call it; it synchronises the block.
+template <int N>
+__device__ __forceinline__ void block_add_counters(unsigned long long* dst,
+                                                   const unsigned long long (&v)[N]) {
+  __shared__ unsigned long long s_sum[N];
+  if (threadIdx.x < N) s_sum[threadIdx.x] = 0;
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const unsigned long long w = warp_sum(v[i]);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd(&s_sum[i], w);
+  }
+  __syncthreads();
+  if (threadIdx.x < N && s_sum[threadIdx.x]) atomicAdd(&dst[threadIdx.x], s_sum[threadIdx.x]);
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_max(T x) {
 #pragma unroll

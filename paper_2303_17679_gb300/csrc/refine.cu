@@ -525,7 +525,70 @@ __global__ void __launch_bounds__(WARPS * 32) k_lp_gain_warp(GainArgs A) {
     if (lane == 0) gain_emit(A, u, from, bg, bt);
     incid += end - beg;
   }
-  if (lane == 0 && incid) atomicAdd(A.work, (unsigned long long)incid);
+  const unsigned long long cv[1] = {lane == 0 ? (unsigned long long)incid : 0ull};
+  block_add_counters(A.work, cv);
+}
+
+// class 0 on hypergraph levels with k <= 16 and few incident nets per node
+// (mean degree <= SUB_MEAN_DEG): one group of SUB_G lanes per node instead of
+// a warp, so a warp has NG nodes' load chains in flight.  Every lane sums
+// w(e) per block of Lambda(e) over its incidences in registers, the group
+// combines the sums with xor shuffles among its own lanes, and every lane of
+// the group picks the same best target.  Groups run independently (their
+// shuffles name only the group's lanes).
+constexpr int SUB_G = 8;
+constexpr int SUB_MEAN_DEG = 16;
+
+__global__ void __launch_bounds__(WARPS * 32) k_lp_gain_sub(GainArgs A) {
+  constexpr int NG = 32 / SUB_G;
+  const int lane = lane_id(), sub = lane % SUB_G, grp = lane / SUB_G;
+  const unsigned gmask = ((1u << SUB_G) - 1u) << (grp * SUB_G);
+  const int32_t lo = A.sr_off[2 * A.s], hi = A.sr_off[2 * A.s + 1];
+  const int k = A.k;
+  unsigned long long incid = 0;
+  for (int32_t i = lo + (blockIdx.x * WARPS + warp_in_block()) * NG + grp; i < hi;
+       i += gridDim.x * WARPS * NG) {
+    const int32_t u = A.list[i];
+    const int from = A.part[u];
+    const int32_t beg = A.ioff[u], end = A.ioff[u + 1];
+    int32_t acc[GAIN_REDUCE_K];
+#pragma unroll
+    for (int t = 0; t < GAIN_REDUCE_K; ++t) acc[t] = 0;
+    long long ben = 0, wsum = 0;
+    for (int32_t j = beg + sub; j < end; j += SUB_G) {
+      const NetRec r = load_rec(A.rec, A.inets[j], A.wide);
+      if ((r.ones >> from) & 1ull) ben += r.w;  // u is the only pin of its block in e
+      wsum += r.w;
+#pragma unroll
+      for (int t = 0; t < GAIN_REDUCE_K; ++t)
+        if ((r.lam >> t) & 1ull) acc[t] += r.w;
+    }
+#pragma unroll
+    for (int d = SUB_G / 2; d > 0; d >>= 1) {
+      ben += __shfl_xor_sync(gmask, ben, d);
+      wsum += __shfl_xor_sync(gmask, wsum, d);
+#pragma unroll
+      for (int t = 0; t < GAIN_REDUCE_K; ++t) acc[t] += __shfl_xor_sync(gmask, acc[t], d);
+    }
+    // (gain desc, t asc), t != from
+    long long best_g = LLONG_MIN;
+    int best_t = -1;
+#pragma unroll
+    for (int t = 0; t < GAIN_REDUCE_K; ++t) {
+      if (t >= k || t == from) continue;
+      const long long g = ben - wsum + acc[t];
+      if (g > best_g) {
+        best_g = g;
+        best_t = t;
+      }
+    }
+    if (sub == 0) {
+      gain_emit(A, u, from, best_g, best_t);
+      incid += (unsigned long long)(end - beg);
+    }
+  }
+  const unsigned long long cv[1] = {incid};
+  block_add_counters(A.work, cv);
 }
 
 // class 1: one block (GAIN_BLOCK_WARPS warps) per node; the warps split I(u)
@@ -981,7 +1044,8 @@ k_lp_apply(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets, 
     }
     if (ch == 0 && lane == 0) part[u] = t;
   }
-  if (lane == 0 && incid) atomicAdd(moved + 2, incid);
+  const unsigned long long cv[1] = {lane == 0 ? incid : 0ull};
+  block_add_counters(moved + 2, cv);
 }
 
 // Folds the pass's block-weight changes into the starting weights of the
@@ -1279,6 +1343,11 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
 
   const int nodes_per_sr = (int)((n + S - 1) / S);
   const int g_gain = grid_for(nodes_per_sr, WARPS, cx.num_sms, 16);
+  // warp-class nodes of hypergraph levels with k <= 16 and a small mean
+  // degree go to lane groups
+  const bool sub_class =
+      !L.graph && k <= GAIN_REDUCE_K && L.p <= (int64_t)SUB_MEAN_DEG * std::max<int32_t>(n, 1);
+  const int g_gain_sub = grid_for(nodes_per_sr, WARPS * (32 / SUB_G), cx.num_sms, 16);
   const int g_gain_block = grid_for(nodes_per_sr, 1, cx.num_sms, 8);
   const int g_bucket = grid_for(nodes_per_sr, 256, cx.num_sms, 4);
   const int g_apply = grid_for((int64_t)acap / S + 1, WARPS, cx.num_sms, 16);
@@ -1287,6 +1356,10 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   KernelTimer gain_timer(cx);
   // nodes above the warp class exist at this level?
   GainArgs G;
+  auto launch_gain_warp = [&](cudaStream_t st) {
+    if (sub_class) k_lp_gain_sub<<<g_gain_sub, WARPS * 32, 0, st>>>(G);
+    else k_lp_gain_warp<<<g_gain, WARPS * 32, 0, st>>>(G);
+  };
   G.ioff = L.ioff.p;
   G.inets = L.inets.p;
   G.rec = rec.p;
@@ -1371,14 +1444,14 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
           HG_CUDA(cudaStreamWaitEvent(fj->side, fj->fork, 0));
           k_lp_gain_block<<<g_gain_block, GAIN_BLOCK_WARPS * 32, 0, fj->side>>>(G);
           check_launch("lp_gain_block");
-          k_lp_gain_warp<<<g_gain, WARPS * 32, 0, sm>>>(G);
+          launch_gain_warp(sm);
           check_launch("lp_gain_warp");
           HG_CUDA(cudaEventRecord(fj->join, fj->side));
           HG_CUDA(cudaStreamWaitEvent(sm, fj->join, 0));
           mark(fj, sm, s, 1);
         } else {
           if (timed) gain_timer.begin();
-          k_lp_gain_warp<<<g_gain, WARPS * 32, 0, sm>>>(G);
+          launch_gain_warp(sm);
           if (timed) gain_timer.end();
           check_launch("lp_gain_warp");
           if (timed) gain_timer.begin();
