@@ -45,10 +45,10 @@ L2_FLUSH_BYTES = 512 << 20
 TRAFFIC = {
     "rating": {"source": "paper_2303_17679_gb300/csrc/coarsen.cu",
                "source_sha256": "7aa0826d3707ff1b7de6a75e42c0af837a3b31e0f1b57fcec49264f3f59f18e4",
-               "bytes_per_launch": 21248456},
+               "bytes_per_launch": 21216630},
     "lp_gain": {"source": "paper_2303_17679_gb300/csrc/refine.cu",
-                "source_sha256": "889f7dbadaa126ba6a275a766798746cda9eef2c9e6d2869382a40ca0ad7bfdd",
-                "bytes_per_launch": 7013833},
+                "source_sha256": "3180c37439691ceb174ae1a194e3618ebe0956555827687c3676b72882892710",
+                "bytes_per_launch": 7014221},
 }
 
 
