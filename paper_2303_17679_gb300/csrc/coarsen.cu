@@ -59,6 +59,7 @@
 // ratings in separate arrays (a 32-bit CAS claims a key, an atomic add sums
 // into the value).
 #include <algorithm>
+#include <type_traits>
 #include <mutex>
 
 #include "common.cuh"
@@ -989,12 +990,24 @@ k_rate_split_argmax(RateArgs A, const int32_t* __restrict__ split, int32_t lo, i
       for (int32_t t = part_off[i] + threadIdx.x; t < part_off[i + 1]; t += blockDim.x)
         better(bv, bc, res_v[t], res_c[t]);
     } else if (dense) {
-      const int32_t cap = (int32_t)tab_cap[i];
-      for (int32_t C = threadIdx.x; C < cap; C += blockDim.x) {
-        const VT v = tval[base + C];
-        if (v == (VT)0) continue;
-        better(bv, bc, v, C);
-        tval[base + C] = 0;
+      // 16-byte loads over the whole table (every table offset and capacity
+      // is a multiple of 4 entries); only vectors holding a rating are
+      // cleared
+      constexpr int PER = 16 / (int)sizeof(VT);
+      using V = typename std::conditional<sizeof(VT) == 4, uint4, ulonglong2>::type;
+      const int32_t nvec = (int32_t)tab_cap[i] / PER;
+      V* tv = reinterpret_cast<V*>(tval + base);
+      for (int32_t x = threadIdx.x; x < nvec; x += blockDim.x) {
+        const V vv = tv[x];
+        const VT* e = reinterpret_cast<const VT*>(&vv);
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+          if (e[q] == (VT)0) continue;
+          any = true;
+          better(bv, bc, e[q], x * PER + q);
+        }
+        if (any) tv[x] = V{};
       }
     } else {
       const int32_t nu = tnused[i];
@@ -1174,7 +1187,7 @@ __global__ void k_split_sizes(const int32_t* __restrict__ split, int32_t nsplit,
     parts[i] = part ? P : 0;
     dense[i] = d ? 1 : 0;
     if (d) {
-      cap[i] = n;
+      cap[i] = (n + 3) & ~3;  // a multiple of 4: every table starts 16-byte aligned
     } else if (part) {
       cap[i] = 0;
     } else {
