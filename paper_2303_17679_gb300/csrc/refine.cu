@@ -470,6 +470,11 @@ __device__ __forceinline__ void gain_best(const GainPart& g, int k, int from, lo
   }
 }
 
+// Sort key: gain descending, node id ascending (gains are < 2^31).
+__device__ __forceinline__ unsigned long long sel_key(long long g, int32_t u) {
+  return ((unsigned long long)(0x7fffffffLL - g) << 32) | (unsigned)u;
+}
+
 struct GainArgs {
   const int32_t* ioff;
   const int32_t* inets;
@@ -484,6 +489,10 @@ struct GainArgs {
   int32_t* mv_to;  // target | source << 8
   long long* mv_g;
   int32_t* dcount;
+  // k <= 16: the sort keys of each direction's first dcap moves, dcap slots
+  // per direction (dcap = 0: not kept)
+  unsigned long long* dkeys;
+  int32_t dcap;
   int32_t* words;
   unsigned long long* work;
   bool graph;       // graph level: gains from adj and part, no Phi / Lambda
@@ -497,7 +506,9 @@ __device__ __forceinline__ void gain_emit(const GainArgs& A, int32_t u, int from
     A.mv_u[slot] = u;
     A.mv_to[slot] = t | (from << 8);  // target block, source block above bit 8
     A.mv_g[slot] = g;
-    atomicAdd(&A.dcount[from * A.k + t], 1);
+    const int d = from * A.k + t;
+    const int32_t pos = atomicAdd(&A.dcount[d], 1);
+    if (pos < A.dcap) A.dkeys[(size_t)d * A.dcap + pos] = sel_key(g, u);
   }
 }
 
@@ -702,16 +713,15 @@ __global__ void k_lp_bucket(const int32_t* __restrict__ mv_to, int k,
 
 constexpr int SEL_THREADS = 256;
 constexpr int SEL_GATHER_K = 16;
+// Moves per direction kept in the best-move kernels' key lists (k <= 16);
+// a direction with more moves is gathered from the move list.
+constexpr int32_t SEL_DIR_KEYS = 1024;
 // Moves per direction sorted in shared memory (more go through global
 // memory): 4096 for k <= 8, 2048 for k <= 16, else 1024 (pairs hold fewer
 // moves as k grows, and a smaller buffer lets more pair blocks share an SM).
 __host__ __device__ inline int sel_cap_for(int k) { return k <= 8 ? 4096 : (k <= 16 ? 2048 : 1024); }
 inline size_t sel_smem_bytes(int cap) { return (size_t)(4 * cap + 2) * sizeof(unsigned long long); }
 
-// Sort key: gain descending, node id ascending (gains are < 2^31).
-__device__ __forceinline__ unsigned long long sel_key(long long g, int32_t u) {
-  return ((unsigned long long)(0x7fffffffLL - g) << 32) | (unsigned)u;
-}
 
 // The weight prefixes of both directions of a pair from one block-wide scan
 // over the concatenation of their sorted moves: A[x] = weight of the first x
@@ -801,7 +811,8 @@ k_lp_select(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
             const int32_t* __restrict__ words, int32_t* __restrict__ part,
             unsigned long long* __restrict__ moved, int32_t* __restrict__ ap_u,
             int32_t* __restrict__ ap_from, int32_t* __restrict__ ap_to,
-            int32_t* __restrict__ ap_count, bool graph) {
+            int32_t* __restrict__ ap_count, bool graph,
+            const unsigned long long* __restrict__ dkeys, int32_t dcap) {
   extern __shared__ __align__(16) unsigned long long sel_smem[];
   const int cap = sel_cap_for(k);
   unsigned long long* s_keys0 = sel_smem;
@@ -859,7 +870,13 @@ k_lp_select(const int32_t* __restrict__ ioff, const int32_t* __restrict__ inets,
   long long* A = na <= cap ? s_pre0 : gpre + (int64_t)oa + dab;
   long long* B = nb <= cap ? s_pre1 : gpre + (int64_t)ob + dba;
 
-  if constexpr (GATHER) {
+  if (GATHER && na <= dcap && nb <= dcap) {
+    // both directions fit the key lists the best-move kernels filled
+    const unsigned long long* da = dkeys + (size_t)dab * dcap;
+    const unsigned long long* db = dkeys + (size_t)dba * dcap;
+    for (int i = threadIdx.x; i < Pa; i += blockDim.x) ka[i] = i < na ? da[i] : ~0ull;
+    for (int i = threadIdx.x; i < Pb; i += blockDim.x) kb[i] = i < nb ? db[i] : ~0ull;
+  } else if constexpr (GATHER) {
     const int32_t nm = words[SW_MOVES];
     const unsigned below = (1u << lane_id()) - 1u;
     // GATHER_ILP moves per thread and round: their directions are loaded
@@ -1331,6 +1348,11 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   ap_from.alloc(&cx.alloc, acap);
   ap_to.alloc(&cx.alloc, acap);
   gkeys.alloc(&cx.alloc, 2 * ncap + 2);
+  // k <= 16: per-direction key lists filled by the best-move kernels, read by
+  // the pair blocks instead of gathering the sub-round's whole move list
+  const int32_t dcap = k <= SEL_GATHER_K ? SEL_DIR_KEYS : 0;
+  DBuf<unsigned long long> dkeys;
+  if (dcap > 0) dkeys.alloc(&cx.alloc, (size_t)kk * dcap);
   gpre.alloc(&cx.alloc, ncap + (size_t)kk + 2);
   dcnt.alloc(&cx.alloc, (size_t)S * kk);
   dfill.alloc(&cx.alloc, (size_t)S * kk);
@@ -1371,6 +1393,8 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
   G.mv_u = mv_u.p;
   G.mv_to = mv_to.p;
   G.mv_g = mv_g.p;
+  G.dkeys = dkeys.p;
+  G.dcap = dcap;
   G.work = counters.p + 1;
   G.graph = L.graph;
   G.adj = L.adj.p;
@@ -1472,7 +1496,7 @@ LPResult lp_refine_level(const Ctx& cx, const Level& L, int level_index, int k, 
         sel<<<g_sel, SEL_THREADS, sel_bytes, sm>>>(
             L.ioff.p, L.inets.p, bucket.p, doff.p, dc_s, mv_u.p, mv_to.p, mv_g.p, L.c.p, st.bw.p,
             dbw.p, s, lmax, k, gkeys.p, gpre.p, w_s, part, counters.p, ap_u.p,
-            ap_from.p, ap_to.p, w_s + SW_APPROVED, L.graph);
+            ap_from.p, ap_to.p, w_s + SW_APPROVED, L.graph, dkeys.p, dcap);
         check_launch("lp_select");
         mark(fj, sm, s, 2);
       }
