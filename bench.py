@@ -44,11 +44,11 @@ L2_FLUSH_BYTES = 512 << 20
 # captures are summarised under profiles/.
 TRAFFIC = {
     "rating": {"source": "paper_2303_17679_gb300/csrc/coarsen.cu",
-               "source_sha256": "7aa0826d3707ff1b7de6a75e42c0af837a3b31e0f1b57fcec49264f3f59f18e4",
-               "bytes_per_launch": 21216630},
+               "source_sha256": "81ed6793c60fad599654f8f6201725e95d2a5b026c40365c9c1f05698443dde5",
+               "bytes_per_launch": 21268333},
     "lp_gain": {"source": "paper_2303_17679_gb300/csrc/refine.cu",
-                "source_sha256": "3180c37439691ceb174ae1a194e3618ebe0956555827687c3676b72882892710",
-                "bytes_per_launch": 7014221},
+                "source_sha256": "6228ca18356c02feff55833c447650f4c67bd3122f2caf14e1086f7b5d0c1b40",
+                "bytes_per_launch": 7014247},
 }
 
 
