@@ -788,7 +788,7 @@ def run_ours(args, world, rank, local):
         "roofline": {"bound": "hbm", "kernel": d["kernel"], "achieved": d.get("achieved_gbs", 0.0),
                      "peak": peak, "unit": "GB/s", "frac": d.get("frac", 0.0), "traffic": traffic,
                      "peak_kind": peak_kind + " (hbm_gbs, copy burst)",
-                     "bytes_model": "survey 8(d) per-phase formulas from per-level statistics",
+                     "bytes_model": "per-phase algorithmic byte formulas (rating, approval, contraction, pin counts, LP gain and apply, objective) from per-level statistics",
                      "durations": f"CUDA events on the library's stream over {ni} instrumented "
                                   "steps run right after the timed steps (the per-kernel events "
                                   "stay out of the headline steps)",
