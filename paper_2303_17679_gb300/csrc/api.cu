@@ -199,14 +199,15 @@ int hg_create(int32_t n, int32_t m, const int32_t* net_offsets, const int32_t* p
   if (mem == HG_MEM_HOST) {
     p = net_offsets[m];
     if (p > 0 && !pins) return HG_ERR_INVALID;
-    if (p < 0 || p >= (1ll << 31)) return HG_ERR_INVALID;
-    // offsets and weights here; the pins (ranges and repeats inside a net,
-    // O(p) host work per call) here too for small inputs, else on the device
-    // after the upload, which keeps concurrent callers' host threads free
-    const bool host_pins = p <= HOST_PIN_CHECK_MAX;
-    const int rc = check_host_csr(n, m, net_offsets, host_pins ? pins : nullptr, net_weights,
-                                  node_weights, &W);
-    if (rc != HG_OK) return rc;
+    if (p < 0 || p >= (1ll << 31) || net_offsets[0] != 0) return HG_ERR_INVALID;
+    // small inputs are checked here (offsets, weights, pin ranges and repeats
+    // inside a net); larger ones on the device right after the upload, which
+    // keeps the O(m + n + p) checks off the caller's thread and overlaps them
+    // with nothing else on the host
+    if (p <= HOST_PIN_CHECK_MAX) {
+      const int rc = check_host_csr(n, m, net_offsets, pins, net_weights, node_weights, &W);
+      if (rc != HG_OK) return rc;
+    }
   }
   auto h = std::make_unique<hg_t>();
   h->opt = o;
@@ -246,9 +247,8 @@ int hg_create(int32_t n, int32_t m, const int32_t* net_offsets, const int32_t* p
     upload(h->cx, L->pins, pins, (size_t)p, mem, 0);
     upload(h->cx, L->w, net_weights, (size_t)m, mem, 1);
     upload(h->cx, L->c, node_weights, (size_t)n, mem, 1);
-    if (mem == HG_MEM_HOST) {
-      if (p > HOST_PIN_CHECK_MAX && !hgk::validate_pins_device(h->cx, *L))
-        throw HgError(HG_ERR_INVALID, "pins failed validation");
+    if (mem == HG_MEM_HOST && p <= HOST_PIN_CHECK_MAX) {
+      // checked on the host above
     } else {
       int64_t wn = 0, ww = 0;
       if (!hgk::validate_level_device(h->cx, *L, &wn, &ww))

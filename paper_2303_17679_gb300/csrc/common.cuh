@@ -322,9 +322,6 @@ void build_graph_adjacency(const Ctx& cx, Level& L);
 // positive.  Returns false if invalid.
 bool validate_level_device(const Ctx& cx, const Level& L, int64_t* total_node_w,
                            int64_t* total_net_w);
-// The pins alone (in range, no node twice in a net) of a level whose offsets
-// are valid: host inputs, whose offsets and weights the host checks.
-bool validate_pins_device(const Ctx& cx, const Level& L);
 
 // ------------------------------------------------------ coarsening (coarsen.cu)
 
