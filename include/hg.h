@@ -175,9 +175,10 @@ void hg_default_options(hg_options* opt);
  * Builds the incident-net lists I(u) on the device (a1).  Rejects with
  * HG_ERR_INVALID: bad sizes or offsets, pins out of range, repeated pins in
  * a net, empty nets, weights <= 0, total node or net weight >= 2^31
- * (host inputs of up to 65,536 pins are checked on the host; larger host
- * inputs and all device inputs are checked on the device right after the
- * upload).  *out is NULL on failure. */
+ * (host inputs: up to 65,536 pins checked on the host; up to 4,194,304
+ * pins offsets and weights on the host and pins on the device after the
+ * upload; larger host inputs and all device inputs on the device right after
+ * the upload).  *out is NULL on failure. */
 int hg_create(int32_t n, int32_t m, const int32_t* net_offsets, const int32_t* pins,
               const int32_t* net_weights, const int32_t* node_weights, int32_t mem,
               const hg_options* opt, void* cuda_stream, hg_t** out);

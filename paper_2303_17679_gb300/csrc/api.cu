@@ -50,6 +50,7 @@ int guarded(hg_t* h, F&& body) {
 // Host inputs with at most this many pins have their pins checked on the
 // host, larger ones on the device.
 constexpr int64_t HOST_PIN_CHECK_MAX = 1 << 16;
+constexpr int64_t HOST_CSR_CHECK_MAX = 1 << 22;
 
 bool valid_level(const hg_t* h, int32_t level) {
   return level >= 0 && level < (int32_t)h->levels.size();
@@ -200,12 +201,15 @@ int hg_create(int32_t n, int32_t m, const int32_t* net_offsets, const int32_t* p
     p = net_offsets[m];
     if (p > 0 && !pins) return HG_ERR_INVALID;
     if (p < 0 || p >= (1ll << 31) || net_offsets[0] != 0) return HG_ERR_INVALID;
-    // small inputs are checked here (offsets, weights, pin ranges and repeats
-    // inside a net); larger ones on the device right after the upload, which
-    // keeps the O(m + n + p) checks off the caller's thread and overlaps them
-    // with nothing else on the host
-    if (p <= HOST_PIN_CHECK_MAX) {
-      const int rc = check_host_csr(n, m, net_offsets, pins, net_weights, node_weights, &W);
+    // small inputs are checked here in full; mid-sized ones here for their
+    // offsets and weights and on the device for their pins (ranges and
+    // repeats inside a net); large ones entirely on the device right after
+    // the upload, where the checks of millions of entries cost less than on
+    // the caller's thread (many concurrent callers of mid-sized inputs keep
+    // their O(m + n) host checks, which run in parallel on their threads)
+    if (p <= HOST_CSR_CHECK_MAX) {
+      const int rc = check_host_csr(n, m, net_offsets, p <= HOST_PIN_CHECK_MAX ? pins : nullptr,
+                                    net_weights, node_weights, &W);
       if (rc != HG_OK) return rc;
     }
   }
@@ -249,6 +253,9 @@ int hg_create(int32_t n, int32_t m, const int32_t* net_offsets, const int32_t* p
     upload(h->cx, L->c, node_weights, (size_t)n, mem, 1);
     if (mem == HG_MEM_HOST && p <= HOST_PIN_CHECK_MAX) {
       // checked on the host above
+    } else if (mem == HG_MEM_HOST && p <= HOST_CSR_CHECK_MAX) {
+      if (!hgk::validate_pins_device(h->cx, *L))
+        throw HgError(HG_ERR_INVALID, "pins failed validation");
     } else {
       int64_t wn = 0, ww = 0;
       if (!hgk::validate_level_device(h->cx, *L, &wn, &ww))

@@ -316,6 +316,9 @@ void build_incidence(const Ctx& cx, Level& L);
 bool level_is_graph(const Ctx& cx, const Level& L);
 // Sets L.graph and builds L.adj (after build_incidence).
 void build_graph_adjacency(const Ctx& cx, Level& L);
+// The pins alone (in range, no node twice in a net) of a level whose offsets
+// are valid: mid-sized host inputs, whose offsets and weights the host checks.
+bool validate_pins_device(const Ctx& cx, const Level& L);
 
 // Device-side validation of a level given by device pointers: offsets
 // monotone, pins in range, no net empty, no repeated pin in a net, weights

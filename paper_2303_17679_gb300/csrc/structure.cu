@@ -311,6 +311,23 @@ bool distinct_pins(const Ctx& cx, const Level& L) {
 
 }  // namespace
 
+bool validate_pins_device(const Ctx& cx, const Level& L) {
+  if (L.p > 0) {
+    k_validate_pins<<<grid_for(L.p, 256, cx.num_sms, 8), 256, 0, cx.stream>>>(L.pins.p, L.p, L.n,
+                                                                             cx.d_status);
+    check_launch("validate_pins");
+    int32_t st = 0;
+    HG_CUDA(cudaMemcpyAsync(&st, cx.d_status, sizeof(st), cudaMemcpyDeviceToHost, cx.stream));
+    HG_CUDA(cudaStreamSynchronize(cx.stream));
+    if (st != DEV_OK) {
+      int32_t zero = 0;
+      HG_CUDA(cudaMemcpy(cx.d_status, &zero, sizeof(zero), cudaMemcpyHostToDevice));
+      return false;
+    }
+  }
+  return distinct_pins(cx, L);
+}
+
 bool validate_level_device(const Ctx& cx, const Level& L, int64_t* total_node_w,
                            int64_t* total_net_w) {
   DBuf<unsigned long long> sums;

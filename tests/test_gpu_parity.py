@@ -460,17 +460,27 @@ def test_device_input_with_repeated_pins_rejected():
                 assert ei.value.status == hg.HG_ERR_INVALID
 
 
-@pytest.mark.parametrize("fault", ["out_of_range", "repeat_small", "repeat_big", "none"])
-def test_large_host_input_pins_checked_on_the_device(fault):
-    """Host inputs above 65,536 pins have their pins checked on the device:
-    a pin out of range or a node repeated inside a net (small or large net)
-    is rejected with HG_ERR_INVALID and the next create succeeds."""
-    hgr = synth.random_uniform(61, 30_000, 40_000)
+@pytest.mark.parametrize("size", ["mid", "large"])
+@pytest.mark.parametrize("fault", ["out_of_range", "repeat_small", "repeat_big", "bad_weight",
+                                   "decreasing_offsets", "none"])
+def test_large_host_input_pins_checked_on_the_device(fault, size):
+    """Host inputs above 65,536 pins have their pins checked on the device
+    (above 4,194,304 pins their offsets and weights too): a pin out of range,
+    a node repeated inside a net (small or large net), a weight of zero or an
+    empty net is rejected with HG_ERR_INVALID and the next create succeeds."""
+    hgr = (synth.random_uniform(61, 30_000, 40_000) if size == "mid"
+           else synth.random_uniform(62, 600_000, 1_200_000))
     assert hgr.p > 1 << 16
+    assert (hgr.p > 1 << 22) == (size == "large")
     off = np.concatenate([hgr.offsets, [hgr.p + 2000]]).astype(np.int32)
     big = np.arange(0, 4000, 2, dtype=np.int32)  # a 2000-pin net
     pins = np.concatenate([hgr.pins, big]).astype(np.int32)
-    if fault == "out_of_range":
+    w = np.concatenate([hgr.net_w, [1]]).astype(np.int32)
+    if fault == "bad_weight":
+        w[hgr.m // 3] = 0
+    elif fault == "decreasing_offsets":
+        off[hgr.m // 2] = off[hgr.m // 2 + 1]  # an empty net
+    elif fault == "out_of_range":
         pins[hgr.p // 2] = hgr.n
     elif fault == "repeat_small":
         e = 7
@@ -478,7 +488,6 @@ def test_large_host_input_pins_checked_on_the_device(fault):
         pins[b + 1] = pins[b]
     elif fault == "repeat_big":
         pins[-1] = pins[-1000]
-    w = np.concatenate([hgr.net_w, [1]]).astype(np.int32)
     stream = torch.cuda.current_stream()
     if fault == "none":
         h = hg.hg_create(hgr.n, hgr.m + 1, off, pins, w, hgr.node_w, hg.HG_MEM_HOST, make_opt(),
