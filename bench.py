@@ -44,7 +44,7 @@ L2_FLUSH_BYTES = 512 << 20
 # captures are summarised under profiles/.
 TRAFFIC = {
     "rating": {"source": "paper_2303_17679_gb300/csrc/coarsen.cu",
-               "source_sha256": "81ed6793c60fad599654f8f6201725e95d2a5b026c40365c9c1f05698443dde5",
+               "source_sha256": "e791612ac7ac4700d2b822fa47e78481781f9cf5a71578e9c4b1bce5f331d485",
                "bytes_per_launch": 21268333},
     "lp_gain": {"source": "paper_2303_17679_gb300/csrc/refine.cu",
                 "source_sha256": "6228ca18356c02feff55833c447650f4c67bd3122f2caf14e1086f7b5d0c1b40",

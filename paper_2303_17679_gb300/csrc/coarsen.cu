@@ -32,6 +32,10 @@
 //              8-byte load, with no dependent gather.
 //   cst[C]   = {cw[C], status[C]}: cluster weight and status (the node's
 //              sub-round while it is unclustered, -1 once clustered).
+//   imeta[j] = {first pin, rated size or 0, Q20 term} of the net of
+//              incidence j, and lnode[x] = {u, ioff[u], ioff[u+1], c(u)} for
+//              every listed node: a node's walk reads its own record, then one
+//              record per incident net.
 // Nodes are bucketed per level by class and sub-round.  With W(u) = sum of
 // |e| over u's rated nets (the pins its rating visits) and D = min(W(u), n)
 // (a bound on its distinct candidates), a team accumulates u's ratings in a
@@ -46,12 +50,13 @@
 //            warps (eight with 64-bit ratings), 8192 slots;
 //   class 4  the rest, split over the grid: a table in global memory direct-
 //            indexed by cluster id when n <= min(2 W, 65536), filled by items
-//            of 32 incident nets spread over the grid; else P = ceil(D / 9830)
-//            part blocks (P <= 8) of 1024 threads, each owning the candidates
-//            of one hash part in a 16384-slot shared table with a list of its
-//            inserted slots; else a global hash table filled by items.  A
-//            second kernel takes the argmax per node (or the best of the
-//            parts' bests).
+//            of 32 incident nets spread over the grid (the table padded to a
+//            multiple of 4 entries); else P = ceil(D / 13516) part blocks
+//            (64-bit ratings: ceil(D / 9830); P <= 8) of 1024 threads, each
+//            owning the candidates of one hash part in a 22528-slot (16384)
+//            shared table with a list of its inserted slots; else a global
+//            hash table filled by items.  A second kernel takes the argmax per
+//            node (or the best of the parts' bests).
 // Class 4 keeps the heaviest nodes (coarse levels: hundreds of thousands of
 // pin visits per node) from serialising a sub-round on one block.  Ratings
 // are accumulated in 32-bit words when the level's largest possible rating
