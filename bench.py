@@ -47,7 +47,7 @@ TRAFFIC = {
                "source_sha256": "e791612ac7ac4700d2b822fa47e78481781f9cf5a71578e9c4b1bce5f331d485",
                "bytes_per_launch": 21268333},
     "lp_gain": {"source": "paper_2303_17679_gb300/csrc/refine.cu",
-                "source_sha256": "6228ca18356c02feff55833c447650f4c67bd3122f2caf14e1086f7b5d0c1b40",
+                "source_sha256": "c51f75595d69410e0552f2464010ee93326afdafa9c1137fd140d2ace5ac64d2",
                 "bytes_per_launch": 7014247},
 }
 

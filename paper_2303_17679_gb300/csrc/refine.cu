@@ -795,9 +795,11 @@ __device__ void block_bitonic_sort2(unsigned long long* a, int Pa, unsigned long
 // finds the last state (i, j) on the merge path of A[0..na-1] and
 // B[0..nb-1] (ties to A) with -slack_a <= A[i] - B[j] <= slack_b.  Moves in
 // the chosen prefixes are approved.
-// GATHER (small k): no bucket pass; every pair block reads the whole move
-// list of the sub-round and keeps the moves of its two directions (their
-// order is irrelevant, the keys are sorted), and the global offsets of a
+// GATHER (small k): no bucket pass; a pair block reads its two directions'
+// sort keys from the lists the best-move kernels filled (dkeys, dcap slots
+// per direction), or, when a direction has more moves than that, reads the
+// whole move list of the sub-round and keeps the moves of its two directions
+// (their order is irrelevant, the keys are sorted); the global offsets of a
 // direction too long for shared memory are summed from dcount.
 template <bool GATHER>
 __global__ void __launch_bounds__(SEL_THREADS)
