@@ -102,7 +102,8 @@ __global__ void k_remap_small(const int32_t* __restrict__ list, int32_t count,
   }
 }
 
-// Nets of 33..4096 pins: one block per net, bitonic sort in shared memory.
+// Nets of 33..4096 pins: one block per net, bitonic sort with the keys in
+// registers (shared memory only for the exchanges between warps).
 __global__ void __launch_bounds__(MID_THREADS, 1024 / MID_THREADS)
 k_remap_mid(const int32_t* __restrict__ list, int32_t count, const int32_t* __restrict__ eoff,
             const int32_t* __restrict__ pins, const int32_t* __restrict__ map, int fp_bits,
@@ -117,22 +118,67 @@ k_remap_mid(const int32_t* __restrict__ list, int32_t count, const int32_t* __re
     const int32_t b = eoff[e], sz = eoff[e + 1] - b;
     int P = 64;
     while (P < sz) P <<= 1;
-    for (int q = threadIdx.x; q < P; q += blockDim.x) s[q] = q < sz ? map[pins[b + q]] : INT_MAX;
-    __syncthreads();
-    for (int kk = 2; kk <= P; kk <<= 1)
-      for (int j = kk >> 1; j > 0; j >>= 1) {
-        for (int q = threadIdx.x; q < P; q += blockDim.x) {
-          const int qx = q ^ j;
-          if (qx > q) {
-            const int32_t x = s[q], y = s[qx];
-            if ((x > y) == ((q & kk) == 0)) {
-              s[q] = y;
-              s[qx] = x;
+    // bitonic sort with the keys in registers: thread t holds items
+    // [t*PER, t*PER+PER); distances below PER are swaps inside a thread,
+    // below 32*PER lane shuffles, the rest exchanges through s (warps that
+    // hold only padding sit the network out)
+    const int t = threadIdx.x;
+    const bool warp_live = warp_in_block() * 32 * PER < P;
+    int32_t v[PER];
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const int q = t * PER + r;
+      v[r] = q < sz ? map[pins[b + q]] : INT_MAX;
+    }
+    for (int kk = 2; kk <= P; kk <<= 1) {
+      for (int j = kk >> 1; j >= PER; j >>= 1) {
+        if (j >= 32 * PER) {
+          __syncthreads();
+#pragma unroll
+          for (int r = 0; r < PER; ++r) s[t * PER + r] = v[r];
+          __syncthreads();
+#pragma unroll
+          for (int r = 0; r < PER; ++r) {
+            const int q = t * PER + r;
+            if (q >= P) continue;
+            const int32_t y = s[q ^ j];
+            const bool up = (q & kk) == 0, lower = (q & j) == 0;
+            const int32_t lo = min(v[r], y), hi = max(v[r], y);
+            v[r] = lower == up ? lo : hi;
+          }
+        } else if (warp_live) {
+          const int lj = j / PER;  // partner lane distance
+#pragma unroll
+          for (int r = 0; r < PER; ++r) {
+            const int q = t * PER + r;
+            const int32_t y = __shfl_xor_sync(FULL, v[r], lj);
+            const bool up = (q & kk) == 0, lower = (q & j) == 0;
+            const int32_t lo = min(v[r], y), hi = max(v[r], y);
+            v[r] = lower == up ? lo : hi;
+          }
+        }
+      }
+      if (warp_live) {
+#pragma unroll
+        for (int jj = PER / 2; jj > 0; jj >>= 1) {
+          if (jj >= kk) continue;
+#pragma unroll
+          for (int r = 0; r < PER; ++r) {
+            const int l = r ^ jj;
+            if (l > r) {
+              const bool up = ((t * PER + r) & kk) == 0;
+              const int32_t lo = min(v[r], v[l]), hi = max(v[r], v[l]);
+              v[r] = up ? lo : hi;
+              v[l] = up ? hi : lo;
             }
           }
         }
-        __syncthreads();
       }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < PER; ++r) s[t * PER + r] = v[r];
+    __syncthreads();
     // keep the first of every run: thread t owns items [t*PER, t*PER+PER)
     int32_t local = 0;
     bool keep[PER];
