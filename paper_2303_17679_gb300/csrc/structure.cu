@@ -94,6 +94,8 @@ __global__ void k_validate_nodes(const int32_t* __restrict__ c, int32_t n, int32
 // on offsets and pins already checked, so every read stays in bounds.
 constexpr int DISTINCT_WARPS = 4;
 constexpr int DISTINCT_SMALL = 1024;
+// largest total of the per-block node bitmaps of k_distinct_big_bitmap
+constexpr int64_t DISTINCT_BITMAP_BYTES = 256ll << 20;
 constexpr int DISTINCT_SET = 2 * DISTINCT_SMALL;
 
 __device__ __forceinline__ bool set_insert_new(int32_t* set, uint32_t mask, int32_t v) {
@@ -164,6 +166,37 @@ __global__ void k_distinct_big(const int32_t* __restrict__ eoff, const int32_t* 
     if (dup) s_dup = 1;
     __syncthreads();
     for (int32_t q = threadIdx.x; q < sz; q += blockDim.x) set_erase(set, cap - 1, pins[b + q]);
+    if (threadIdx.x == 0 && s_dup) dev_fail(status, DEV_BAD_INPUT);
+    __syncthreads();
+  }
+}
+
+// The same check with a bitmap of the n nodes per block (n bits), when the
+// bitmaps of all blocks are small: one atomicOr per pin finds a repeat and one
+// atomicAnd per pin clears the net's bits again, with no probing.
+__global__ void k_distinct_big_bitmap(const int32_t* __restrict__ eoff,
+                                      const int32_t* __restrict__ pins, int32_t m,
+                                      uint32_t* __restrict__ scratch, int64_t words,
+                                      int32_t* status) {
+  uint32_t* set = scratch + (size_t)blockIdx.x * (size_t)words;
+  __shared__ int s_dup;
+  for (int64_t e = blockIdx.x; e < m; e += gridDim.x) {
+    const int32_t b = eoff[e], sz = eoff[e + 1] - b;
+    if (sz <= DISTINCT_SMALL) continue;
+    if (threadIdx.x == 0) s_dup = 0;
+    __syncthreads();
+    bool dup = false;
+    for (int32_t q = threadIdx.x; q < sz; q += blockDim.x) {
+      const int32_t v = pins[b + q];
+      const uint32_t bit = 1u << (v & 31);
+      dup |= (atomicOr(&set[v >> 5], bit) & bit) != 0;
+    }
+    if (dup) s_dup = 1;
+    __syncthreads();
+    for (int32_t q = threadIdx.x; q < sz; q += blockDim.x) {
+      const int32_t v = pins[b + q];
+      atomicAnd(&set[v >> 5], ~(1u << (v & 31)));
+    }
     if (threadIdx.x == 0 && s_dup) dev_fail(status, DEV_BAD_INPUT);
     __syncthreads();
   }
@@ -286,7 +319,16 @@ bool distinct_pins(const Ctx& cx, const Level& L) {
                      cx.stream>>>(L.eoff.p, L.pins.p, L.m, cx.d_status);
   check_launch("distinct_small");
   const int32_t biggest = read_i32(cx, mx.p);
-  if (biggest > DISTINCT_SMALL) {
+  const int64_t words = ((int64_t)L.n + 31) / 32;
+  if (biggest > DISTINCT_SMALL && (int64_t)cx.num_sms * words * 4 <= DISTINCT_BITMAP_BYTES) {
+    const int blocks = cx.num_sms;
+    DBuf<uint32_t> scratch;
+    scratch.alloc(&cx.alloc, (size_t)blocks * (size_t)words);
+    HG_CUDA(cudaMemsetAsync(scratch.p, 0, scratch.bytes(), cx.stream));
+    k_distinct_big_bitmap<<<blocks, 256, 0, cx.stream>>>(L.eoff.p, L.pins.p, L.m, scratch.p,
+                                                         words, cx.d_status);
+    check_launch("distinct_big_bitmap");
+  } else if (biggest > DISTINCT_SMALL) {
     uint32_t cap = 1;
     while (cap < 2u * (uint32_t)biggest) cap <<= 1;
     const int blocks = cx.num_sms;
