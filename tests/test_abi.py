@@ -74,6 +74,30 @@ def test_malformed_host_input_rejected(lib, case):
     assert not h.value
 
 
+@pytest.mark.parametrize("fault", ["empty_net", "zero_weight", "heavy_nodes"])
+def test_mid_sized_host_input_checked_before_any_device_work(lib, fault):
+    """Host inputs of 65,536 to 4,194,304 pins have their offsets and weights
+    checked on the caller's thread before anything touches the device, so a
+    bad one is rejected on a host without a GPU."""
+    from paper_2303_17679_gb300 import hg
+    rng = np.random.default_rng(5)
+    n, m, size = 50_000, 30_000, 4
+    off = np.arange(0, size * m + 1, size, dtype=np.int32)
+    pins = np.concatenate([rng.choice(n, size, replace=False) for _ in range(m)]).astype(np.int32)
+    assert 1 << 16 < off[-1] <= 1 << 22
+    w = np.ones(m, np.int32)
+    c = np.ones(n, np.int32)
+    if fault == "empty_net":
+        off[m // 2] = off[m // 2 + 1]
+    elif fault == "zero_weight":
+        w[m // 3] = 0
+    else:
+        c[:] = 2 ** 20  # total node weight above 2^31
+    rc, h = _create(lib, n, m, off, pins, w, c)
+    assert rc == hg.HG_ERR_INVALID
+    assert not h.value
+
+
 def test_bad_options_rejected(lib):
     from paper_2303_17679_gb300 import hg
     o = hg.hg_default_options()
