@@ -440,7 +440,7 @@ def test_gain_table_and_objective_reject_bad_block_ids():
 def test_device_input_with_repeated_pins_rejected():
     """hg_create on device arrays rejects a node repeated inside a net, for
     small nets (warp match), mid-size nets (shared hash set) and nets above
-    1024 pins (global hash set); the valid versions are accepted."""
+    1024 pins (per-block node bitmap); the valid versions are accepted."""
     stream = torch.cuda.current_stream()
     n = 5000
     for size in (5, 300, 3000):
@@ -458,6 +458,30 @@ def test_device_input_with_repeated_pins_rejected():
                 with pytest.raises(hg.HgError) as ei:
                     hg.hg_create(n, 2, *args, hg.HG_MEM_DEVICE, make_opt(), stream)
                 assert ei.value.status == hg.HG_ERR_INVALID
+
+
+@pytest.mark.parametrize("repeat", [False, True])
+def test_repeated_pin_in_a_big_net_of_a_huge_node_set(repeat):
+    """With more than 14 million nodes the per-block node bitmaps of the
+    big-net repeat check would exceed their budget, so the check falls back
+    to per-block hash sets: a node repeated inside a 3000-pin net is still
+    rejected, and the net without the repeat is accepted."""
+    n = 15_000_000
+    size = 3000
+    pins = np.arange(0, n, n // size, dtype=np.int32)[:size].copy()
+    if repeat:
+        pins[-1] = pins[10]
+    off = np.array([0, size, size + 2], np.int32)
+    pins = np.concatenate([pins, [1, 2]]).astype(np.int32)
+    stream = torch.cuda.current_stream()
+    args = (dev(off), dev(pins), dev(np.ones(2, np.int32)), None)
+    if not repeat:
+        h = hg.hg_create(n, 2, *args, hg.HG_MEM_DEVICE, make_opt(), stream)
+        hg.hg_destroy(h)
+        return
+    with pytest.raises(hg.HgError) as ei:
+        hg.hg_create(n, 2, *args, hg.HG_MEM_DEVICE, make_opt(), stream)
+    assert ei.value.status == hg.HG_ERR_INVALID
 
 
 @pytest.mark.parametrize("size", ["mid", "large"])
